@@ -1,0 +1,246 @@
+"""FP64 CPU oracle of the warm-started stochastic-reconfiguration (WSSR) step.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. The product path
+(the CUDA library and its Python binding) never calls it and shares no code
+with it; the two meet only through the seeded inputs of ``synth``.
+
+What it computes (arXiv 2512.05749), written plainly in float64 numpy, each
+function following the passage it cites:
+
+* centring of the per-sample log-derivatives by their sample mean
+  (Section 3.1, Eq. (Osr) and Eq. (SN));
+* the S-matrix S = O_c^T O_c / N with O rows = samples (Section 3.1,
+  Eq. (Osrn): the paper's column-sample matrix carries the 1/sqrt(N));
+* simple subspace iteration U <- orth(S U) warm-started from the previous
+  subspace (Section 4.2, Eq. (max:SSI) and Algorithm 1), with Householder QR
+  as orth;
+* a Rayleigh-Ritz finish: a one-sided Jacobi SVD of O_c V / sqrt(N)
+  (Hestenes' method) gives sigma and the rotation of V (this replaces the
+  |diag R| sort at the end of Algorithm 1, whose output is left
+  unnormalised by the paper);
+* the low-rank-plus-damping apply of Eq. (updated_sr_1) (Section 4.1):
+  damped reading delta = [V diag(1/(sigma^2+lam)) V^T + lam^-1 (I - V V^T)] g,
+  and the paper's own cutoff reading (S^dagger + sigma_floor^-1 S^perp) g.
+
+Pins (tests/test_oracle_*.py): planted spectra with known singular values,
+orthonormality, warm start from the exact subspace being a fixed point, the
+closed-form convergence rate of subspace iteration on a diagonal matrix, the
+full-rank limit against a dense solve and the push-through identity of
+Eq. (mT), brute force on tiny inputs, and numpy/LAPACK as an external check.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "column_mean", "centre", "householder_qr", "jacobi_svd", "orth",
+    "subspace_iteration", "rayleigh_ritz", "fix_signs", "woodbury_apply",
+    "wssr_step", "init_subspace", "projector_distance", "S_matvec",
+]
+
+
+def column_mean(O: np.ndarray) -> np.ndarray:
+    """mu = (1/N) sum_n O[n, :] -- the sample estimate of the expectation in
+    Eq. (Osr) (Section 3.1); divisor N, not N-1."""
+    O = np.asarray(O, dtype=np.float64)
+    return O.sum(axis=0) / O.shape[0]
+
+
+def centre(O: np.ndarray) -> np.ndarray:
+    """O_c = O - 1 mu^T: every row minus the sample mean (Eq. (Osr))."""
+    O = np.asarray(O, dtype=np.float64)
+    return O - column_mean(O)[None, :]
+
+
+def S_matvec(Oc: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """S X with S = O_c^T O_c / N (Eq. (SN) with the 1/N of Eq. (Osrn))."""
+    return Oc.T @ (Oc @ X) / Oc.shape[0]
+
+
+def householder_qr(A: np.ndarray):
+    """Thin Householder QR of a tall matrix A (L x r, L >= r).
+
+    Returns Q (L x r, orthonormal columns) and R (r x r, upper triangular)
+    with a non-negative diagonal, A = Q R. Reflector k zeroes A[k+1:, k]
+    (Golub & Van Loan, Algorithm 5.2.1).
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    L, r = A.shape
+    if L < r:
+        raise ValueError("householder_qr needs L >= r")
+    vs = []
+    for k in range(r):
+        x = A[k:, k]
+        nx = np.linalg.norm(x)
+        if nx == 0.0:
+            vs.append(None)
+            continue
+        alpha = -nx if x[0] >= 0 else nx
+        v = x.copy()
+        v[0] -= alpha
+        nv = np.linalg.norm(v)
+        if nv == 0.0:
+            vs.append(None)
+            continue
+        v /= nv
+        A[k:, k:] -= 2.0 * np.outer(v, v @ A[k:, k:])
+        vs.append(v)
+    R = np.triu(A[:r, :r])
+    Q = np.zeros((L, r))
+    Q[:r, :r] = np.eye(r)
+    for k in reversed(range(r)):
+        v = vs[k]
+        if v is None:
+            continue
+        Q[k:, :] -= 2.0 * np.outer(v, v @ Q[k:, :])
+    s = np.where(np.diag(R) < 0, -1.0, 1.0)
+    return Q * s[None, :], R * s[:, None]
+
+
+def orth(A: np.ndarray) -> np.ndarray:
+    """orth(.) of Section 4.2: an orthonormal basis of range(A) (Householder Q)."""
+    return householder_qr(A)[0]
+
+
+def jacobi_svd(B: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
+    """One-sided Jacobi SVD (Hestenes 1958) of a tall matrix B (L x r).
+
+    Returns (P, s, W) with B = P diag(s) W^T, s descending, P (L x r) and
+    W (r x r) orthonormal. B is first reduced to its triangular factor
+    (B = Q R, Householder), then the columns of R are rotated pairwise until
+    every pair is orthogonal to ``tol`` relative to their norms; the singular
+    values are the final column norms (Demmel & Veselic 1992).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    L, r = B.shape
+    Qb, A = householder_qr(B)
+    A = A.copy()
+    W = np.eye(r)
+    for _ in range(max_sweeps):
+        rotated = False
+        for p in range(r - 1):
+            for q in range(p + 1, r):
+                ap, aq = A[:, p], A[:, q]
+                alpha = ap @ ap
+                beta = aq @ aq
+                gamma = ap @ aq
+                if gamma == 0.0 or abs(gamma) <= tol * np.sqrt(alpha * beta):
+                    continue
+                rotated = True
+                zeta = (beta - alpha) / (2.0 * gamma)
+                t = np.copysign(1.0, zeta) / (abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+                c = 1.0 / np.sqrt(1.0 + t * t)
+                s = c * t
+                A[:, p], A[:, q] = c * ap - s * aq, s * ap + c * aq
+                wp, wq = W[:, p].copy(), W[:, q].copy()
+                W[:, p], W[:, q] = c * wp - s * wq, s * wp + c * wq
+        if not rotated:
+            break
+    sv = np.linalg.norm(A, axis=0)
+    order = np.argsort(-sv, kind="stable")
+    sv, A, W = sv[order], A[:, order], W[:, order]
+    P = np.zeros_like(A)
+    nz = sv > 0
+    P[:, nz] = A[:, nz] / sv[nz][None, :]
+    return Qb @ P, sv, W
+
+
+def subspace_iteration(Oc: np.ndarray, V_prev: np.ndarray, m: int) -> np.ndarray:
+    """m steps of simple subspace iteration on S = O_c^T O_c / N.
+
+    Each step orthonormalises the current block and multiplies it by S
+    (Section 4.2: U^i = orth(O^ O^^T U^{i-1}); Algorithm 1: QR, then the two
+    products). A final orthonormalisation closes the loop. The span reached
+    is span(S^m V_prev).
+    """
+    V = np.asarray(V_prev, dtype=np.float64)
+    for _ in range(m):
+        Q = orth(V)
+        V = S_matvec(Oc, Q)
+    return orth(V)
+
+
+def rayleigh_ritz(Oc: np.ndarray, V: np.ndarray):
+    """Rayleigh-Ritz on span(V): SVD of B = O_c V / sqrt(N) = P diag(sigma) W^T.
+
+    Returns (V W, sigma): sigma are the Ritz singular values of O_c / sqrt(N)
+    (sigma^2 = Ritz values of S) in descending order, V W the Ritz vectors.
+    """
+    B = Oc @ V / np.sqrt(Oc.shape[0])
+    _, sigma, W = jacobi_svd(B)
+    return V @ W, sigma
+
+
+def fix_signs(V: np.ndarray) -> np.ndarray:
+    """Sign convention: each column's largest-magnitude entry is positive
+    (ties go to the lowest index)."""
+    V = np.array(V, dtype=np.float64, copy=True)
+    idx = np.argmax(np.abs(V), axis=0)
+    s = np.where(V[idx, np.arange(V.shape[1])] < 0, -1.0, 1.0)
+    return V * s[None, :]
+
+
+def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
+                   mode: str = "damped", sigma_floor: float | None = None) -> np.ndarray:
+    """The low-rank-plus-regulariser apply of Eq. (updated_sr_1) (Section 4.1).
+
+    ``damped``: delta = g/lam + V (d * (V^T g)), d_i = -sigma_i^2 / (lam (sigma_i^2 + lam)),
+    i.e. [V diag(1/(sigma^2+lam)) V^T + lam^-1 (I - V V^T)] g, which equals
+    (S + lam I)^-1 g when span(V) holds the whole range of S.
+
+    ``cutoff``: the paper's form (S^dagger + sigma_floor^-1 S^perp) g with
+    S^dagger = V diag(sigma^-2) V^T and S^perp = I - V V^T, i.e.
+    d_i = 1/sigma_i^2 - 1/sigma_floor (sigma_floor in S-eigenvalue units).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    c = V.T @ g
+    s2 = sigma * sigma
+    if mode == "damped":
+        d = -s2 / (lam * (s2 + lam))
+        return g / lam + V @ (d * c)
+    if mode == "cutoff":
+        if sigma_floor is None:
+            sigma_floor = lam
+        d = 1.0 / s2 - 1.0 / sigma_floor
+        return g / sigma_floor + V @ (d * c)
+    raise ValueError(mode)
+
+
+def wssr_step(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: int,
+              mode: str = "damped", sigma_floor: float | None = None):
+    """One WSSR step (Algorithm 2's SSI-SVD and update lines, history weight 0).
+
+    Returns (delta, sigma, V): delta ~ (S+lam I)^-1 g, sigma the r Ritz
+    singular values of O_c / sqrt(N) (descending), V (M x r) the Ritz
+    vectors with the sign convention of :func:`fix_signs`.
+    """
+    Oc = centre(O)
+    V = subspace_iteration(Oc, V_prev, m)
+    V, sigma = rayleigh_ritz(Oc, V)
+    V = fix_signs(V)
+    delta = woodbury_apply(V, sigma, g, lam, mode, sigma_floor)
+    return delta, sigma, V
+
+
+def init_subspace(O: np.ndarray, V_rand: np.ndarray, m_init: int = 20) -> np.ndarray:
+    """Cold start for the first step (the paper uses LMSVD there, Algorithm 2):
+    orthonormalise a seeded Gaussian block, then run m_init subspace
+    iterations followed by Rayleigh-Ritz. Returns V (M x r)."""
+    Oc = centre(O)
+    V = subspace_iteration(Oc, V_rand, m_init)
+    V, _ = rayleigh_ritz(Oc, V)
+    return fix_signs(V)
+
+
+def projector_distance(V1: np.ndarray, V2: np.ndarray) -> float:
+    """||V1 V1^T - V2 V2^T||_F for orthonormal V1, V2 of equal rank r.
+
+    Uses ||P1 - P2||_F^2 = 2r - 2||V2^T V1||_F^2 = 2 ||(I - P2) V1||_F^2 and
+    evaluates the last form, which avoids the cancellation of the first."""
+    V1 = np.asarray(V1, dtype=np.float64)
+    V2 = np.asarray(V2, dtype=np.float64)
+    resid = V1 - V2 @ (V2.T @ V1)
+    return float(np.sqrt(2.0) * np.linalg.norm(resid))

@@ -1,0 +1,196 @@
+"""Pins of the oracle's WSSR step (CPU only).
+
+* a hand-derived golden example (tests/golden/wssr_tiny.json);
+* planted spectra whose singular values are known by construction;
+* warm start from the exact dominant subspace is a fixed point (Section 4.2);
+* the closed-form convergence rate of subspace iteration on a diagonal S;
+* the full-rank limit: the damped apply equals (S + lam I)^-1 g, checked
+  against a dense solve and against the push-through (Woodbury) identity
+  that underlies Eq. (mT);
+* brute force on tiny inputs (powers of S in extended precision, LAPACK eigh);
+* the apply formula against explicit M x M operators for both readings of
+  Eq. (updated_sr_1).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import wssr_oracle as orc
+from synth import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "wssr_tiny.json")
+
+
+def _centred_orthonormal(N, K, seed):
+    """N x K orthonormal columns that are also orthogonal to the ones vector."""
+    G = np.random.default_rng(seed).standard_normal((N, K))
+    G -= G.mean(axis=0, keepdims=True)
+    Q, _ = np.linalg.qr(G)
+    return Q
+
+
+def _diag_S_problem(N, M, sv, seed, offset=3.0):
+    """O with S = diag(sv^2): O = sqrt(N) P diag(sv) + column offsets, P centred."""
+    P = _centred_orthonormal(N, M, seed)
+    offs = offset * np.random.default_rng(seed + 1).standard_normal(M)
+    return np.sqrt(N) * P * np.asarray(sv)[None, :] + offs[None, :]
+
+
+def test_golden_tiny_example():
+    gd = json.load(open(GOLDEN))
+    O = np.array(gd["O"])
+    g = np.array(gd["g"])
+    lam = gd["lam"]
+    assert np.allclose(orc.column_mean(O), gd["mean"], atol=1e-15)
+    Oc = orc.centre(O)
+    assert np.allclose(orc.S_matvec(Oc, np.eye(3)), gd["S"], atol=1e-15)
+    # rank 2 from a generic start: converged after enough iterations (ratio 0.25 per step)
+    V_prev = np.array(gd["r2"]["V_prev"])
+    delta, sigma, V = orc.wssr_step(O, g, V_prev, lam, m=60)
+    assert np.allclose(sigma, gd["r2"]["sigma"], atol=1e-13)
+    assert np.allclose(V, gd["r2"]["V"], atol=1e-13)
+    assert np.allclose(delta, gd["r2"]["delta_damped"], atol=1e-13)
+    delta_c, _, _ = orc.wssr_step(O, g, V_prev, lam, m=60, mode="cutoff", sigma_floor=lam)
+    assert np.allclose(delta_c, gd["r2"]["delta_cutoff"], atol=1e-13)
+    # rank 3 = full rank: the exact damped SR direction
+    delta3, sigma3, _ = orc.wssr_step(O, g, np.eye(3), lam, m=1)
+    assert np.allclose(sigma3, gd["r3"]["sigma"], atol=1e-13)
+    assert np.allclose(delta3, gd["r3"]["delta_damped"], atol=1e-13)
+
+
+def test_planted_spectrum_recovered():
+    N, M, r = 64, 40, 6
+    sv = 2.0 ** -np.arange(M, dtype=float)   # well separated
+    O = _diag_S_problem(N, M, sv, seed=3)
+    Vp = np.random.default_rng(4).standard_normal((M, r))
+    _, sigma, V = orc.wssr_step(O, np.ones(M), Vp, 1e-3, m=80)
+    assert np.abs(sigma / sv[:r] - 1).max() < 1e-12
+    assert orc.projector_distance(V, np.eye(M)[:, :r]) < 1e-12
+
+
+def test_planted_workload_generator_spectrum():
+    """synth's planted matrix (noise 0, U centred) has exactly the planted values."""
+    w = wl.small_planted(50, 30, 5, K=30, noise=0.0, sigma_power=1.0)
+    O = wl.planted_O_np(w)
+    Oc = orc.centre(O)
+    # generator U is not centred: compare against LAPACK on the centred matrix
+    sl = np.linalg.svd(Oc / np.sqrt(w.N), compute_uv=False)
+    Vp = np.random.default_rng(0).standard_normal((w.M, w.r))
+    _, sigma, _ = orc.wssr_step(O, np.ones(w.M), Vp, 1e-3, m=400)
+    assert np.abs(sigma / sl[:w.r] - 1).max() < 1e-10
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_exact_subspace_is_fixed_point(m):
+    N, M, r = 80, 30, 5
+    sv = np.linspace(3.0, 0.1, M)
+    O = _diag_S_problem(N, M, sv, seed=9)
+    Oc = orc.centre(O)
+    lamS, U = np.linalg.eigh(orc.S_matvec(Oc, np.eye(M)))
+    Vexact = U[:, ::-1][:, :r]
+    delta, sigma, V = orc.wssr_step(O, np.arange(M, dtype=float), Vexact, 1e-2, m=m)
+    assert orc.projector_distance(V, Vexact) < 1e-12
+    assert np.abs(sigma - np.sqrt(lamS[::-1][:r])).max() < 1e-13
+    assert np.abs(np.abs(np.sum(V * Vexact, axis=0)) - 1).max() < 1e-12
+
+
+def test_subspace_iteration_closed_form_rate():
+    """S diagonal, V_prev = [e1, e2 + eps e3]: after m steps the angle to
+    span(e1, e2) has tan = eps (s3/s2)^m with s = sv^2 (eigenvalues of S)."""
+    N, M = 40, 6
+    sv = np.array([2.0, 1.5, 1.2, 0.5, 0.3, 0.1])
+    O = _diag_S_problem(N, M, sv, seed=21)
+    Oc = orc.centre(O)
+    eps = 0.3
+    Vp = np.zeros((M, 2))
+    Vp[0, 0] = 1.0
+    Vp[1, 1] = 1.0
+    Vp[2, 1] = eps
+    for m in range(1, 6):
+        V = orc.subspace_iteration(Oc, Vp, m)
+        d = orc.projector_distance(V, np.eye(M)[:, :2])
+        sin_t = d / np.sqrt(2.0)
+        tan_t = sin_t / np.sqrt(1 - sin_t ** 2)
+        expect = eps * (sv[2] ** 2 / sv[1] ** 2) ** m
+        assert abs(tan_t - expect) < 1e-12 + 1e-9 * expect
+
+
+@pytest.mark.parametrize("N,M", [(10, 6), (6, 12), (9, 9)])
+def test_full_rank_limit_matches_dense_and_push_through(N, M):
+    rng = np.random.default_rng(N * 100 + M)
+    O = rng.standard_normal((N, M)) + 2.0
+    g = rng.standard_normal(M)
+    lam = 0.05
+    Oc = orc.centre(O)
+    r = min(N - 1, M)
+    delta, sigma, V = orc.wssr_step(O, g, rng.standard_normal((M, r)), lam, m=3)
+    S = Oc.T @ Oc / N
+    dense = np.linalg.solve(S + lam * np.eye(M), g)
+    push = (g - Oc.T @ np.linalg.solve(N * lam * np.eye(N) + Oc @ Oc.T, Oc @ g)) / lam
+    assert np.abs(dense - push).max() < 1e-11 * np.abs(dense).max()
+    assert np.abs(delta - dense).max() < 1e-11 * np.abs(dense).max()
+
+
+@pytest.mark.parametrize("N,M,r,m", [(12, 7, 2, 2), (5, 12, 3, 3), (11, 11, 4, 1)])
+def test_brute_force_tiny(N, M, r, m):
+    rng = np.random.default_rng(7 * N + M + r)
+    O = rng.standard_normal((N, M)) * np.linspace(2, 0.2, M)[None, :] + 1.5
+    Vp = rng.standard_normal((M, r))
+    Oc = orc.centre(O)
+    # span(S^m V_prev) by unnormalised powers in extended precision
+    Ocl = np.asarray(O, dtype=np.longdouble)
+    Ocl = Ocl - Ocl.sum(axis=0) / N
+    K = np.asarray(Vp, dtype=np.longdouble)
+    for _ in range(m):
+        K = Ocl.T @ (Ocl @ K) / N
+    Qb, _ = np.linalg.qr(np.asarray(K, dtype=np.float64))
+    V_it = orc.subspace_iteration(Oc, Vp, m)
+    assert orc.projector_distance(V_it, Qb) < 1e-10
+    # Ritz values on that span from LAPACK eigh of the projected S
+    Sp = Qb.T @ (Oc.T @ Oc / N) @ Qb
+    ritz = np.sqrt(np.clip(np.linalg.eigvalsh(Sp)[::-1], 0, None))
+    _, sigma, _ = orc.wssr_step(O, np.ones(M), Vp, 1e-3, m=m)
+    assert np.abs(sigma - ritz).max() < 1e-11 * ritz[0]
+
+
+@pytest.mark.parametrize("mode", ["damped", "cutoff"])
+def test_woodbury_against_explicit_operator(mode):
+    rng = np.random.default_rng(2)
+    M, r = 14, 4
+    V, _ = np.linalg.qr(rng.standard_normal((M, r)))
+    sigma = np.array([1.3, 0.7, 0.2, 0.05])
+    g = rng.standard_normal(M)
+    lam = 0.02
+    P = V @ V.T
+    if mode == "damped":
+        Op = V @ np.diag(1 / (sigma ** 2 + lam)) @ V.T + (np.eye(M) - P) / lam
+        got = orc.woodbury_apply(V, sigma, g, lam, "damped")
+    else:
+        floor = 0.01
+        Op = V @ np.diag(1 / sigma ** 2) @ V.T + (np.eye(M) - P) / floor
+        got = orc.woodbury_apply(V, sigma, g, lam, "cutoff", sigma_floor=floor)
+    assert np.abs(got - Op @ g).max() < 1e-12 * np.abs(Op @ g).max()
+
+
+def test_init_subspace_recovers_dominant_block():
+    N, M, r = 60, 40, 4
+    sv = np.concatenate([[4.0, 3.0, 2.0, 1.5], np.linspace(0.5, 0.01, M - 4)])
+    O = _diag_S_problem(N, M, sv, seed=5)
+    V = orc.init_subspace(O, np.random.default_rng(6).standard_normal((M, r)), m_init=20)
+    # error bound (0.5/1.5)^(2*20) ~ 1e-19: exact to rounding
+    assert orc.projector_distance(V, np.eye(M)[:, :r]) < 1e-12
+
+
+def test_removing_centring_is_detected():
+    """A column mean offset changes S unless it is removed: guards against a
+    dropped centring step."""
+    N, M = 30, 8
+    sv = np.linspace(1, 0.1, M)
+    O = _diag_S_problem(N, M, sv, seed=13, offset=5.0)
+    _, sigma, _ = orc.wssr_step(O, np.ones(M), np.eye(M)[:, :3], 1e-3, m=50)
+    assert np.abs(sigma - sv[:3]).max() < 1e-12
+    # uncentred S would have a leading value of order |offset|
+    Sraw = np.linalg.svd(O / np.sqrt(N), compute_uv=False)
+    assert Sraw[0] > 3.0
