@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the WSSR step (one line of JSON on stdout).
+
+Default workload: planted-spectrum O with N=16384 samples, M=1,000,000
+parameters, rank r=256, lambda=1e-4, m=2 subspace iterations, O stored and
+multiplied in BF16 (33 GB resident in HBM). A "step" is one wssr_step call:
+m x (pass A, Cholesky QR of Y, pass B, CholeskyQR2 of Z), the Rayleigh-Ritz
+finish (one more pass A) and the Woodbury apply.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--dtype bf16|f32] [--engine auto|simt|tcgen05] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (see cpu_sample()).
+Multi-GPU: every rank runs an independent replica (the step has no data
+exchange); rank 0 prints the line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WSSR step ms & % roofline at N=16k,M=1M,r=256 BF16 vs FP32; rel err vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max SM clock)
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(w, cols: int):
+    """Same recipe as the workload (planted spectrum, noise, offsets) with all
+    N samples but only `cols` parameters; the step cost of the oracle scales
+    linearly in M, so the sample time is scaled by M / cols."""
+    import dataclasses
+
+    import numpy as np
+
+    from synth import workloads as wl
+    ws = dataclasses.replace(w, M=cols, name=w.name + f"-sample{cols}")
+    O = wl.planted_O_np(ws)
+    if w.dtype == "bf16":
+        import torch
+        O = torch.from_numpy(O.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    else:
+        O = O.astype(np.float32).astype(np.float64)
+    g = wl.gradient_np(cols, 0, "bench").astype(np.float32).astype(np.float64)
+    V0 = wl.start_subspace_np(cols, w.r, "bench")
+    return ws, O, g, V0
+
+
+def time_oracle(w, cols: int, steps: int = 1):
+    from oracle import wssr_oracle as orc
+    ws, O, g, V0 = cpu_sample(w, cols)
+    Vp = orc.orth(V0)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        _, _, Vp = orc.wssr_step(O, g, Vp, w.lam, w.m)
+        times.append(time.perf_counter() - t0)
+    scale = w.M / cols
+    ms = [t * 1e3 * scale for t in times]
+    return ms, {"kind": "oracle", "cores": os.cpu_count(),
+                "sample": f"N={w.N}, M={cols} of {w.M} parameters, r={w.r}, m={w.m}; "
+                          f"time x {scale:.1f} (cost linear in M)"}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cols = args.cpu_cols
+    for _ in range(args.warmup if args.warmup <= 1 else 1):
+        time_oracle(w, cols, 1)
+    ms, info = time_oracle(w, cols, args.steps)
+    v = sum(ms) / len(ms)
+    info["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, args, "fp64 numpy oracle"),
+            "cpu_baseline": info,
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, args, engine):
+    return {"workload": w.name, "N": w.N, "M": w.M, "r": w.r, "lambda": w.lam, "m": w.m,
+            "o_dtype": args.dtype, "engine": engine, "parallelism": f"replicas{args.gpus}",
+            "l2": f"inputs larger than L2 (O = {w.N * w.M * (2 if args.dtype == 'bf16' else 4) / 1e9:.1f} GB)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def roofline_for(w, args, prof, steps, peaks, engine_name):
+    """Roofline of the dominant kernel (pass A or pass B product)."""
+    ms_a, n_a = prof["pass_A"]
+    ms_b, n_b = prof["pass_B"]
+    launches_a = max(1, n_a)
+    launches_b = max(1, n_b)
+    if ms_a >= ms_b:
+        name, t = "pass_A", ms_a / launches_a
+    else:
+        name, t = "pass_B", ms_b / launches_b
+    esz = 2 if args.dtype == "bf16" else 4
+    bytes_O = w.N * w.M * esz
+    flops = 2.0 * w.N * w.M * w.r
+    if engine_name == "tcgen05":
+        achieved = bytes_O / (t * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "ms_per_launch": t,
+                "algorithmic_per_launch": bytes_O, "peak_source": "measured copy bandwidth"}
+    achieved = flops / (t * 1e-3) / 1e12
+    peak = FP32_SIMT_PEAK_TFLOPS
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "ms_per_launch": t,
+            "algorithmic_per_launch": flops,
+            "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+
+
+def step_roofline_ms(w, args, peaks):
+    esz = 2 if args.dtype == "bf16" else 4
+    passes = 2 * w.m + 1
+    t_bytes = w.N * w.M * esz / (peaks["hbm_gbs"] * 1e9)
+    t_flop = 2.0 * w.N * w.M * w.r / (peaks["bf16_tflops"] * 1e12)
+    return passes * max(t_bytes, t_flop) * 1e3
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_05749_gb300 import WSSR
+    from synth import workloads as wl
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # ---- inputs, resident in HBM before the timed region ----
+    dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    ld = w.M + ((-w.M) % 8)
+    O = wl.planted_O_torch(w, dev, out_dtype=dt, ld=ld)
+    gs = [wl.gradient_torch(w.M, t, dev, "bench") for t in range(max(1, args.steps))]
+    V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
+    torch.cuda.synchronize()
+
+    s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine)
+    engine_name = "tcgen05" if (args.dtype == "bf16" and s.handle and args.engine != "simt"
+                                and _uses_tc(s)) else "simt"
+    V, _ = s.init_subspace(O, V0)
+    s.check("init_subspace")
+    delta = torch.empty(w.M, device=dev)
+    sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
+    Vb = torch.empty_like(V)
+    for t in range(args.warmup):
+        s.step(O, gs[t % len(gs)], V, out=(delta, sigma, Vb))
+        V, Vb = Vb, V
+    s.check("warmup")
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.profile_begin()
+    launches = 0
+    e0.record(stream)
+    for t in range(args.steps):
+        s.step(O, gs[t], V, out=(delta, sigma, Vb))
+        launches += s.last_launch_count()
+        V, Vb = Vb, V
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = s.profile_end()
+    s.check("timed steps")
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+
+    # ---- end to end through the public API from pinned host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        O_host = torch.empty(O.shape, dtype=O.dtype, pin_memory=True)
+        O_host.copy_(O)
+        g_host = [g.cpu().pin_memory() for g in gs[:args.e2e_steps]]
+        d_host = torch.empty(w.M, pin_memory=True)
+        s_host = torch.empty(w.r, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for t in range(args.e2e_steps):
+            O.copy_(O_host, non_blocking=True)
+            gs[t].copy_(g_host[t], non_blocking=True)
+            s.step(O, gs[t], V, out=(delta, sigma, Vb))
+            V, Vb = Vb, V
+            d_host.copy_(delta, non_blocking=True)
+            s_host.copy_(sigma, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        s.check("e2e")
+        e2e_ms = e2.elapsed_time(e3) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": e2e_ms, "unit": "ms",
+               "h2d_bytes_per_step": int(O.numel() * O.element_size() + 4 * w.M),
+               "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
+        del O_host
+
+    peaks, src = load_peaks()
+    roof = roofline_for(w, args, prof, args.steps, peaks, engine_name)
+    roof["peak_source"] += f" ({src})"
+    step_roof = step_roofline_ms(w, args, peaks)
+    s.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and args.cpu_cols > 0:
+        ms, info = time_oracle(w, args.cpu_cols, 1)
+        info["value"] = ms[0]
+        info["unit"] = "ms"
+        cpu = info
+    line = {
+        "metric": METRIC, "value": ms_step / world, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic", "config": workload_config(w, args, engine_name),
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof,
+        "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
+                          "model": f"{2 * w.m + 1} O passes x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _uses_tc(s) -> bool:
+    from paper_2512_05749_gb300 import wssr as W
+    import ctypes
+    # engine resolution is internal; AUTO uses tcgen05 whenever it is supported for BF16
+    try:
+        probe = W.WSSR(64, 64, 8, 1e-3, dtype="bf16", engine="tcgen05")
+        probe.close()
+        return True
+    except W.WSSRError:
+        return False
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="planted-n16384-m1m-r256")
+    ap.add_argument("--dtype", default=None, choices=[None, "bf16", "f32"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tcgen05"])
+    ap.add_argument("--m-init", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-cols", type=int, default=2048)
+    args = ap.parse_args()
+    from synth import workloads as wl
+    w = wl.WORKLOADS[args.workload]
+    if args.dtype is None:
+        args.dtype = w.dtype
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * wssr.h -- C ABI of the GB300 warm-started stochastic-reconfiguration (WSSR)
+ * step library (libwssr.so).
+ *
+ * The operation (arXiv 2512.05749):
+ *   O        N x M per-sample log-derivative matrix, rows = samples
+ *            (Section 3.1, Eq. (Osr) and Eq. (Osrn); here O is NOT pre-scaled
+ *            by 1/sqrt(N) and NOT centred -- the library centres it).
+ *   O_c      O - 1 mu^T with mu the column (sample) mean, divisor N (Eq. (Osr)).
+ *   S        O_c^T O_c / N, the S-matrix (Eq. (SN) with Eq. (Osrn)'s scaling).
+ *   V        M x r orthonormal basis of the dominant subspace of S; the
+ *            paper's left singular vectors U of O^ = O_c^T / sqrt(N)
+ *            (Eq. (svd:det), Section 4.1).
+ *   sigma    r singular values of O_c / sqrt(N), descending (sigma^2 are
+ *            the Ritz values of S; the paper's s_i, Section 4.1).
+ *   delta    [V diag(1/(sigma^2+lambda)) V^T + lambda^-1 (I - V V^T)] g
+ *            (damped reading of Eq. (updated_sr_1)), or with
+ *            WSSR_APPLY_CUTOFF the paper's (S^dagger + sigma_floor^-1 S^perp) g.
+ *
+ * One wssr_step = m rounds of warm-started simple subspace iteration on S
+ * (Section 4.2, Algorithm 1; orthonormalisation by Cholesky QR), a
+ * Rayleigh-Ritz finish on span(V), and the apply.
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers on the current CUDA device,
+ *     owned by the caller; the library never frees them. Matrices are dense
+ *     row-major. float = IEEE binary32, double = binary64, bf16 = bfloat16
+ *     stored as uint16_t.
+ *   - The library allocates device memory only in wssr_create (its
+ *     workspace) and frees it in wssr_destroy.
+ *   - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t,
+ *     0 = legacy default stream). A returned WSSR_OK only means that the
+ *     work was validated and enqueued; device-side failures (Cholesky
+ *     breakdown, non-finite data, a timed-out wait) are recorded in a sticky
+ *     status word that wssr_sync / wssr_get_status return.
+ *   - Nothing aborts, throws or traps. Argument errors return
+ *     WSSR_ERR_INVALID_ARG and enqueue nothing.
+ *   - One handle must not be used from two streams at once (its workspace
+ *     is shared by all calls on it).
+ */
+#ifndef WSSR_H_
+#define WSSR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wssr_ctx* wssr_handle;
+typedef void* wssr_stream_t; /* cudaStream_t */
+
+typedef enum {
+  WSSR_OK = 0,
+  WSSR_ERR_INVALID_ARG = 1,    /* bad shape, null pointer, misaligned O, bad option */
+  WSSR_ERR_OOM = 2,            /* workspace allocation failed in wssr_create */
+  WSSR_ERR_BREAKDOWN = 3,      /* Cholesky QR met a non-positive pivot (rank-deficient block) */
+  WSSR_ERR_NONFINITE = 4,      /* NaN/Inf met in O, g, V_prev or a small factor */
+  WSSR_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait ran out (kernel returned early) */
+  WSSR_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  WSSR_ERR_UNSUPPORTED = 7     /* feature not available for these options/shape */
+} wssr_status;
+
+enum { WSSR_DTYPE_F32 = 0, WSSR_DTYPE_BF16 = 1 };
+enum { WSSR_APPLY_DAMPED = 0, WSSR_APPLY_CUTOFF = 1 };
+enum { WSSR_OP_DENSE = 0 };
+/* Product engines for the two O passes. AUTO = tcgen05 tensor cores for
+ * BF16 when the shape allows it, SIMT FMA otherwise. */
+enum { WSSR_ENGINE_AUTO = 0, WSSR_ENGINE_SIMT = 1, WSSR_ENGINE_TCGEN05 = 2 };
+
+typedef struct {
+  int32_t m;            /* subspace iterations per step (>= 1; default 2) */
+  int32_t m_init;       /* iterations of wssr_init_subspace (default 20) */
+  int32_t dtype;        /* WSSR_DTYPE_*: element type of O in memory (default F32) */
+  int32_t apply_mode;   /* WSSR_APPLY_* (default DAMPED) */
+  double sigma_floor;   /* CUTOFF mode: the paper's sigma_floor, in S-eigenvalue
+                           units (> 0); ignored for DAMPED */
+  int64_t wait_cap;     /* iteration cap of every device spin-wait (default 1<<26) */
+  int32_t engine;       /* WSSR_ENGINE_* (default AUTO) */
+  int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
+} wssr_options;
+
+/* O given as a dense matrix. O points to N rows of `ld` elements
+ * (ld >= M; only the first M are read). For the tensor-core engine the
+ * row pitch ld * sizeof(elem) must be a multiple of 16 bytes and O must be
+ * 16-byte aligned. */
+typedef struct {
+  int32_t kind;        /* WSSR_OP_DENSE */
+  int32_t reserved;
+  const void* O;       /* device, N x ld, element type = options.dtype */
+  int64_t ld;
+} wssr_operator;
+
+/* Fill `opt` with the defaults listed above. */
+void wssr_default_options(wssr_options* opt);
+
+/* Create a context for N samples, M parameters, rank r, damping lambda > 0.
+ * Constraints: 2 <= N, 1 <= r <= 256, r % 8 == 0, r <= N - 1, r <= M.
+ * Allocates the whole workspace (about 3 M r floats + small terms).
+ * opt may be NULL (defaults). On failure *out is NULL. */
+wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda,
+                        const wssr_options* opt, wssr_handle* out);
+
+/* One WSSR step (Section 4.2 Algorithm 1 warm-started from V_prev, Rayleigh-Ritz,
+ * Eq. (updated_sr_1) apply).
+ *   op      the N x M matrix O (not centred)
+ *   g       M floats, the energy gradient
+ *   V_prev  M x r floats, previous subspace (need not be exactly orthonormal,
+ *           must have full column rank)
+ *   delta   out, M floats
+ *   sigma   out, r doubles, descending
+ *   V_out   out, M x r floats, orthonormal Ritz vectors (columns defined up
+ *           to sign); may alias V_prev.
+ * No allocation; the workspace of `h` is reused. */
+wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g,
+                      const float* V_prev, float* delta, double* sigma, float* V_out,
+                      wssr_stream_t stream);
+
+/* Cold start of the first step (the paper uses LMSVD there, Algorithm 2):
+ * orthonormalise the caller's seeded block V_rand (M x r), run m_init
+ * subspace iterations and a Rayleigh-Ritz finish. V_out may alias V_rand.
+ * sigma (r doubles) may be NULL. */
+wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const float* V_rand,
+                               float* V_out, double* sigma, wssr_stream_t stream);
+
+/* ---- The individual passes of the step (same context, same workspace). ---- */
+
+/* Pass A (Algorithm 1, product with O^ transposed): Y = O_c X for an M x r
+ * block X (floats; cast to options.dtype before the product), Y N x r floats.
+ * Centring uses the exact identity O_c X = O X - 1 (1^T O X) / N. */
+wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X, float* Y,
+                         wssr_stream_t stream);
+
+/* Pass B (Algorithm 1, product with O^): Z = O_c^T Y for an N x r block Y
+ * (floats; cast to options.dtype), Z M x r floats. The column mean mu is
+ * accumulated in the same pass: Z = O^T Y - mu (1^T Y). */
+wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y, float* Z,
+                          wssr_stream_t stream);
+
+/* Orthonormalise an L x r float block in place by Cholesky QR, `passes`
+ * times (1 or 2; 2 = CholeskyQR2). L must be N or M of the context.
+ * Section 4.2's orth(.); Fukaya et al. 2014 for CholeskyQR2. */
+wssr_status wssr_orthonormalize(wssr_handle h, float* X, int64_t L, int32_t passes,
+                                wssr_stream_t stream);
+
+/* The Eq. (updated_sr_1) apply alone: delta from orthonormal V (M x r floats),
+ * sigma (r doubles) and g (M floats), with the context's lambda/apply mode. */
+wssr_status wssr_woodbury(wssr_handle h, const float* V, const double* sigma, const float* g,
+                          float* delta, wssr_stream_t stream);
+
+/* Wait for `h`'s last stream and return (then clear) the sticky device
+ * status; also surfaces asynchronous CUDA errors as WSSR_ERR_CUDA. */
+wssr_status wssr_sync(wssr_handle h);
+
+/* Read the sticky device status after the caller synchronised the stream. */
+wssr_status wssr_get_status(wssr_handle h);
+
+/* Number of kernel launches enqueued by the last wssr_step/wssr_init_subspace. */
+int64_t wssr_last_launch_count(wssr_handle h);
+
+/* ---- Per-kernel timing with CUDA events on the launching stream. ---- */
+/* Kernel categories: the O-pass products (the dominant kernels), the
+ * Cholesky-QR work, the Rayleigh-Ritz work, the Woodbury apply. */
+enum {
+  WSSR_KCAT_PASS_A = 0, /* Y = O X product kernel (pass A) */
+  WSSR_KCAT_PASS_B = 1, /* Z = O^T Y product kernel (pass B) */
+  WSSR_KCAT_ORTH = 2,   /* Gram, factor and apply kernels of Cholesky QR, casts, centring */
+  WSSR_KCAT_RR = 3,     /* Rayleigh-Ritz Gram, Jacobi, rotations */
+  WSSR_KCAT_APPLY = 4,  /* V^T g and the Woodbury apply */
+  WSSR_KCAT_COUNT = 5
+};
+
+/* Start recording an event pair around every kernel group enqueued on `h`
+ * from now on (adds two cudaEventRecord per group; no host sync). */
+wssr_status wssr_profile_begin(wssr_handle h);
+
+/* Stop recording, synchronise the recorded events and write, per category
+ * (ncat entries, ncat <= WSSR_KCAT_COUNT), the summed device milliseconds
+ * and the number of kernel launches. Either output may be NULL. */
+wssr_status wssr_profile_end(wssr_handle h, double* ms, int64_t* launches, int32_t ncat);
+
+/* Free the workspace (synchronises the device first). NULL is ignored. */
+void wssr_destroy(wssr_handle h);
+
+const char* wssr_status_string(wssr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WSSR_H_ */

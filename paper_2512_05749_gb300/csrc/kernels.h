@@ -1,0 +1,76 @@
+// Internal launch wrappers of the WSSR kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wssr {
+
+// ---- O passes, SIMT engine (simt_passes.cu) ----
+template <typename T>
+void launch_passA_simt(const void* O, int64_t ldo, int64_t N, int64_t M, const void* X, int r,
+                       int splits, float* Yp, cudaStream_t st);
+template <typename T>
+void launch_passB_simt(const void* O, int64_t ldo, int64_t N, int64_t M, const void* Y, int r,
+                       const double* ysum, float* Z, float* mu_out, cudaStream_t st);
+int passA_simt_splits(int64_t N, int64_t M, int r, int num_sms);
+int passA_simt_effective_splits(int64_t M, int splits);
+
+// ---- O passes, tcgen05 engine (tc_passes.cu) ----
+struct TcPassA;  // opaque plan objects live in tc_passes.cu
+bool tc_supported(int dev);
+int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* XhatT,
+                    int64_t ldx, int r, float* Yp, int* part_rows, int max_parts, int num_sms,
+                    int64_t wait_cap, int* status, cudaStream_t st, int* nparts_out);
+int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT,
+                    int64_t ldy, int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
+                    int num_sms, int64_t wait_cap, int* status, cudaStream_t st);
+
+// ---- small / tall-skinny kernels (small_ops.cu) ----
+// Y[n, :] = sum_s Yp[s][n, :] and per-block FP64 column sums.
+void launch_reduce_splits(const float* Yp, int nsplit, int64_t N, int r, float* Y, double* csum_part,
+                          int64_t* nblocks_out, cudaStream_t st);
+// Y[n, :] -= mean (mean = sum_b csum_part[b] / N)
+void launch_centre(float* Y, int64_t N, int r, const double* csum_part, int64_t nblocks,
+                   double* mean_out, cudaStream_t st);
+// G (r x r FP64, full) = X^T X (X: L x r FP32). part: workspace of gram_part_elems(L, r) doubles.
+int64_t gram_part_elems(int64_t L, int r);
+void launch_gram(const float* X, int64_t L, int r, double* part, double* G, double scale,
+                 cudaStream_t st);
+// Cholesky of the equilibrated Gram + inverse factor: T = R^-1 (FP32 r x r, upper).
+void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
+                     cudaStream_t st);
+size_t chol_inv_smem(int r);
+// Xo = X T (L x r times r x r), optional bf16 copies (row-major L x r, transposed r x ldT)
+// and FP64 column-sum partials of the bf16/f32 operand values written.
+void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
+                  int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
+                  int64_t* nblocks_out, cudaStream_t st);
+void launch_colsum_finalize(const double* part, int64_t nblocks, int r, double* out,
+                            cudaStream_t st);
+// Cast an L x r float block to the operand type (row-major copy and/or transposed bf16).
+// colsum_part (optional): FP64 column sums of the cast values per 64-row block.
+void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf16, void* out_T,
+                 int64_t ldT, double* colsum_part, cudaStream_t st);
+// Symmetric eigensolve of H (FP64 r x r) by FP32 cyclic Jacobi on one CTA.
+// Writes the rotation log and eigenvalues; launch_jacobi_vectors builds the sorted W.
+size_t jacobi_smem(int r);
+int64_t jacobi_log_elems(int r, int max_sweeps);
+void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
+                   float* evals, int* status, cudaStream_t st);
+void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
+                           float* W, cudaStream_t st);
+// c = V^T g (FP64), M x r V.
+int64_t dot_part_elems(int64_t M, int r);
+void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, double* c,
+                cudaStream_t st);
+// sigma_i = sqrt(Hp_ii) from the FP64 Gram of the rotated block; d_i; e_i = d_i c_i
+void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t st);
+void launch_woodbury_coeffs(const double* sigma, const double* c, int r, double lam, int mode,
+                            double sigma_floor, double* e, int* status, cudaStream_t st);
+void launch_woodbury(const float* V, const float* g, const double* e, int64_t M, int r,
+                     double lam_eff, float* delta, cudaStream_t st);
+// finite check of a float array: sets WSSR_ERR_NONFINITE
+void launch_check_finite(const float* x, int64_t n, int* status, cudaStream_t st);
+
+}  // namespace wssr

@@ -1,0 +1,720 @@
+// Tall-skinny and r x r kernels of the WSSR step:
+//   - split-K reduction and sample-mean centring of Y = O X (Eq. (Osr));
+//   - Gram matrices X^T X accumulated in FP64 across tiles;
+//   - Cholesky QR (Section 4.2's orth): FP64 equilibration of the Gram,
+//     Cholesky and inverse factor on one CTA, then the tall apply X T;
+//   - the Rayleigh-Ritz eigensolve (cyclic Jacobi, one CTA, rotation log
+//     replayed by a multi-CTA kernel to form the eigenvectors);
+//   - the Woodbury apply of Eq. (updated_sr_1).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace wssr {
+
+// ---------------------------------------------------------------------------
+// Split-K reduction and centring
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int RED_ROWS = 64;
+
+__global__ void k_reduce_splits(const float* __restrict__ Yp, int nsplit, int64_t N, int r,
+                                float* __restrict__ Y, double* __restrict__ csum_part) {
+  const int j = threadIdx.x;
+  const int64_t nb = (int64_t)blockIdx.x * RED_ROWS;
+  if (j >= r) return;
+  double cs = 0.0;
+  for (int i = 0; i < RED_ROWS; ++i) {
+    const int64_t n = nb + i;
+    if (n >= N) break;
+    float y = 0.f;
+    for (int s = 0; s < nsplit; ++s) y += Yp[((int64_t)s * N + n) * r + j];
+    Y[n * r + j] = y;
+    cs += (double)y;
+  }
+  csum_part[(int64_t)blockIdx.x * r + j] = cs;
+}
+
+__global__ void k_colsum_finalize(const double* __restrict__ part, int64_t nblocks, int r,
+                                  double scale, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= r) return;
+  double s = 0.0;
+  for (int64_t b = 0; b < nblocks; ++b) s += part[b * r + j];
+  out[j] = s * scale;
+}
+
+__global__ void k_subtract_mean(float* __restrict__ Y, int64_t N, int r,
+                                const double* __restrict__ mean) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * r) return;
+  const int j = (int)(e % r);
+  Y[e] = (float)((double)Y[e] - mean[j]);
+}
+}  // namespace
+
+void launch_reduce_splits(const float* Yp, int nsplit, int64_t N, int r, float* Y, double* csum_part,
+                          int64_t* nblocks_out, cudaStream_t st) {
+  const int64_t nb = ceil_div(N, RED_ROWS);
+  k_reduce_splits<<<(unsigned)nb, 256, 0, st>>>(Yp, nsplit, N, r, Y, csum_part);
+  *nblocks_out = nb;
+}
+
+void launch_colsum_finalize(const double* part, int64_t nblocks, int r, double* out,
+                            cudaStream_t st) {
+  k_colsum_finalize<<<1, 256, 0, st>>>(part, nblocks, r, 1.0, out);
+}
+
+void launch_centre(float* Y, int64_t N, int r, const double* csum_part, int64_t nblocks,
+                   double* mean_out, cudaStream_t st) {
+  k_colsum_finalize<<<1, 256, 0, st>>>(csum_part, nblocks, r, 1.0 / (double)N, mean_out);
+  const int64_t tot = N * r;
+  k_subtract_mean<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Y, N, r, mean_out);
+}
+
+// ---------------------------------------------------------------------------
+// Gram G = scale * X^T X, FP32 tile products flushed to FP64 every 256 rows
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int GT = 64;          // output tile
+constexpr int GK = 32;          // rows per smem stage
+constexpr int GFLUSH = 256;     // rows per FP32 partial
+
+int gram_nb(int64_t L) {
+  int64_t nb = ceil_div(L, 512);
+  if (nb > 96) nb = 96;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, int64_t L, int r,
+                                                   int64_t chunk, double* __restrict__ part) {
+  __shared__ __align__(16) float Xi[GK][GT];
+  __shared__ __align__(16) float Xj[GK][GT];
+  // tile pair (ti <= tj) from blockIdx.y
+  const int T = (r + GT - 1) / GT;
+  int p = blockIdx.y, ti = 0;
+  while (p >= T - ti) { p -= T - ti; ++ti; }
+  const int tj = ti + p;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t rb = (int64_t)blockIdx.x * chunk;
+  const int64_t re = rb + chunk < L ? rb + chunk : L;
+  float a32[4][4];
+  double a64[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) a32[a][b] = 0.f, a64[a][b] = 0.0;
+  int64_t since = 0;
+  for (int64_t k0 = rb; k0 < re; k0 += GK) {
+    for (int e = tid; e < GK * GT; e += 256) {
+      const int row = e / GT, col = e % GT;
+      const int64_t n = k0 + row;
+      const int ci = ti * GT + col, cj = tj * GT + col;
+      Xi[row][col] = (n < re && ci < r) ? X[n * r + ci] : 0.f;
+      Xj[row][col] = (n < re && cj < r) ? X[n * r + cj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      float4 u = *reinterpret_cast<const float4*>(&Xi[kk][ty * 4]);
+      float4 v = *reinterpret_cast<const float4*>(&Xj[kk][tx * 4]);
+      float ua[4] = {u.x, u.y, u.z, u.w}, va[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) a32[a][b] = fmaf(ua[a], va[b], a32[a][b]);
+    }
+    __syncthreads();
+    since += GK;
+    if (since >= GFLUSH) {
+      since = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) a64[a][b] += (double)a32[a][b], a32[a][b] = 0.f;
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * r * r;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = ti * GT + ty * 4 + a;
+    if (i >= r) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = tj * GT + tx * 4 + b;
+      if (j < r) out[(int64_t)i * r + j] = a64[a][b] + (double)a32[a][b];
+    }
+  }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int nb, int r, double scale,
+                              double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * r) return;
+  const int i = e / r, j = e % r;
+  // partials exist for (i, j) with tile(i) <= tile(j)
+  const int si = (i / GT <= j / GT) ? i : j, sj = (i / GT <= j / GT) ? j : i;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * r * r + (int64_t)si * r + sj];
+  G[e] = s * scale;
+}
+}  // namespace
+
+int64_t gram_part_elems(int64_t L, int r) { return (int64_t)gram_nb(L) * r * r; }
+
+void launch_gram(const float* X, int64_t L, int r, double* part, double* G, double scale,
+                 cudaStream_t st) {
+  const int nb = gram_nb(L);
+  const int64_t chunk = ceil_div(ceil_div(L, nb), GK) * GK;
+  const int nbe = (int)ceil_div(L, chunk);
+  const int T = (r + GT - 1) / GT;
+  dim3 grid((unsigned)nbe, (unsigned)(T * (T + 1) / 2));
+  k_gram_part<<<grid, 256, 0, st>>>(X, L, r, chunk, part);
+  k_gram_reduce<<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(part, nbe, r, scale, G);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky QR factor: T = R^-1 with G = R^T R. One CTA of 1024 threads.
+// FP64 equilibration D = diag(G)^-1/2, FP32 Cholesky of D G D in packed
+// upper storage, in-place inverse, T = D R'^-1.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ int pidx(int i, int j, int r) {  // i <= j
+  return i * r - (i * (i - 1)) / 2 + (j - i);
+}
+
+__global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int r,
+                                                   float* __restrict__ T, int* status,
+                                                   int* shift_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* d = reinterpret_cast<double*>(smem_raw);
+  float* A = reinterpret_cast<float*>(smem_raw + sizeof(double) * 256);
+  __shared__ int flag;
+  __shared__ float tmp[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  if (tid < r) {
+    const double gii = G[(int64_t)tid * r + tid];
+    if (!isfinite(gii)) flag = 2;
+    else if (!(gii > 0.0)) flag = 1;
+    d[tid] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
+  }
+  __syncthreads();
+  if (flag) {
+    if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
+    return;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const float shift = attempt ? 1e-5f : 0.f;
+    for (int e = tid; e < r * r; e += 1024) {
+      const int i = e / r, j = e % r;
+      if (i <= j) {
+        const double g = G[e];
+        if (!isfinite(g)) flag = 2;
+        A[pidx(i, j, r)] = (float)(g * d[i] * d[j]) + (i == j ? shift : 0.f);
+      }
+    }
+    __syncthreads();
+    if (flag == 2) break;
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+      const float piv = A[pidx(k, k, r)];
+      if (!(piv > 1e-8f)) {  // uniform: every thread read the same value
+        if (tid == 0) flag = 1;
+        break;
+      }
+      const float rho = sqrtf(piv), inv = 1.f / rho;
+      __syncthreads();
+      for (int j = k + tid; j < r; j += 1024) A[pidx(k, j, r)] = (j == k) ? rho : A[pidx(k, j, r)] * inv;
+      __syncthreads();
+      for (int i = k + 1 + warp; i < r; i += 32) {
+        const float aki = A[pidx(k, i, r)];
+        for (int j = i + lane; j < r; j += 32) A[pidx(i, j, r)] -= aki * A[pidx(k, j, r)];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (flag == 0) break;
+    if (flag == 1 && attempt == 0) {
+      if (tid == 0 && shift_count) atomicAdd(shift_count, 1);
+      __syncthreads();
+    }
+  }
+  if (flag) {
+    if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
+    return;
+  }
+  // In-place inverse of the upper-triangular factor, one row at a time from
+  // the bottom: X[i][j] = (delta_ij - sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i].
+  // Four threads share each column j (r <= 256 columns, 1024 threads).
+  const int jcol = tid >> 2, q = tid & 3;
+  for (int i = r - 1; i >= 0; --i) {
+    float s = 0.f;
+    if (jcol < r && jcol > i) {
+      for (int k = i + 1 + q; k <= jcol; k += 4) s = fmaf(A[pidx(i, k, r)], A[pidx(k, jcol, r)], s);
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (q == 0 && jcol < r && jcol >= i) tmp[jcol] = s;
+    __syncthreads();
+    if (tid < r && tid >= i) {
+      const float rii = A[pidx(i, i, r)];
+      A[pidx(i, tid, r)] = (tid == i) ? 1.f / rii : -tmp[tid] / rii;
+    }
+    __syncthreads();
+  }
+  // T = D R'^-1 (rows scaled by d_i), full r x r with zeros below the diagonal.
+  for (int e = tid; e < r * r; e += 1024) {
+    const int i = e / r, j = e % r;
+    T[e] = (i <= j) ? (float)((double)A[pidx(i, j, r)] * d[i]) : 0.f;
+  }
+}
+}  // namespace
+
+size_t chol_inv_smem(int r) { return sizeof(double) * 256 + sizeof(float) * (size_t)r * (r + 1) / 2; }
+
+void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
+                     cudaStream_t st) {
+  const size_t sm = chol_inv_smem(r);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_chol_inv<<<1, 1024, sm, st>>>(G, r, T, status, shift_count);
+}
+
+// ---------------------------------------------------------------------------
+// Tall apply Xo = X T with optional low-precision copies and column sums
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int AM = 64, AN = 64, AK = 32;
+
+__global__ void __launch_bounds__(256) k_apply(const float* __restrict__ X, int64_t L, int r,
+                                               const float* __restrict__ T, float* __restrict__ Xo,
+                                               void* lp_row, int lp_bf16, bf16* __restrict__ outT,
+                                               int64_t ldT, double* __restrict__ colsum_part) {
+  __shared__ __align__(16) float As[AK][AM + 4];
+  __shared__ __align__(16) float Bs[AK][AN];
+  __shared__ float Cs[AN][AM + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.x * AM;
+  const int j0 = blockIdx.y * AN;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < r; k0 += AK) {
+    for (int e = tid; e < AM * AK; e += 256) {
+      const int row = e / AK, col = e % AK;
+      const int64_t m = m0 + row;
+      const int k = k0 + col;
+      As[col][row] = (m < L && k < r) ? X[m * r + k] : 0.f;
+    }
+    for (int e = tid; e < AK * AN; e += 256) {
+      const int row = e / AN, col = e % AN;
+      const int k = k0 + row, j = j0 + col;
+      Bs[row][col] = (k < r && j < r) ? T[(int64_t)k * r + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < AK; ++kk) {
+      float4 u = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      float ua[4] = {u.x, u.y, u.z, u.w}, va[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ua[a], va[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t m = m0 + ty * 4 + a;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx * 4 + b;
+      float v = acc[a][b];
+      const bool ok = (m < L && j < r);
+      if (ok) Xo[m * r + j] = v;
+      if (lp_bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+      if (ok && lp_row) {
+        if (lp_bf16) reinterpret_cast<bf16*>(lp_row)[m * r + j] = __float2bfloat16_rn(v);
+      }
+      Cs[tx * 4 + b][ty * 4 + a] = ok ? v : 0.f;
+    }
+  }
+  if (outT == nullptr && colsum_part == nullptr) return;
+  __syncthreads();
+  if (outT) {
+    for (int e = tid; e < AM * AN; e += 256) {
+      const int c = e / AM, rr = e % AM;
+      const int j = j0 + c;
+      const int64_t m = m0 + rr;
+      if (j < r && m < L) outT[(int64_t)j * ldT + m] = __float2bfloat16_rn(Cs[c][rr]);
+    }
+  }
+  if (colsum_part && tid < AN) {
+    const int j = j0 + tid;
+    if (j < r) {
+      double s = 0.0;
+      for (int rr = 0; rr < AM; ++rr) s += (double)Cs[tid][rr];
+      colsum_part[(int64_t)blockIdx.x * r + j] = s;
+    }
+  }
+}
+}  // namespace
+
+void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
+                  int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
+                  int64_t* nblocks_out, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(L, AM), (unsigned)ceil_div(r, AN));
+  k_apply<<<grid, 256, 0, st>>>(X, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T, ldT,
+                                colsum_part);
+  if (nblocks_out) *nblocks_out = ceil_div(L, AM);
+}
+
+// ---------------------------------------------------------------------------
+// Cast an L x r float block to bf16 (row-major and/or transposed r x ldT)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) k_cast(const float* __restrict__ X, int64_t L, int r, int to_bf16,
+                                              bf16* __restrict__ out_row, bf16* __restrict__ outT,
+                                              int64_t ldT, double* __restrict__ colsum_part) {
+  __shared__ float Cs[64][65];
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.x * 64;
+  const int j0 = blockIdx.y * 64;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int rr = e / 64, c = e % 64;
+    const int64_t m = m0 + rr;
+    const int j = j0 + c;
+    float v = (m < L && j < r) ? X[m * r + j] : 0.f;
+    if (to_bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+    if (m < L && j < r && out_row) out_row[m * r + j] = __float2bfloat16_rn(v);
+    Cs[c][rr] = v;
+  }
+  if (!outT && !colsum_part) return;
+  __syncthreads();
+  if (outT) {
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int c = e / 64, rr = e % 64;
+      const int64_t m = m0 + rr;
+      const int j = j0 + c;
+      if (m < L && j < r) outT[(int64_t)j * ldT + m] = __float2bfloat16_rn(Cs[c][rr]);
+    }
+  }
+  if (colsum_part && tid < 64) {
+    const int j = j0 + tid;
+    if (j < r) {
+      double s = 0.0;
+      for (int rr = 0; rr < 64; ++rr) s += (double)Cs[tid][rr];
+      colsum_part[(int64_t)blockIdx.x * r + j] = s;
+    }
+  }
+}
+}  // namespace
+
+void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf16, void* out_T,
+                 int64_t ldT, double* colsum_part, cudaStream_t st) {
+  if (!to_bf16 && !colsum_part) return;  // nothing to produce for the float engine
+  dim3 grid((unsigned)ceil_div(L, 64), (unsigned)ceil_div(r, 64));
+  k_cast<<<grid, 256, 0, st>>>(X, L, r, to_bf16, (bf16*)out_rowmajor, (bf16*)out_T, ldT, colsum_part);
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz eigensolve: cyclic Jacobi (round-robin parallel ordering)
+// on the symmetric r x r matrix H in FP32, one CTA; rotations are logged and
+// replayed onto the identity by k_jacobi_vectors.
+// Rotation convention: J = [[c, s], [-s, c]] on the (p, q) plane,
+// A <- J^T A J, W <- W J; t = tan(theta) zeroes a_pq (smaller root).
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ void rr_pair(int k, int i, int r, int& p, int& q) {
+  const int n1 = r - 1;
+  p = (i == 0) ? 0 : ((i + k - 1) % n1) + 1;
+  q = ((r - 2 - i + k) % n1) + 1;
+}
+
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
+                                                 float2* __restrict__ rot_log, int* nsweeps_out,
+                                                 float* __restrict__ evals, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* A = reinterpret_cast<float*>(smem_raw);
+  __shared__ float cs_c[128], cs_s[128], cs_t[128];
+  __shared__ int rot_round, rot_sweep, bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h = r / 2;
+  const float tol = 3e-7f;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int e = tid; e < r * r; e += 1024) {
+    const int i = e / r, j = e % r;
+    if (i <= j) {
+      const double v = H[e];
+      if (!isfinite(v)) bad = 1;
+      A[pidx(i, j, r)] = (float)v;
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) {
+      set_status(status, WSSR_ERR_NONFINITE);
+      *nsweeps_out = 0;
+    }
+    return;
+  }
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rot_sweep = 0;
+    __syncthreads();
+    for (int k = 0; k < r - 1; ++k) {
+      if (tid == 0) rot_round = 0;
+      __syncthreads();
+      if (tid < h) {
+        int p, q;
+        rr_pair(k, tid, r, p, q);
+        const float app = A[pidx(p, p, r)], aqq = A[pidx(q, q, r)];
+        const float apq = A[p < q ? pidx(p, q, r) : pidx(q, p, r)];
+        float c = 1.f, s = 0.f, t = 0.f;
+        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
+          const float tau = (aqq - app) / (2.f * apq);
+          t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+          rot_round = 1;  // benign race: every writer stores 1
+        }
+        cs_c[tid] = c;
+        cs_s[tid] = s;
+        cs_t[tid] = t;
+        rot_log[((int64_t)sweep * (r - 1) + k) * h + tid] = make_float2(c, s);
+      }
+      __syncthreads();
+      if (rot_round) {
+        for (int i1 = warp; i1 < h; i1 += 32) {
+          int p1, q1;
+          rr_pair(k, i1, r, p1, q1);
+          const float c1 = cs_c[i1], s1 = cs_s[i1];
+          for (int i2 = i1 + lane; i2 < h; i2 += 32) {
+            if (i2 == i1) {
+              const float t1 = cs_t[i1];
+              const int ipq = p1 < q1 ? pidx(p1, q1, r) : pidx(q1, p1, r);
+              const float apq = A[ipq];
+              A[pidx(p1, p1, r)] -= t1 * apq;
+              A[pidx(q1, q1, r)] += t1 * apq;
+              A[ipq] = 0.f;
+            } else {
+              int p2, q2;
+              rr_pair(k, i2, r, p2, q2);
+              const float c2 = cs_c[i2], s2 = cs_s[i2];
+              const int i_pp = p1 < p2 ? pidx(p1, p2, r) : pidx(p2, p1, r);
+              const int i_pq = p1 < q2 ? pidx(p1, q2, r) : pidx(q2, p1, r);
+              const int i_qp = q1 < p2 ? pidx(q1, p2, r) : pidx(p2, q1, r);
+              const int i_qq = q1 < q2 ? pidx(q1, q2, r) : pidx(q2, q1, r);
+              const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
+              // B J2 (columns p2, q2)
+              const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
+              const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
+              // J1^T (rows p1, q1)
+              A[i_pp] = c1 * xpp - s1 * xqp;
+              A[i_qp] = s1 * xpp + c1 * xqp;
+              A[i_pq] = c1 * xpq - s1 * xqq;
+              A[i_qq] = s1 * xpq + c1 * xqq;
+            }
+          }
+        }
+        if (tid == 0) rot_sweep = 1;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!rot_sweep) {
+      ++sweep;  // this sweep did no rotation; keep its (identity) log
+      break;
+    }
+  }
+  if (tid == 0) *nsweeps_out = sweep;
+  for (int i = tid; i < r; i += 1024) evals[i] = A[pidx(i, i, r)];
+}
+
+// Replays the logged rotations on rows of the identity (4 rows per CTA),
+// then writes W with columns sorted by descending eigenvalue.
+__global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* __restrict__ nsweeps,
+                                 const float* __restrict__ evals, int r, float* __restrict__ W) {
+  __shared__ float Wr[4][256];
+  __shared__ int rank_of[256];
+  const int tid = threadIdx.x;
+  const int h = r / 2;
+  const int row_l = tid / h, pi = tid % h;  // blockDim = 4 * h
+  const int row = blockIdx.x * 4 + row_l;
+  for (int e = tid; e < 4 * r; e += blockDim.x) {
+    const int rl = e / r, c = e % r;
+    Wr[rl][c] = (blockIdx.x * 4 + rl == c) ? 1.f : 0.f;
+  }
+  for (int i = tid; i < r; i += blockDim.x) {
+    const float li = evals[i];
+    int rk = 0;
+    for (int j = 0; j < r; ++j) {
+      const float lj = evals[j];
+      rk += (lj > li) || (lj == li && j < i);
+    }
+    rank_of[i] = rk;
+  }
+  __syncthreads();
+  const int total = nsweeps[0] * (r - 1);
+  for (int t = 0; t < total; ++t) {
+    const int k = t % (r - 1);
+    int p, q;
+    rr_pair(k, pi, r, p, q);
+    const float2 cs = rot_log[(int64_t)t * h + pi];
+    if (cs.y != 0.f) {
+      const float wp = Wr[row_l][p], wq = Wr[row_l][q];
+      Wr[row_l][p] = cs.x * wp - cs.y * wq;
+      Wr[row_l][q] = cs.y * wp + cs.x * wq;
+    }
+    __syncthreads();
+  }
+  if (row < r) {
+    for (int c = pi; c < r; c += h) W[(int64_t)row * r + rank_of[c]] = Wr[row_l][c];
+  }
+}
+}  // namespace
+
+size_t jacobi_smem(int r) { return sizeof(float) * (size_t)r * (r + 1) / 2; }
+int64_t jacobi_log_elems(int r, int max_sweeps) { return (int64_t)max_sweeps * (r - 1) * (r / 2); }
+
+void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
+                   float* evals, int* status, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_jacobi<<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals,
+                                            status);
+}
+
+void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
+                           float* W, cudaStream_t st) {
+  k_jacobi_vectors<<<(unsigned)ceil_div(r, 4), 4 * (r / 2), 0, st>>>((const float2*)rot_log, nsweeps,
+                                                                     evals, r, W);
+}
+
+// ---------------------------------------------------------------------------
+// c = V^T g, sigma from the FP64 Rayleigh quotients, Woodbury apply
+// ---------------------------------------------------------------------------
+namespace {
+int dot_nb(int64_t M) {
+  int64_t nb = ceil_div(M, 2048);
+  if (nb > 512) nb = 512;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+__global__ void k_dot_part(const float* __restrict__ V, const float* __restrict__ g, int64_t M, int r,
+                           int64_t chunk, double* __restrict__ part) {
+  const int j = threadIdx.x;
+  if (j >= r) return;
+  const int64_t mb = (int64_t)blockIdx.x * chunk;
+  const int64_t me = mb + chunk < M ? mb + chunk : M;
+  double s64 = 0.0;
+  float s32 = 0.f;
+  int cnt = 0;
+  for (int64_t m = mb; m < me; ++m) {
+    s32 = fmaf(V[m * r + j], g[m], s32);
+    if (++cnt == 64) {
+      s64 += (double)s32;
+      s32 = 0.f;
+      cnt = 0;
+    }
+  }
+  part[(int64_t)blockIdx.x * r + j] = s64 + (double)s32;
+}
+
+__global__ void k_finalize_sigma(const double* __restrict__ Hp, int r, double* __restrict__ sigma) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r) return;
+  const double v = Hp[(int64_t)i * r + i];
+  sigma[i] = v > 0.0 ? sqrt(v) : 0.0;
+}
+
+__global__ void k_woodbury_coeffs(const double* __restrict__ sigma, const double* __restrict__ c,
+                                  int r, double lam, int mode, double floor_, double* __restrict__ e,
+                                  int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r) return;
+  const double s2 = sigma[i] * sigma[i];
+  double d;
+  if (mode == WSSR_APPLY_CUTOFF) {
+    d = (s2 > 0.0) ? 1.0 / s2 - 1.0 / floor_ : 0.0;
+  } else {
+    d = -s2 / (lam * (s2 + lam));
+  }
+  const double v = d * c[i];
+  if (!isfinite(v)) set_status(status, WSSR_ERR_NONFINITE);
+  e[i] = v;
+}
+
+__global__ void __launch_bounds__(256) k_woodbury(const float* __restrict__ V, const float* __restrict__ g,
+                                                  const double* __restrict__ e, int64_t M, int r,
+                                                  float inv_lam, float* __restrict__ delta) {
+  __shared__ float es[256];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) es[i] = (float)e[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t m = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (m >= M) return;
+  float s = 0.f;
+  for (int j = lane; j < r; j += 32) s = fmaf(V[m * r + j], es[j], s);
+  s = warp_sum(s);
+  if (lane == 0) delta[m] = fmaf(g[m], inv_lam, s);
+}
+
+__global__ void k_check_finite(const float* __restrict__ x, int64_t n, int* status) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(status, WSSR_ERR_NONFINITE);
+}
+}  // namespace
+
+int64_t dot_part_elems(int64_t M, int r) { return (int64_t)dot_nb(M) * r; }
+
+void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, double* c,
+                cudaStream_t st) {
+  const int nb = dot_nb(M);
+  const int64_t chunk = ceil_div(M, nb);
+  const int nbe = (int)ceil_div(M, chunk);
+  k_dot_part<<<nbe, 256, 0, st>>>(V, g, M, r, chunk, part);
+  k_colsum_finalize<<<1, 256, 0, st>>>(part, nbe, r, 1.0, c);
+}
+
+void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t st) {
+  k_finalize_sigma<<<1, 256, 0, st>>>(Hp, r, sigma);
+}
+
+void launch_woodbury_coeffs(const double* sigma, const double* c, int r, double lam, int mode,
+                            double sigma_floor, double* e, int* status, cudaStream_t st) {
+  k_woodbury_coeffs<<<1, 256, 0, st>>>(sigma, c, r, lam, mode, sigma_floor, e, status);
+}
+
+void launch_woodbury(const float* V, const float* g, const double* e, int64_t M, int r,
+                     double lam_eff, float* delta, cudaStream_t st) {
+  k_woodbury<<<(unsigned)ceil_div(M, 8), 256, 0, st>>>(V, g, e, M, r, (float)(1.0 / lam_eff), delta);
+}
+
+void launch_check_finite(const float* x, int64_t n, int* status, cudaStream_t st) {
+  int64_t blocks = ceil_div(n, 256 * 8);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_check_finite<<<(unsigned)blocks, 256, 0, st>>>(x, n, status);
+}
+
+}  // namespace wssr

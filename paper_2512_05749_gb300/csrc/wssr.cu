@@ -1,0 +1,557 @@
+// Host orchestration and C ABI of the WSSR step library.
+//
+// One wssr_step enqueues, on the caller's stream and without any host
+// synchronisation (Section 4.2, Algorithm 1, warm-started; Section 4.1,
+// Eq. (updated_sr_1)):
+//   repeat m times:
+//     pass A   Y = O_c X                (X = current subspace, operand precision)
+//     orth(Y)  one Cholesky QR pass     (keeps the next product well conditioned)
+//     pass B   Z = O_c^T Y              (column mean mu accumulated in-pass)
+//     orth(Z)  CholeskyQR2              -> V (FP32) and its operand copy
+//   Rayleigh-Ritz: Y = O_c V, H = Y^T Y / N (FP64), Jacobi H = W L W^T,
+//     V_out = V W, sigma_i^2 = FP64 Rayleigh quotients of Y W
+//   apply:  c = V_out^T g, delta = g / lam + V_out (d * c)
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace wssr;
+
+struct wssr_ctx {
+  int64_t N = 0, M = 0;
+  int r = 0;
+  double lam = 0;
+  wssr_options opt{};
+  int dev = 0, num_sms = 0;
+  bool use_tc = false;
+  cudaStream_t last_stream = nullptr;
+  int64_t launches = 0;
+
+  int* status = nullptr;       // [0] sticky status, [1] shift count
+  float* Yp = nullptr;         // pass A partials
+  int64_t yp_elems = 0;
+  int splits_simt = 1;
+  int* tc_part_rows = nullptr; // tc pass A partial -> row-block map
+  int tc_max_parts = 0;
+  float* Y = nullptr;
+  float* Y2 = nullptr;
+  double* csum_part = nullptr; // per-block column sums (N or M blocks of 64)
+  double* mean_r = nullptr;
+  double* ysum = nullptr;
+  float* Z = nullptr;
+  float* V = nullptr;
+  float* V2 = nullptr;
+  void* Xhat = nullptr;        // pass A operand copy (bf16)
+  void* Yhat = nullptr;        // pass B operand copy (bf16)
+  float* mu = nullptr;
+  double* gram_part = nullptr;
+  double* G = nullptr;
+  float* T = nullptr;
+  float* rot_log = nullptr;
+  int* nsweeps = nullptr;
+  float* evals = nullptr;
+  float* W = nullptr;
+  double* Hp = nullptr;
+  double* c = nullptr;
+  double* e = nullptr;
+  double* dot_part = nullptr;
+
+  // profiling: event pairs around kernel groups
+  bool prof = false;
+  struct Mark {
+    int cat;
+    int nlaunch;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+
+bool is_bf16(const wssr_ctx* h) { return h->opt.dtype == WSSR_DTYPE_BF16; }
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes < 256 ? 256 : bytes);
+}
+
+void free_all(wssr_ctx* h) {
+  void* ptrs[] = {h->status, h->Yp, h->tc_part_rows, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
+                  h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
+                  h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+wssr_status check_launch(wssr_ctx* h) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
+cudaEvent_t pool_event(wssr_ctx* h) {
+  if (h->pool_used == h->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->pool.push_back(e);
+  }
+  return h->pool[h->pool_used++];
+}
+
+// RAII timer around a kernel group of category `cat` (no-op unless profiling).
+struct Timed {
+  wssr_ctx* h;
+  int cat;
+  int64_t l0;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Timed(wssr_ctx* h_, int cat_, cudaStream_t st_) : h(h_), cat(cat_), l0(h_->launches), st(st_) {
+    if (h->prof && (a = pool_event(h))) cudaEventRecord(a, st);
+  }
+  ~Timed() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(h);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    h->marks.push_back({cat, (int)(h->launches - l0), a, b});
+  }
+};
+
+// ---- pass A: Y (N x r, centred) = O_c X; X is the float block, cast as needed ----
+wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const float* X, bool x_cast_ready, float* Y,
+                   cudaStream_t st) {
+  const int64_t N = h->N, M = h->M;
+  const int r = h->r;
+  if (h->use_tc) {
+    if (!x_cast_ready) {
+      launch_cast(X, M, r, nullptr, 1, h->Xhat, M, nullptr, st);
+      h->launches++;
+    }
+    int nparts = 0;
+    int rc;
+    {
+    Timed tm(h, WSSR_KCAT_PASS_A, st);
+    rc = tc_passA_launch(op->O, op->ld, N, M, h->Xhat, M, r, h->Yp, h->tc_part_rows,
+                             h->tc_max_parts, h->num_sms, h->opt.wait_cap, h->status, st, &nparts);
+    h->launches++;
+    }
+    if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+    int64_t nb = 0;
+    launch_reduce_splits(h->Yp, nparts, N, r, Y, h->csum_part, &nb, st);
+    h->launches++;
+    launch_centre(Y, N, r, h->csum_part, nb, h->mean_r, st);
+    h->launches += 2;
+  } else {
+    const void* Xop = X;
+    if (is_bf16(h)) {
+      if (!x_cast_ready) {
+        launch_cast(X, M, r, h->Xhat, 1, nullptr, 0, nullptr, st);
+        h->launches++;
+      }
+      Xop = h->Xhat;
+    }
+    {
+      Timed tm(h, WSSR_KCAT_PASS_A, st);
+      if (is_bf16(h)) launch_passA_simt<bf16>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
+      else launch_passA_simt<float>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
+      h->launches++;
+    }
+    int64_t nb = 0;
+    launch_reduce_splits(h->Yp, passA_simt_effective_splits(M, h->splits_simt), N, r, Y,
+                         h->csum_part, &nb, st);
+    h->launches++;
+    launch_centre(Y, N, r, h->csum_part, nb, h->mean_r, st);
+    h->launches += 2;
+  }
+  return check_launch(h);
+}
+
+// ---- pass B: Z (M x r) = O_c^T Yop where Yop is the operand copy and ysum its column sums ----
+wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float* Z,
+                   cudaStream_t st) {
+  const int64_t N = h->N, M = h->M;
+  const int r = h->r;
+  Timed tm(h, WSSR_KCAT_PASS_B, st);
+  if (h->use_tc) {
+    int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, N, r, h->ysum, Z, h->mu, 1, h->num_sms,
+                             h->opt.wait_cap, h->status, st);
+    if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+  } else if (is_bf16(h)) {
+    launch_passB_simt<bf16>(op->O, op->ld, N, M, Yop, r, h->ysum, Z, h->mu, st);
+  } else {
+    launch_passB_simt<float>(op->O, op->ld, N, M, Yop, r, h->ysum, Z, h->mu, st);
+  }
+  h->launches++;
+  return check_launch(h);
+}
+
+// One Cholesky QR pass: Xo = X R^-1 with optional operand copies / column sums.
+void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row, void* lpT,
+                 double* colsum_part, int64_t* nb_out, cudaStream_t st) {
+  const int r = h->r;
+  Timed tm(h, WSSR_KCAT_ORTH, st);
+  launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
+  launch_chol_inv(h->G, r, h->T, h->status, h->status + 1, st);
+  launch_apply(X, L, r, h->T, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, L, colsum_part, nb_out, st);
+  h->launches += 4;
+}
+
+// Orthonormalise Y in place-ish (result in h->Y2) and produce the pass B operand.
+const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
+  const int64_t N = h->N;
+  int64_t nb = 0;
+  void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
+  void* lpT = h->use_tc ? h->Yhat : nullptr;
+  cholqr_pass(h, Y, N, h->Y2, lp_row, lpT, h->csum_part, &nb, st);
+  launch_colsum_finalize(h->csum_part, nb, h->r, h->ysum, st);
+  h->launches++;
+  if (h->use_tc || is_bf16(h)) return h->Yhat;
+  return h->Y2;
+}
+
+// CholeskyQR2 of Z (M x r) -> h->V, plus the pass A operand copy of V.
+void orth_Z(wssr_ctx* h, cudaStream_t st) {
+  const int64_t M = h->M;
+  cholqr_pass(h, h->Z, M, h->V2, nullptr, nullptr, nullptr, nullptr, st);
+  void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Xhat : nullptr;
+  void* lpT = h->use_tc ? h->Xhat : nullptr;
+  cholqr_pass(h, h->V2, M, h->V, lp_row, lpT, nullptr, nullptr, st);
+}
+
+// Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
+wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, int m, float* V_out,
+                   double* sigma, cudaStream_t st) {
+  const int64_t N = h->N, M = h->M;
+  const int r = h->r;
+  const float* X = V_start;
+  bool ready = false;
+  wssr_status s;
+  for (int it = 0; it < m; ++it) {
+    if ((s = pass_A(h, op, X, ready, h->Y, st)) != WSSR_OK) return s;
+    const void* Yop = orth_Y_and_operand(h, h->Y, st);
+    if ((s = pass_B(h, op, Yop, h->Z, st)) != WSSR_OK) return s;
+    orth_Z(h, st);
+    X = h->V;
+    ready = true;
+  }
+  // Rayleigh-Ritz on span(V)
+  if ((s = pass_A(h, op, X, ready, h->Y, st)) != WSSR_OK) return s;
+  Timed tm(h, WSSR_KCAT_RR, st);
+  launch_gram(h->Y, N, r, h->gram_part, h->G, 1.0 / (double)N, st);
+  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
+  launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->W, st);
+  launch_apply(X, M, r, h->W, V_out, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  launch_apply(h->Y, N, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  launch_gram(h->Y2, N, r, h->gram_part, h->Hp, 1.0 / (double)N, st);
+  h->launches += 2 + 1 + 1 + 1 + 1 + 2;
+  double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
+  launch_finalize_sigma(h->Hp, r, sig, st);
+  h->launches++;
+  return check_launch(h);
+}
+
+wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const float* g, float* delta,
+                     cudaStream_t st) {
+  const int r = h->r;
+  Timed tm(h, WSSR_KCAT_APPLY, st);
+  launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
+  const double lam_eff = (h->opt.apply_mode == WSSR_APPLY_CUTOFF) ? h->opt.sigma_floor : h->lam;
+  launch_woodbury_coeffs(sigma, h->c, r, h->lam, h->opt.apply_mode, h->opt.sigma_floor, h->e,
+                         h->status, st);
+  launch_woodbury(V, g, h->e, h->M, r, lam_eff, delta, st);
+  h->launches += 4;
+  return check_launch(h);
+}
+
+wssr_status check_op(const wssr_ctx* h, const wssr_operator* op) {
+  if (!op || op->kind != WSSR_OP_DENSE || !op->O || op->ld < h->M) return WSSR_ERR_INVALID_ARG;
+  if (h->use_tc) {
+    const size_t esz = 2;
+    if (((uintptr_t)op->O) % 16 != 0 || ((size_t)op->ld * esz) % 16 != 0) return WSSR_ERR_INVALID_ARG;
+  }
+  return WSSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void wssr_default_options(wssr_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->m = 2;
+  opt->m_init = 20;
+  opt->dtype = WSSR_DTYPE_F32;
+  opt->apply_mode = WSSR_APPLY_DAMPED;
+  opt->sigma_floor = 0.0;
+  opt->wait_cap = (int64_t)1 << 26;
+  opt->engine = WSSR_ENGINE_AUTO;
+  opt->jacobi_sweeps = 12;
+}
+
+wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const wssr_options* opt_in,
+                        wssr_handle* out) {
+  if (!out) return WSSR_ERR_INVALID_ARG;
+  *out = nullptr;
+  wssr_options opt;
+  if (opt_in) opt = *opt_in;
+  else wssr_default_options(&opt);
+  if (N < 2 || M < 1 || r < 8 || r > 256 || r % 8 != 0 || r > N - 1 || r > M) return WSSR_ERR_INVALID_ARG;
+  if (!(lambda > 0.0)) return WSSR_ERR_INVALID_ARG;
+  if (opt.m < 1 || opt.m_init < 1 || opt.jacobi_sweeps < 1 || opt.jacobi_sweeps > 64) return WSSR_ERR_INVALID_ARG;
+  if (opt.dtype != WSSR_DTYPE_F32 && opt.dtype != WSSR_DTYPE_BF16) return WSSR_ERR_INVALID_ARG;
+  if (opt.apply_mode != WSSR_APPLY_DAMPED && opt.apply_mode != WSSR_APPLY_CUTOFF) return WSSR_ERR_INVALID_ARG;
+  if (opt.apply_mode == WSSR_APPLY_CUTOFF && !(opt.sigma_floor > 0.0)) return WSSR_ERR_INVALID_ARG;
+  if (opt.engine < WSSR_ENGINE_AUTO || opt.engine > WSSR_ENGINE_TCGEN05) return WSSR_ERR_INVALID_ARG;
+  if (opt.wait_cap < 1) return WSSR_ERR_INVALID_ARG;
+
+  wssr_ctx* h = new (std::nothrow) wssr_ctx();
+  if (!h) return WSSR_ERR_OOM;
+  h->N = N;
+  h->M = M;
+  h->r = r;
+  h->lam = lambda;
+  h->opt = opt;
+  if (cudaGetDevice(&h->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess) {
+    delete h;
+    return WSSR_ERR_CUDA;
+  }
+  const bool tc_ok = tc_supported(h->dev);
+  if (opt.engine == WSSR_ENGINE_TCGEN05) {
+    if (!tc_ok || opt.dtype != WSSR_DTYPE_BF16) {
+      delete h;
+      return WSSR_ERR_UNSUPPORTED;
+    }
+    h->use_tc = true;
+  } else if (opt.engine == WSSR_ENGINE_AUTO) {
+    h->use_tc = tc_ok && opt.dtype == WSSR_DTYPE_BF16;
+  }
+
+  const size_t f = sizeof(float), d = sizeof(double);
+  h->splits_simt = passA_simt_splits(N, M, r, h->num_sms);
+  int64_t parts = h->splits_simt;
+  if (h->use_tc) {
+    h->tc_max_parts = 4 * h->num_sms;
+    parts = std::max<int64_t>(parts, h->tc_max_parts);
+  }
+  // tc partials are 128-row tiles; SIMT partials cover all N rows per split
+  h->yp_elems = h->use_tc ? (int64_t)h->tc_max_parts * 128 * r : (int64_t)h->splits_simt * N * r;
+  const int64_t blocks64 = ceil_div(std::max(N, M), 64);
+  const int64_t gpart = std::max(gram_part_elems(N, r), gram_part_elems(M, r));
+  cudaError_t e = cudaSuccess;
+#define ALLOC(p, bytes) \
+  if (e == cudaSuccess) e = dalloc(&h->p, (bytes))
+  ALLOC(status, 2 * sizeof(int));
+  ALLOC(Yp, h->yp_elems * f);
+  ALLOC(tc_part_rows, (size_t)std::max(1, h->tc_max_parts) * sizeof(int));
+  ALLOC(Y, (size_t)N * r * f);
+  ALLOC(Y2, (size_t)N * r * f);
+  ALLOC(csum_part, (size_t)blocks64 * r * d);
+  ALLOC(mean_r, (size_t)r * d);
+  ALLOC(ysum, (size_t)r * d);
+  ALLOC(Z, (size_t)M * r * f);
+  ALLOC(V, (size_t)M * r * f);
+  ALLOC(V2, (size_t)M * r * f);
+  if (opt.dtype == WSSR_DTYPE_BF16) {
+    ALLOC(Xhat, (size_t)M * r * 2);
+    ALLOC(Yhat, (size_t)N * r * 2);
+  }
+  ALLOC(mu, (size_t)M * f);
+  ALLOC(gram_part, (size_t)gpart * d);
+  ALLOC(G, (size_t)r * r * d);
+  ALLOC(T, (size_t)r * r * f);
+  ALLOC(rot_log, (size_t)jacobi_log_elems(r, opt.jacobi_sweeps) * 2 * f);
+  ALLOC(nsweeps, sizeof(int));
+  ALLOC(evals, (size_t)r * f);
+  ALLOC(W, (size_t)r * r * f);
+  ALLOC(Hp, (size_t)r * r * d);
+  ALLOC(c, (size_t)r * d);
+  ALLOC(e, (size_t)r * d);
+  ALLOC(dot_part, (size_t)dot_part_elems(M, r) * d);
+#undef ALLOC
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? WSSR_ERR_OOM : WSSR_ERR_CUDA;
+  }
+  if (cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return WSSR_ERR_CUDA;
+  }
+  *out = h;
+  return WSSR_OK;
+}
+
+wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, const float* V_prev,
+                      float* delta, double* sigma, float* V_out, wssr_stream_t stream) {
+  if (!h || !g || !V_prev || !delta || !sigma || !V_out) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, st)) != WSSR_OK) return s;
+  return woodbury(h, V_out, sigma, g, delta, st);
+}
+
+wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const float* V_rand,
+                               float* V_out, double* sigma, wssr_stream_t stream) {
+  if (!h || !V_rand || !V_out) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  // orthonormalise the random block first (Cholesky QR twice), then iterate
+  cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, nullptr, nullptr, st);
+  cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, nullptr, nullptr, st);
+  return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, st);
+}
+
+wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X, float* Y,
+                         wssr_stream_t stream) {
+  if (!h || !X || !Y) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  return pass_A(h, op, X, false, Y, st);
+}
+
+wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y, float* Z,
+                          wssr_stream_t stream) {
+  if (!h || !Y || !Z) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  const int64_t N = h->N;
+  const int r = h->r;
+  const void* Yop = Y;
+  void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
+  void* lpT = h->use_tc ? h->Yhat : nullptr;
+  launch_cast(Y, N, r, lp_row, is_bf16(h) ? 1 : 0, lpT, N, h->csum_part, st);
+  launch_colsum_finalize(h->csum_part, ceil_div(N, 64), r, h->ysum, st);
+  h->launches += 2;
+  if (is_bf16(h)) Yop = h->Yhat;
+  return pass_B(h, op, Yop, Z, st);
+}
+
+wssr_status wssr_orthonormalize(wssr_handle h, float* X, int64_t L, int32_t passes,
+                                wssr_stream_t stream) {
+  if (!h || !X || (L != h->N && L != h->M) || passes < 1 || passes > 2) return WSSR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  float* tmp = (L == h->M) ? h->V2 : h->Y2;
+  cholqr_pass(h, X, L, tmp, nullptr, nullptr, nullptr, nullptr, st);
+  if (passes == 2) {
+    cholqr_pass(h, tmp, L, X, nullptr, nullptr, nullptr, nullptr, st);
+  } else {
+    if (cudaMemcpyAsync(X, tmp, (size_t)L * h->r * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return WSSR_ERR_CUDA;
+  }
+  return check_launch(h);
+}
+
+wssr_status wssr_woodbury(wssr_handle h, const float* V, const double* sigma, const float* g,
+                          float* delta, wssr_stream_t stream) {
+  if (!h || !V || !sigma || !g || !delta) return WSSR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  return woodbury(h, V, sigma, g, delta, st);
+}
+
+wssr_status wssr_get_status(wssr_handle h) {
+  if (!h) return WSSR_ERR_INVALID_ARG;
+  int s = 0;
+  if (cudaMemcpy(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WSSR_ERR_CUDA;
+  return (wssr_status)s;
+}
+
+wssr_status wssr_sync(wssr_handle h) {
+  if (!h) return WSSR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return WSSR_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return WSSR_ERR_CUDA;
+  int s = 0;
+  if (cudaMemcpy(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WSSR_ERR_CUDA;
+  if (s != 0 && cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) return WSSR_ERR_CUDA;
+  return (wssr_status)s;
+}
+
+int64_t wssr_last_launch_count(wssr_handle h) { return h ? h->launches : -1; }
+
+wssr_status wssr_profile_begin(wssr_handle h) {
+  if (!h) return WSSR_ERR_INVALID_ARG;
+  h->prof = true;
+  h->marks.clear();
+  h->pool_used = 0;
+  return WSSR_OK;
+}
+
+wssr_status wssr_profile_end(wssr_handle h, double* ms, int64_t* launches, int32_t ncat) {
+  if (!h || ncat < 0 || ncat > WSSR_KCAT_COUNT) return WSSR_ERR_INVALID_ARG;
+  h->prof = false;
+  for (int i = 0; i < ncat; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  wssr_status rc = WSSR_OK;
+  for (auto& mk : h->marks) {
+    if (cudaEventSynchronize(mk.b) != cudaSuccess) {
+      rc = WSSR_ERR_CUDA;
+      break;
+    }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, mk.a, mk.b) != cudaSuccess) {
+      rc = WSSR_ERR_CUDA;
+      break;
+    }
+    if (mk.cat < ncat) {
+      if (ms) ms[mk.cat] += t;
+      if (launches) launches[mk.cat] += mk.nlaunch;
+    }
+  }
+  h->marks.clear();
+  h->pool_used = 0;
+  return rc;
+}
+
+void wssr_destroy(wssr_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  free_all(h);
+  delete h;
+}
+
+const char* wssr_status_string(wssr_status s) {
+  switch (s) {
+    case WSSR_OK: return "ok";
+    case WSSR_ERR_INVALID_ARG: return "invalid argument";
+    case WSSR_ERR_OOM: return "out of device memory";
+    case WSSR_ERR_BREAKDOWN: return "Cholesky QR breakdown (rank-deficient block)";
+    case WSSR_ERR_NONFINITE: return "non-finite value";
+    case WSSR_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case WSSR_ERR_CUDA: return "CUDA runtime error";
+    case WSSR_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+"""Python binding of libwssr.so (include/wssr.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all
+arithmetic of the step runs in the library's CUDA kernels. Tensors are
+passed as device pointers (``tensor.data_ptr()``) together with the current
+CUDA stream. There is no CPU path: if the library cannot be loaded, the
+import of this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+WSSR_OK = 0
+WSSR_ERR_INVALID_ARG = 1
+WSSR_ERR_OOM = 2
+WSSR_ERR_BREAKDOWN = 3
+WSSR_ERR_NONFINITE = 4
+WSSR_ERR_DEVICE_TIMEOUT = 5
+WSSR_ERR_CUDA = 6
+WSSR_ERR_UNSUPPORTED = 7
+
+WSSR_DTYPE_F32 = 0
+WSSR_DTYPE_BF16 = 1
+WSSR_APPLY_DAMPED = 0
+WSSR_APPLY_CUTOFF = 1
+WSSR_OP_DENSE = 0
+WSSR_ENGINE_AUTO = 0
+WSSR_ENGINE_SIMT = 1
+WSSR_ENGINE_TCGEN05 = 2
+
+# every symbol include/wssr.h declares
+EXPORTED = [
+    "wssr_default_options", "wssr_create", "wssr_step", "wssr_init_subspace", "wssr_apply_O",
+    "wssr_apply_Ot", "wssr_orthonormalize", "wssr_woodbury", "wssr_sync", "wssr_get_status",
+    "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
+    "wssr_profile_end",
+]
+
+KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply"]
+
+
+class wssr_options(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int32),
+        ("m_init", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("apply_mode", ctypes.c_int32),
+        ("sigma_floor", ctypes.c_double),
+        ("wait_cap", ctypes.c_int64),
+        ("engine", ctypes.c_int32),
+        ("jacobi_sweeps", ctypes.c_int32),
+    ]
+
+
+class wssr_operator(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("O", ctypes.c_void_p),
+        ("ld", ctypes.c_int64),
+    ]
+
+
+class WSSRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "libwssr.so")
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libwssr.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libwssr.so not found at {path}; run paper_2512_05749_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "wssr_default_options": (None, [P(wssr_options)]),
+        "wssr_create": (i32, [i64, i64, i32, f64, P(wssr_options), P(vp)]),
+        "wssr_step": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp]),
+        "wssr_init_subspace": (i32, [vp, P(wssr_operator), vp, vp, vp, vp]),
+        "wssr_apply_O": (i32, [vp, P(wssr_operator), vp, vp, vp]),
+        "wssr_apply_Ot": (i32, [vp, P(wssr_operator), vp, vp, vp]),
+        "wssr_orthonormalize": (i32, [vp, vp, i64, i32, vp]),
+        "wssr_woodbury": (i32, [vp, vp, vp, vp, vp, vp]),
+        "wssr_sync": (i32, [vp]),
+        "wssr_get_status": (i32, [vp]),
+        "wssr_last_launch_count": (i64, [vp]),
+        "wssr_destroy": (None, [vp]),
+        "wssr_status_string": (ctypes.c_char_p, [i32]),
+        "wssr_profile_begin": (i32, [vp]),
+        "wssr_profile_end": (i32, [vp, P(f64), P(i64), i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().wssr_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != WSSR_OK:
+        raise WSSRError(code, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def wssr_default_options() -> wssr_options:
+    opt = wssr_options()
+    load().wssr_default_options(ctypes.byref(opt))
+    return opt
+
+
+def make_operator(O, ld: Optional[int] = None) -> wssr_operator:
+    """Describe a dense N x ld row-major O tensor (float32 or bfloat16)."""
+    op = wssr_operator()
+    op.kind = WSSR_OP_DENSE
+    op.O = _ptr(O)
+    op.ld = int(ld if ld is not None else O.stride(0))
+    return op
+
+
+def wssr_create(N: int, M: int, r: int, lam: float, opt: Optional[wssr_options] = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().wssr_create(N, M, r, lam, ctypes.byref(opt) if opt is not None else None,
+                              ctypes.byref(h)), "wssr_create")
+    return h.value
+
+
+def wssr_step(h: int, op: wssr_operator, g, V_prev, delta, sigma, V_out, stream=None):
+    _check(load().wssr_step(h, ctypes.byref(op), _ptr(g), _ptr(V_prev), _ptr(delta), _ptr(sigma),
+                            _ptr(V_out), _stream(stream)), "wssr_step")
+
+
+def wssr_init_subspace(h: int, op: wssr_operator, V_rand, V_out, sigma=None, stream=None):
+    _check(load().wssr_init_subspace(h, ctypes.byref(op), _ptr(V_rand), _ptr(V_out), _ptr(sigma),
+                                     _stream(stream)), "wssr_init_subspace")
+
+
+def wssr_apply_O(h: int, op: wssr_operator, X, Y, stream=None):
+    _check(load().wssr_apply_O(h, ctypes.byref(op), _ptr(X), _ptr(Y), _stream(stream)),
+           "wssr_apply_O")
+
+
+def wssr_apply_Ot(h: int, op: wssr_operator, Y, Z, stream=None):
+    _check(load().wssr_apply_Ot(h, ctypes.byref(op), _ptr(Y), _ptr(Z), _stream(stream)),
+           "wssr_apply_Ot")
+
+
+def wssr_orthonormalize(h: int, X, passes: int = 2, stream=None):
+    _check(load().wssr_orthonormalize(h, _ptr(X), X.shape[0], passes, _stream(stream)),
+           "wssr_orthonormalize")
+
+
+def wssr_woodbury(h: int, V, sigma, g, delta, stream=None):
+    _check(load().wssr_woodbury(h, _ptr(V), _ptr(sigma), _ptr(g), _ptr(delta), _stream(stream)),
+           "wssr_woodbury")
+
+
+def wssr_sync(h: int) -> int:
+    return int(load().wssr_sync(h))
+
+
+def wssr_get_status(h: int) -> int:
+    return int(load().wssr_get_status(h))
+
+
+def wssr_last_launch_count(h: int) -> int:
+    return int(load().wssr_last_launch_count(h))
+
+
+def wssr_profile_begin(h: int):
+    _check(load().wssr_profile_begin(h), "wssr_profile_begin")
+
+
+def wssr_profile_end(h: int):
+    """Returns {category: (ms, launches)} summed since wssr_profile_begin."""
+    n = len(KCAT_NAMES)
+    ms = (ctypes.c_double * n)()
+    la = (ctypes.c_int64 * n)()
+    _check(load().wssr_profile_end(h, ms, la, n), "wssr_profile_end")
+    return {KCAT_NAMES[i]: (ms[i], la[i]) for i in range(n)}
+
+
+def wssr_destroy(h: int):
+    if h:
+        load().wssr_destroy(h)
+
+
+class WSSR:
+    """Owns one library context; methods take torch CUDA tensors.
+
+    >>> s = WSSR(N, M, r, lam, dtype="bf16")
+    >>> delta, sigma, V = s.step(O, g, V_prev)
+    """
+
+    def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
+                 dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
+                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 1 << 26):
+        opt = wssr_default_options()
+        opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
+        opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]
+        opt.apply_mode = {"damped": WSSR_APPLY_DAMPED, "cutoff": WSSR_APPLY_CUTOFF}[apply_mode]
+        opt.sigma_floor = sigma_floor
+        opt.engine = {"auto": WSSR_ENGINE_AUTO, "simt": WSSR_ENGINE_SIMT,
+                      "tcgen05": WSSR_ENGINE_TCGEN05}[engine]
+        self.N, self.M, self.r, self.lam, self.dtype = N, M, r, lam, dtype
+        self.handle = wssr_create(N, M, r, lam, opt)
+
+    def close(self):
+        if self.handle:
+            wssr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _op(self, O):
+        import torch
+        want = torch.bfloat16 if self.dtype == "bf16" else torch.float32
+        if O.dtype != want or not O.is_cuda or O.stride(1) != 1 or O.shape[0] != self.N:
+            raise ValueError(f"O must be a CUDA {want} tensor of shape ({self.N}, >= {self.M}) "
+                             "with unit column stride")
+        return make_operator(O, O.stride(0))
+
+    def step(self, O, g, V_prev, out=None, stream=None):
+        import torch
+        dev = g.device
+        if out is None:
+            delta = torch.empty(self.M, device=dev, dtype=torch.float32)
+            sigma = torch.empty(self.r, device=dev, dtype=torch.float64)
+            V = torch.empty(self.M, self.r, device=dev, dtype=torch.float32)
+        else:
+            delta, sigma, V = out
+        wssr_step(self.handle, self._op(O), g, V_prev, delta, sigma, V, stream)
+        return delta, sigma, V
+
+    def init_subspace(self, O, V_rand, stream=None):
+        import torch
+        V = torch.empty(self.M, self.r, device=V_rand.device, dtype=torch.float32)
+        sigma = torch.empty(self.r, device=V_rand.device, dtype=torch.float64)
+        wssr_init_subspace(self.handle, self._op(O), V_rand, V, sigma, stream)
+        return V, sigma
+
+    def apply_O(self, O, X, stream=None):
+        import torch
+        Y = torch.empty(self.N, self.r, device=X.device, dtype=torch.float32)
+        wssr_apply_O(self.handle, self._op(O), X, Y, stream)
+        return Y
+
+    def apply_Ot(self, O, Y, stream=None):
+        import torch
+        Z = torch.empty(self.M, self.r, device=Y.device, dtype=torch.float32)
+        wssr_apply_Ot(self.handle, self._op(O), Y, Z, stream)
+        return Z
+
+    def orthonormalize(self, X, passes=2, stream=None):
+        wssr_orthonormalize(self.handle, X, passes, stream)
+        return X
+
+    def woodbury(self, V, sigma, g, stream=None):
+        import torch
+        delta = torch.empty(self.M, device=g.device, dtype=torch.float32)
+        wssr_woodbury(self.handle, V, sigma, g, delta, stream)
+        return delta
+
+    def sync(self) -> int:
+        return wssr_sync(self.handle)
+
+    def check(self, where="wssr"):
+        code = self.sync()
+        if code != WSSR_OK:
+            raise WSSRError(code, where)
+
+    def last_launch_count(self) -> int:
+        return wssr_last_launch_count(self.handle)
+
+    def profile_begin(self):
+        wssr_profile_begin(self.handle)
+
+    def profile_end(self):
+        return wssr_profile_end(self.handle)
