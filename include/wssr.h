@@ -149,6 +149,29 @@ wssr_status wssr_orthonormalize(wssr_handle h, float* X, int64_t L, int32_t pass
 wssr_status wssr_woodbury(wssr_handle h, const float* V, const double* sigma, const float* g,
                           float* delta, wssr_stream_t stream);
 
+/* The same apply as wssr_woodbury, for callers that cannot allocate device
+ * memory. The paper has no counterpart to this entry point; it exists for
+ * callers that run inside a host application which already owns all device
+ * memory (a caching allocator or a hard memory cap), or in latency-critical
+ * loops where cudaMalloc/cudaFree, which can synchronise the whole device,
+ * are not acceptable. It needs no handle and allocates nothing: its scratch
+ * (FP64 partial sums of V^T g and the r coefficients, 1,052,672 bytes) is a
+ * fixed device array inside the library, present on every GPU that loads it
+ * until the process exits.
+ *   V (M x r floats, orthonormal), sigma (r doubles), g (M floats), delta
+ *   (out, M floats): device pointers; lambda > 0; apply_mode WSSR_APPLY_*;
+ *   sigma_floor > 0 for WSSR_APPLY_CUTOFF.
+ * Limits: 1 <= r <= 256 and M >= 1 (larger r returns WSSR_ERR_INVALID_ARG,
+ * as do null pointers and bad modes). The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. All calls share
+ * the one array: calls whose kernels overlap on the GPU (other streams, other
+ * host threads) race and give wrong results. Non-finite inputs give a
+ * non-finite delta; no status word is kept. */
+wssr_status wssr_woodbury_noalloc(const float* V, const double* sigma, const float* g,
+                                  float* delta, int64_t M, int32_t r, double lambda,
+                                  int32_t apply_mode, double sigma_floor, wssr_stream_t stream);
+
 /* Wait for `h`'s last stream and return (then clear) the sticky device
  * status; also surfaces asynchronous CUDA errors as WSSR_ERR_CUDA. */
 wssr_status wssr_sync(wssr_handle h);

@@ -37,7 +37,7 @@ EXPORTED = [
     "wssr_default_options", "wssr_create", "wssr_step", "wssr_init_subspace", "wssr_apply_O",
     "wssr_apply_Ot", "wssr_orthonormalize", "wssr_woodbury", "wssr_sync", "wssr_get_status",
     "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
-    "wssr_profile_end",
+    "wssr_profile_end", "wssr_woodbury_noalloc",
 ]
 
 KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply"]
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_status_string": (ctypes.c_char_p, [i32]),
         "wssr_profile_begin": (i32, [vp]),
         "wssr_profile_end": (i32, [vp, P(f64), P(i64), i32]),
+        "wssr_woodbury_noalloc": (i32, [vp, vp, vp, vp, i64, i32, f64, i32, f64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,16 @@ def wssr_orthonormalize(h: int, X, passes: int = 2, stream=None):
 def wssr_woodbury(h: int, V, sigma, g, delta, stream=None):
     _check(load().wssr_woodbury(h, _ptr(V), _ptr(sigma), _ptr(g), _ptr(delta), _stream(stream)),
            "wssr_woodbury")
+
+
+def wssr_woodbury_noalloc(V, sigma, g, delta, lam: float, apply_mode: int = WSSR_APPLY_DAMPED,
+                          sigma_floor: float = 0.0, stream=None):
+    """The Woodbury apply without a handle and without any device allocation
+    (for callers that cannot call cudaMalloc); see include/wssr.h."""
+    M, r = V.shape
+    _check(load().wssr_woodbury_noalloc(_ptr(V), _ptr(sigma), _ptr(g), _ptr(delta), M, r, lam,
+                                        apply_mode, sigma_floor, _stream(stream)),
+           "wssr_woodbury_noalloc")
 
 
 def wssr_sync(h: int) -> int:
