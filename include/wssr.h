@@ -76,7 +76,8 @@ typedef struct {
   int32_t apply_mode;   /* WSSR_APPLY_* (default DAMPED) */
   double sigma_floor;   /* CUTOFF mode: the paper's sigma_floor, in S-eigenvalue
                            units (> 0); ignored for DAMPED */
-  int64_t wait_cap;     /* iteration cap of every device spin-wait (default 1<<26) */
+  int64_t wait_cap;     /* bound of every device wait, microseconds of GPU time (default 2000000);
+                           on expiry the kernel records WSSR_ERR_DEVICE_TIMEOUT and returns */
   int32_t engine;       /* WSSR_ENGINE_* (default AUTO) */
   int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
 } wssr_options;

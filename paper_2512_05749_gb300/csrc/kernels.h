@@ -17,14 +17,17 @@ int passA_simt_splits(int64_t N, int64_t M, int r, int num_sms);
 int passA_simt_effective_splits(int64_t M, int splits);
 
 // ---- O passes, tcgen05 engine (tc_passes.cu) ----
-struct TcPassA;  // opaque plan objects live in tc_passes.cu
+// Operand copies are transposed bf16 blocks: XhatT (r x ldx), YhatT (r x ldy),
+// ldx, ldy multiples of 8. Return 0 on success, < 0 if a tensor map could not
+// be encoded or the launch failed.
 bool tc_supported(int dev);
-int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* XhatT,
-                    int64_t ldx, int r, float* Yp, int* part_rows, int max_parts, int num_sms,
-                    int64_t wait_cap, int* status, cudaStream_t st, int* nparts_out);
-int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT,
-                    int64_t ldy, int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
-                    int num_sms, int64_t wait_cap, int* status, cudaStream_t st);
+int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms);
+int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* XhatT, int64_t ldx,
+                    int r, int splits, float* Yp, int64_t wait_us, int* status, cudaStream_t st,
+                    int* splits_used);
+int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
+                    int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
+                    int64_t wait_us, int* status, cudaStream_t st);
 
 // ---- small / tall-skinny kernels (small_ops.cu) ----
 // Y[n, :] = sum_s Yp[s][n, :] and per-block FP64 column sums.

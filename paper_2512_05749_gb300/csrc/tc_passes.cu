@@ -1,19 +1,572 @@
-// tcgen05 (Blackwell 5th-generation tensor core) engine of the two O passes.
+// tcgen05 (5th-generation tensor core) engine of the two O passes of the
+// WSSR step (Section 4.2, Algorithm 1's two products), for O stored in BF16.
+//
+//   pass A   Yp[split] (N x r) = O[:, K_split] Xhat^T[K_split, :]   (K = parameters)
+//   pass B   Z (M x r)         = O^T Yhat - mu (1^T Yhat)            (K = samples)
+//
+// One CTA = 6 warps:
+//   warp 0      TMA producer: 2D tiled bulk copies (128-byte swizzle) of O and
+//               of the operand block into a ring of shared-memory stages;
+//   warp 1      allocates TMEM, one elected thread issues tcgen05.mma
+//               (kind::f16, BF16 x BF16 -> FP32, M = 128, N = r rounded up to
+//               16) and tcgen05.commit to release stages;
+//   warps 2-5   epilogue: tcgen05.ld of the 128 x N accumulator (each warp its
+//               32-lane quarter), stores to global. In pass B they also sum the
+//               O tiles of every stage (the column mean mu) while the MMAs run.
+// Operand layouts in shared memory (canonical SW128 layouts of the MMA):
+//   pass A: A = O tile, 128 samples x 64 parameters, K-major;
+//           B = Xhat^T tile, N rows x 64 parameters, K-major.
+//   pass B: A = O tile, 64 samples x 128 parameters, MN-major (two 64-wide
+//           boxes, 8 KB apart); B = Yhat^T tile, N rows x 64 samples, K-major.
+// Every mbarrier wait is bounded by a global-timer deadline; on expiry the
+// kernel records WSSR_ERR_DEVICE_TIMEOUT, lets in-flight copies and MMAs
+// finish (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace wssr {
+namespace {
 
-bool tc_supported(int dev) { (void)dev; return false; }
+constexpr int BM = 128;       // accumulator rows = TMEM lanes
+constexpr int BK = 64;        // K per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int UK = 16;        // K per tcgen05.mma of kind::f16
+constexpr int THREADS = 192;
+constexpr int MAX_STAGES = 8;
+constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KB
 
-int tc_passA_launch(const void*, int64_t, int64_t, int64_t, const void*, int64_t, int, float*, int*,
-                    int, int, int64_t, int*, cudaStream_t, int*) {
-  return -1;
+struct Ctl {
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
+  uint64_t accum;
+  uint32_t tmem;
+  int abort;
+  float mu[BM];
+  float ysum[256];
+  double red[8][BM];
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns,
+                                       volatile int* abort_flag) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    if (mbar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t x[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+        "=r"(x[7]), "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]),
+        "=r"(x[14]), "=r"(x[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(x[i]);
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Barrier over the 128 epilogue threads that also ANDs a per-thread flag.
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, 1, 128, pi;\n"
+      " selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)v)
+      : "memory");
+  return out != 0;
 }
 
-int tc_passB_launch(const void*, int64_t, int64_t, int64_t, const void*, int64_t, int, const double*,
-                    float*, float*, int, int, int64_t, int*, cudaStream_t) {
-  return -1;
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (>> 4), version 1, 128-byte swizzle (layout type 2).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+__device__ __forceinline__ void timeout(Ctl* ctl, int* status) {
+  *(volatile int*)&ctl->abort = 1;
+  set_status(status, WSSR_ERR_DEVICE_TIMEOUT);
+}
+
+// Producer: TMA loads for iterations [0, nk). load(i, stage_ptr, bar).
+// On abort, waits (bounded) for the copies it issued so none lands after exit.
+template <typename LoadFn>
+__device__ __forceinline__ void producer(Ctl* ctl, uint8_t* base, uint32_t stage_bytes, int stages,
+                                         int nk, uint64_t limit_ns, int* status, LoadFn load) {
+  int issued = 0;
+  for (int i = 0; i < nk; ++i) {
+    const int s = i % stages, u = i / stages;
+    if (u > 0 && !mbar_wait(&ctl->empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
+      timeout(ctl, status);
+      break;
+    }
+    mbar_expect_tx(&ctl->full[s], stage_bytes);
+    load(i, base + (size_t)s * stage_bytes, &ctl->full[s]);
+    issued = i + 1;
+  }
+  if (ctl->abort) {
+    // let the copies already issued land before the CTA can exit
+    int no_abort = 0;
+    const int j0 = issued > stages ? issued - stages : 0;
+    for (int j = j0; j < issued; ++j)
+      mbar_wait(&ctl->full[j % stages], (j / stages) & 1, limit_ns, (volatile int*)&no_abort);
+  }
+}
+
+// MMA issuer: for each stage, BK/UK MMAs; commit releases the stage.
+__device__ __forceinline__ void mma_issuer(Ctl* ctl, uint8_t* base, uint32_t stage_bytes,
+                                           int stages, int nk, uint32_t tmem, uint32_t idesc,
+                                           bool a_mn, uint64_t limit_ns, int* status) {
+  for (int i = 0; i < nk; ++i) {
+    const int s = i % stages, u = i / stages;
+    if (!mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort)) {
+      timeout(ctl, status);
+      break;
+    }
+    tc_fence_after();
+    const uint32_t sa = saddr(base + (size_t)s * stage_bytes);
+    const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+    for (int kk = 0; kk < BK / UK; ++kk) {
+      // A: K-major advances 32 bytes per 16 K; MN-major advances two 8-row groups.
+      const uint64_t da = a_mn ? smem_desc(sa + kk * 2048, 8192, 1024) : smem_desc(sa + kk * 32, 16, 1024);
+      const uint64_t db = smem_desc(sb + kk * 32, 16, 1024);
+      mma_bf16(tmem, da, db, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+    }
+    mma_commit(&ctl->empty[s]);
+  }
+  // arrives when every MMA issued above has completed
+  mma_commit(&ctl->accum);
+  // keep TMEM alive until the accumulator is complete even on abort
+  int dummy = 0;
+  mbar_wait(&ctl->accum, 0, limit_ns, (volatile int*)&dummy);
+}
+
+// ---------------------------------------------------------------------------
+// Pass A
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_passA(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmX,
+               int64_t N, int r, int nmma, int tmem_cols, int stages, int k_chunks, int kc_per_split,
+               float* __restrict__ Yp, uint64_t limit_ns, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  const uint32_t stage_bytes = A_BYTES + (uint32_t)nmma * BK * 2;
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, split = blockIdx.y;
+  const int kc0 = split * kc_per_split;
+  const int kc1 = kc0 + kc_per_split < k_chunks ? kc0 + kc_per_split : k_chunks;
+  const int nk = kc1 - kc0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    mbar_init(&ctl->accum, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+
+  if (warp == 0) {
+    if (lane == 0 && nk > 0) {
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
+               [&](int i, uint8_t* st, uint64_t* bar) {
+                 const int k = (kc0 + i) * BK;
+                 tma_load_2d(st, &tmO, bar, k, n_tile * BM);
+                 tma_load_2d(st + A_BYTES, &tmX, bar, k, 0);
+               });
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nk > 0)
+      mma_issuer(ctl, base, stage_bytes, stages, nk, tmem, make_idesc(BM, nmma, 0, 0), false,
+                 limit_ns, status);
+  } else {
+    const int q = warp & 3;
+    const bool ok = nk > 0 && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
+    if (!ok && nk > 0) timeout(ctl, status);
+    tc_fence_after();
+    const int64_t n = (int64_t)n_tile * BM + q * 32 + lane;
+    float* out = Yp + ((int64_t)split * N + n) * r;
+    for (int c = 0; c < nmma; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+      if (nk == 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if ((ok || nk == 0) && n < N) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass B
+// ---------------------------------------------------------------------------
+template <bool WITH_MU>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
+               int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
+               const double* __restrict__ ysum, float* __restrict__ Z, float* __restrict__ mu_io,
+               uint64_t limit_ns, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  const uint32_t stage_bytes = A_BYTES + (uint32_t)nmma * BK * 2;
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int nk = (int)ceil_div(N, BK);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], WITH_MU ? 2 : 1);
+    }
+    mbar_init(&ctl->accum, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
+               [&](int i, uint8_t* st, uint64_t* bar) {
+                 const int n = i * BK;
+                 tma_load_2d(st, &tmO, bar, (int)m0, n);
+                 tma_load_2d(st + 8192, &tmO, bar, (int)m0 + 64, n);
+                 tma_load_2d(st + A_BYTES, &tmY, bar, n, 0);
+               });
+    }
+  } else if (warp == 1) {
+    if (lane == 0)
+      mma_issuer(ctl, base, stage_bytes, stages, nk, tmem, make_idesc(BM, nmma, 1, 0), true,
+                 limit_ns, status);
+  } else {
+    const int et = threadIdx.x - 64;  // 0..127
+    for (int j = et; j < r; j += 128) ctl->ysum[j] = (float)ysum[j];
+    if (WITH_MU) {
+      // Column sums of the O tiles: thread = (8 parameters, 8 samples of each stage).
+      const int pg = et & 15, sg = et >> 4;
+      const int box = pg >> 3, c = pg & 7;
+      float acc[8];
+      double acc64[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = 0.f, acc64[e] = 0.0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % stages, u = i / stages;
+        const bool got = mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort);
+        const uint8_t* sa = base + (size_t)s * stage_bytes + box * 8192;
+        if (got) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int row = sg * 8 + j;
+            const uint4 v = *reinterpret_cast<const uint4*>(sa + row * 128 + ((c ^ j) << 4));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              acc[2 * e] += __uint_as_float(w[e] << 16);
+              acc[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
+            }
+          }
+        }
+        // all 128 threads decide together, so the named barrier never misses arrivals
+        if (!epi_bar_and(got)) {
+          if (et == 0) timeout(ctl, status);
+          break;
+        }
+        if (et == 0) mbar_arrive(&ctl->empty[s]);
+        if ((i & 15) == 15) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc64[e] += (double)acc[e], acc[e] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) ctl->red[sg][pg * 8 + e] = acc64[e] + (double)acc[e];
+      epi_bar();
+      double sum = 0.0;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) sum += ctl->red[g][et];
+      const float mu = (float)(sum / (double)N);
+      ctl->mu[et] = mu;
+      if (m0 + et < M) mu_io[m0 + et] = mu;
+    }
+    epi_bar();
+    const int q = warp & 3;
+    const bool ok = mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
+    if (!ok) timeout(ctl, status);
+    tc_fence_after();
+    const int row = q * 32 + lane;
+    const int64_t m = m0 + row;
+    const float mu = WITH_MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
+    float* out = Z + m * r;
+    for (int c = 0; c < nmma; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+      if (ok && m < M) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          if (c + i < r)
+            *reinterpret_cast<float4*>(out + c + i) =
+                make_float4(v[i] - mu * ctl->ysum[c + i], v[i + 1] - mu * ctl->ysum[c + i + 1],
+                            v[i + 2] - mu * ctl->ysum[c + i + 2], v[i + 3] - mu * ctl->ysum[c + i + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D bf16 tensor map: inner x outer elements, row pitch in bytes, box in elements.
+bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+               uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(g), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int nmma_for(int r) { return (r + 15) / 16 * 16; }
+int tmem_cols_for(int nmma) {
+  int c = 32;
+  while (c < nmma) c <<= 1;
+  return c;
+}
+int stages_for(int nmma) {
+  const size_t stage = A_BYTES + (size_t)nmma * BK * 2;
+  const size_t avail = 227 * 1024 - 1024 - sizeof(Ctl);
+  size_t s = avail / stage;
+  if (s > MAX_STAGES) s = MAX_STAGES;
+  return (int)s;
+}
+size_t smem_for(int nmma, int stages) {
+  return 1024 + (size_t)stages * (A_BYTES + (size_t)nmma * BK * 2) + sizeof(Ctl);
+}
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+}  // namespace
+
+bool tc_supported(int dev) {
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms) {
+  const int64_t n_tiles = ceil_div(N, BM), k_chunks = ceil_div(M, BK);
+  int64_t S = num_sms / gcd64(n_tiles, num_sms);
+  while (n_tiles * S < 2 * num_sms) S *= 2;
+  int64_t cap = k_chunks / 8;
+  if (cap < 1) cap = 1;
+  if (S > cap) S = cap;
+  const int64_t mem_cap = (512LL << 20) / (N * r * 4);
+  if (S > mem_cap) S = mem_cap > 1 ? mem_cap : 1;
+  if (S > 4096) S = 4096;
+  return (int)S;
+}
+
+int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* XhatT, int64_t ldx,
+                    int r, int splits, float* Yp, int64_t wait_us, int* status, cudaStream_t st,
+                    int* splits_used) {
+  const int nmma = nmma_for(r);
+  const int stages = stages_for(nmma);
+  CUtensorMap tmO, tmX;
+  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, BM)) return -1;
+  if (!encode_2d(&tmX, XhatT, (uint64_t)M, (uint64_t)r, (uint64_t)ldx * 2, BK, (uint32_t)nmma)) return -1;
+  const int k_chunks = (int)ceil_div(M, BK);
+  const int kc_per_split = (int)ceil_div(k_chunks, splits);
+  const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
+  const size_t smem = smem_for(nmma, stages);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_passA, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)ceil_div(N, BM), (unsigned)s_eff);
+  k_tc_passA<<<grid, THREADS, smem, st>>>(tmO, tmX, N, r, nmma, tmem_cols_for(nmma), stages, k_chunks,
+                                          kc_per_split, Yp, (uint64_t)wait_us * 1000ull, status);
+  *splits_used = s_eff;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+}
+
+int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
+                    int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
+                    int64_t wait_us, int* status, cudaStream_t st) {
+  const int nmma = nmma_for(r);
+  const int stages = stages_for(nmma);
+  CUtensorMap tmO, tmY;
+  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, 64, BK)) return -1;
+  if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)nmma)) return -1;
+  const size_t smem = smem_for(nmma, stages);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_passB<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)ceil_div(M, BM));
+  if (compute_mu)
+    k_tc_passB<true><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
+                                                  ysum, Z, mu_io, (uint64_t)wait_us * 1000ull, status);
+  else
+    k_tc_passB<false><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
+                                                   ysum, Z, mu_io, (uint64_t)wait_us * 1000ull, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
 }  // namespace wssr

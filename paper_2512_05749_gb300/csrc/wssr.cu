@@ -38,8 +38,9 @@ struct wssr_ctx {
   float* Yp = nullptr;         // pass A partials
   int64_t yp_elems = 0;
   int splits_simt = 1;
-  int* tc_part_rows = nullptr; // tc pass A partial -> row-block map
-  int tc_max_parts = 0;
+  int splits_tc = 1;           // pass A splits of the tcgen05 engine
+  int64_t ldx = 0, ldy = 0;    // row pitch of the transposed bf16 operand copies
+  bool mu_valid = false;       // tcgen05 pass B: mu of the current O already in h->mu
   float* Y = nullptr;
   float* Y2 = nullptr;
   double* csum_part = nullptr; // per-block column sums (N or M blocks of 64)
@@ -85,7 +86,7 @@ cudaError_t dalloc(P** p, size_t bytes) {
 }
 
 void free_all(wssr_ctx* h) {
-  void* ptrs[] = {h->status, h->Yp, h->tc_part_rows, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
+  void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part};
   for (void* p : ptrs)
@@ -132,16 +133,16 @@ wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const float* X, bool x_
   const int r = h->r;
   if (h->use_tc) {
     if (!x_cast_ready) {
-      launch_cast(X, M, r, nullptr, 1, h->Xhat, M, nullptr, st);
+      launch_cast(X, M, r, nullptr, 1, h->Xhat, h->ldx, nullptr, st);
       h->launches++;
     }
     int nparts = 0;
     int rc;
     {
-    Timed tm(h, WSSR_KCAT_PASS_A, st);
-    rc = tc_passA_launch(op->O, op->ld, N, M, h->Xhat, M, r, h->Yp, h->tc_part_rows,
-                             h->tc_max_parts, h->num_sms, h->opt.wait_cap, h->status, st, &nparts);
-    h->launches++;
+      Timed tm(h, WSSR_KCAT_PASS_A, st);
+      rc = tc_passA_launch(op->O, op->ld, N, M, h->Xhat, h->ldx, r, h->splits_tc, h->Yp,
+                           h->opt.wait_cap, h->status, st, &nparts);
+      h->launches++;
     }
     if (rc != 0) return WSSR_ERR_UNSUPPORTED;
     int64_t nb = 0;
@@ -181,9 +182,10 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_PASS_B, st);
   if (h->use_tc) {
-    int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, N, r, h->ysum, Z, h->mu, 1, h->num_sms,
-                             h->opt.wait_cap, h->status, st);
+    int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Z, h->mu,
+                             h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st);
     if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+    h->mu_valid = true;
   } else if (is_bf16(h)) {
     launch_passB_simt<bf16>(op->O, op->ld, N, M, Yop, r, h->ysum, Z, h->mu, st);
   } else {
@@ -195,12 +197,12 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
 
 // One Cholesky QR pass: Xo = X R^-1 with optional operand copies / column sums.
 void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row, void* lpT,
-                 double* colsum_part, int64_t* nb_out, cudaStream_t st) {
+                 int64_t ldT, double* colsum_part, int64_t* nb_out, cudaStream_t st) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_ORTH, st);
   launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
   launch_chol_inv(h->G, r, h->T, h->status, h->status + 1, st);
-  launch_apply(X, L, r, h->T, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, L, colsum_part, nb_out, st);
+  launch_apply(X, L, r, h->T, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st);
   h->launches += 4;
 }
 
@@ -210,7 +212,7 @@ const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
   int64_t nb = 0;
   void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
   void* lpT = h->use_tc ? h->Yhat : nullptr;
-  cholqr_pass(h, Y, N, h->Y2, lp_row, lpT, h->csum_part, &nb, st);
+  cholqr_pass(h, Y, N, h->Y2, lp_row, lpT, h->ldy, h->csum_part, &nb, st);
   launch_colsum_finalize(h->csum_part, nb, h->r, h->ysum, st);
   h->launches++;
   if (h->use_tc || is_bf16(h)) return h->Yhat;
@@ -220,10 +222,10 @@ const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
 // CholeskyQR2 of Z (M x r) -> h->V, plus the pass A operand copy of V.
 void orth_Z(wssr_ctx* h, cudaStream_t st) {
   const int64_t M = h->M;
-  cholqr_pass(h, h->Z, M, h->V2, nullptr, nullptr, nullptr, nullptr, st);
+  cholqr_pass(h, h->Z, M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
   void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Xhat : nullptr;
   void* lpT = h->use_tc ? h->Xhat : nullptr;
-  cholqr_pass(h, h->V2, M, h->V, lp_row, lpT, nullptr, nullptr, st);
+  cholqr_pass(h, h->V2, M, h->V, lp_row, lpT, h->ldx, nullptr, nullptr, st);
 }
 
 // Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
@@ -292,7 +294,7 @@ void wssr_default_options(wssr_options* opt) {
   opt->dtype = WSSR_DTYPE_F32;
   opt->apply_mode = WSSR_APPLY_DAMPED;
   opt->sigma_floor = 0.0;
-  opt->wait_cap = (int64_t)1 << 26;
+  opt->wait_cap = 2000000;
   opt->engine = WSSR_ENGINE_AUTO;
   opt->jacobi_sweeps = 12;
 }
@@ -338,13 +340,11 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
 
   const size_t f = sizeof(float), d = sizeof(double);
   h->splits_simt = passA_simt_splits(N, M, r, h->num_sms);
-  int64_t parts = h->splits_simt;
-  if (h->use_tc) {
-    h->tc_max_parts = 4 * h->num_sms;
-    parts = std::max<int64_t>(parts, h->tc_max_parts);
-  }
-  // tc partials are 128-row tiles; SIMT partials cover all N rows per split
-  h->yp_elems = h->use_tc ? (int64_t)h->tc_max_parts * 128 * r : (int64_t)h->splits_simt * N * r;
+  h->splits_tc = h->use_tc ? tc_passA_splits(N, M, r, h->num_sms) : 1;
+  h->ldx = (M + 7) / 8 * 8;
+  h->ldy = (N + 7) / 8 * 8;
+  // pass A partials: one N x r block per split
+  h->yp_elems = (int64_t)(h->use_tc ? h->splits_tc : h->splits_simt) * N * r;
   const int64_t blocks64 = ceil_div(std::max(N, M), 64);
   const int64_t gpart = std::max(gram_part_elems(N, r), gram_part_elems(M, r));
   cudaError_t e = cudaSuccess;
@@ -352,7 +352,6 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (e == cudaSuccess) e = dalloc(&h->p, (bytes))
   ALLOC(status, 2 * sizeof(int));
   ALLOC(Yp, h->yp_elems * f);
-  ALLOC(tc_part_rows, (size_t)std::max(1, h->tc_max_parts) * sizeof(int));
   ALLOC(Y, (size_t)N * r * f);
   ALLOC(Y2, (size_t)N * r * f);
   ALLOC(csum_part, (size_t)blocks64 * r * d);
@@ -362,8 +361,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(V, (size_t)M * r * f);
   ALLOC(V2, (size_t)M * r * f);
   if (opt.dtype == WSSR_DTYPE_BF16) {
-    ALLOC(Xhat, (size_t)M * r * 2);
-    ALLOC(Yhat, (size_t)N * r * 2);
+    ALLOC(Xhat, (size_t)h->ldx * r * 2);
+    ALLOC(Yhat, (size_t)h->ldy * r * 2);
   }
   ALLOC(mu, (size_t)M * f);
   ALLOC(gram_part, (size_t)gpart * d);
@@ -401,6 +400,7 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
+  h->mu_valid = false;
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, st)) != WSSR_OK) return s;
   return woodbury(h, V_out, sigma, g, delta, st);
 }
@@ -414,8 +414,9 @@ wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const flo
   h->last_stream = st;
   h->launches = 0;
   // orthonormalise the random block first (Cholesky QR twice), then iterate
-  cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, nullptr, nullptr, st);
-  cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, nullptr, nullptr, st);
+  h->mu_valid = false;
+  cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
+  cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
   return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, st);
 }
 
@@ -443,7 +444,8 @@ wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y
   const void* Yop = Y;
   void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
   void* lpT = h->use_tc ? h->Yhat : nullptr;
-  launch_cast(Y, N, r, lp_row, is_bf16(h) ? 1 : 0, lpT, N, h->csum_part, st);
+  launch_cast(Y, N, r, lp_row, is_bf16(h) ? 1 : 0, lpT, h->ldy, h->csum_part, st);
+  h->mu_valid = false;
   launch_colsum_finalize(h->csum_part, ceil_div(N, 64), r, h->ysum, st);
   h->launches += 2;
   if (is_bf16(h)) Yop = h->Yhat;
@@ -457,9 +459,9 @@ wssr_status wssr_orthonormalize(wssr_handle h, float* X, int64_t L, int32_t pass
   h->last_stream = st;
   h->launches = 0;
   float* tmp = (L == h->M) ? h->V2 : h->Y2;
-  cholqr_pass(h, X, L, tmp, nullptr, nullptr, nullptr, nullptr, st);
+  cholqr_pass(h, X, L, tmp, nullptr, nullptr, 0, nullptr, nullptr, st);
   if (passes == 2) {
-    cholqr_pass(h, tmp, L, X, nullptr, nullptr, nullptr, nullptr, st);
+    cholqr_pass(h, tmp, L, X, nullptr, nullptr, 0, nullptr, nullptr, st);
   } else {
     if (cudaMemcpyAsync(X, tmp, (size_t)L * h->r * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)

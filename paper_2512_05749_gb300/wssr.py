@@ -241,7 +241,7 @@ class WSSR:
 
     def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
                  dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
-                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 1 << 26):
+                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000):
         opt = wssr_default_options()
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
         opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]

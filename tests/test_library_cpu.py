@@ -35,7 +35,7 @@ def test_options_layout_and_defaults():
     opt = W.wssr_default_options()
     assert (opt.m, opt.m_init, opt.dtype, opt.apply_mode, opt.engine, opt.jacobi_sweeps) == \
         (2, 20, W.WSSR_DTYPE_F32, W.WSSR_APPLY_DAMPED, W.WSSR_ENGINE_AUTO, 12)
-    assert opt.wait_cap == 1 << 26
+    assert opt.wait_cap == 2_000_000
 
 
 def test_status_strings():
