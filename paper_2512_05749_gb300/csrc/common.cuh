@@ -43,6 +43,16 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// K-blocked operand layout of a tall block X (L x r) in bf16: for every 64
+// consecutive rows of X (parameters), one contiguous block of r x 64
+// elements holding X^T restricted to those rows (row j of the block = column
+// j of X). A 64-parameter TMA box of all r columns is then one contiguous
+// r x 128-byte region instead of r rows one matrix pitch apart.
+__host__ __device__ __forceinline__ int64_t blk_index(int64_t m, int j, int r) {
+  return (((m >> 6) * r + j) << 6) + (m & 63);
+}
+__host__ __device__ __forceinline__ int64_t blk_elems(int64_t L, int r) { return ceil_div(L, 64) * 64 * r; }
+
 }  // namespace wssr
 
 // Host-side launch helpers (defined in wssr.cu).

@@ -17,17 +17,22 @@ int passA_simt_splits(int64_t N, int64_t M, int r, int num_sms);
 int passA_simt_effective_splits(int64_t M, int splits);
 
 // ---- O passes, tcgen05 engine (tc_passes.cu) ----
-// Operand copies are transposed bf16 blocks: XhatT (r x ldx), YhatT (r x ldy),
-// ldx, ldy multiples of 8. Return 0 on success, < 0 if a tensor map could not
-// be encoded or the launch failed.
+// The pass A operand Xhat and pass B's bf16 output are K-blocked (blk_index);
+// the pass B operand YhatT is transposed with row pitch ldy (multiple of 8).
+// Return 0 on success, < 0 if a tensor map could not be encoded or the launch failed.
 bool tc_supported(int dev);
 int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms);
 int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* XhatT, int64_t ldx,
                     int r, int splits, float* Yp, int64_t wait_us, int* status, cudaStream_t st,
                     int* splits_used);
+// Z (M x r floats) when ZT == nullptr, else the K-blocked bf16 block ZT.
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
-                    int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
-                    int64_t wait_us, int* status, cudaStream_t st);
+                    int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
+                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st);
+// FP32 partial Grams Gp[split] (r x r) of the K-blocked bf16 block XT (L rows).
+int tc_gram_splits(int64_t L, int num_sms);
+int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                   int* status, cudaStream_t st, int* splits_used);
 
 // ---- small / tall-skinny kernels (small_ops.cu) ----
 // Y[n, :] = sum_s Yp[s][n, :] and per-block FP64 column sums.
@@ -49,9 +54,20 @@ size_t chol_inv_smem(int r);
 void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
                   int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
                   int64_t* nblocks_out, cudaStream_t st);
+// Same with the tall block given as layout 0 = float row-major, 1 = bf16
+// row-major, 2 = bf16 K-blocked (blk_index).
+void launch_apply_any(const void* X, int layout, int64_t ldx, int64_t L, int r, const float* T,
+                      float* Xo, void* out_lp_rowmajor, int lp_is_bf16, void* out_bf16_T, int64_t ldT,
+                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st);
 void launch_colsum_finalize(const double* part, int64_t nblocks, int r, double* out,
                             cudaStream_t st);
-// Cast an L x r float block to the operand type (row-major copy and/or transposed bf16).
+// Gram of a float or bf16 row-major L x r block (FP64 result).
+void launch_gram_any(const void* X, int x_bf16, int64_t L, int r, double* part, double* G,
+                     double scale, cudaStream_t st);
+// G (FP64) = scale * sum_s Gp[s] for FP32 partial r x r matrices.
+void launch_sum_partials(const float* Gp, int S, int r, double scale, double* G, cudaStream_t st);
+// Cast an L x r float block to the operand type (row-major copy and/or a bf16
+// copy that is transposed with row pitch ldT, or K-blocked (blk_index) when ldT == 0).
 // colsum_part (optional): FP64 column sums of the cast values per 64-row block.
 void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf16, void* out_T,
                  int64_t ldT, double* colsum_part, cudaStream_t st);

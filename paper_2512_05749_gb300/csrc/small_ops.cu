@@ -88,7 +88,8 @@ int gram_nb(int64_t L) {
   return (int)nb;
 }
 
-__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, int64_t L, int r,
+template <typename TIn>
+__global__ void __launch_bounds__(256) k_gram_part(const TIn* __restrict__ X, int64_t L, int r,
                                                    int64_t chunk, double* __restrict__ part) {
   __shared__ __align__(16) float Xi[GK][GT];
   __shared__ __align__(16) float Xj[GK][GT];
@@ -112,8 +113,8 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
       const int row = e / GT, col = e % GT;
       const int64_t n = k0 + row;
       const int ci = ti * GT + col, cj = tj * GT + col;
-      Xi[row][col] = (n < re && ci < r) ? X[n * r + ci] : 0.f;
-      Xj[row][col] = (n < re && cj < r) ? X[n * r + cj] : 0.f;
+      Xi[row][col] = (n < re && ci < r) ? to_f32(X[n * r + ci]) : 0.f;
+      Xj[row][col] = (n < re && cj < r) ? to_f32(X[n * r + cj]) : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -164,15 +165,39 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int r, do
 
 int64_t gram_part_elems(int64_t L, int r) { return (int64_t)gram_nb(L) * r * r; }
 
-void launch_gram(const float* X, int64_t L, int r, double* part, double* G, double scale,
-                 cudaStream_t st) {
+void launch_gram_any(const void* X, int x_bf16, int64_t L, int r, double* part, double* G,
+                     double scale, cudaStream_t st) {
   const int nb = gram_nb(L);
   const int64_t chunk = ceil_div(ceil_div(L, nb), GK) * GK;
   const int nbe = (int)ceil_div(L, chunk);
   const int T = (r + GT - 1) / GT;
   dim3 grid((unsigned)nbe, (unsigned)(T * (T + 1) / 2));
-  k_gram_part<<<grid, 256, 0, st>>>(X, L, r, chunk, part);
+  if (x_bf16)
+    k_gram_part<bf16><<<grid, 256, 0, st>>>((const bf16*)X, L, r, chunk, part);
+  else
+    k_gram_part<float><<<grid, 256, 0, st>>>((const float*)X, L, r, chunk, part);
   k_gram_reduce<<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(part, nbe, r, scale, G);
+}
+
+void launch_gram(const float* X, int64_t L, int r, double* part, double* G, double scale,
+                 cudaStream_t st) {
+  launch_gram_any(X, 0, L, r, part, G, scale, st);
+}
+
+namespace {
+__global__ void k_sum_partials(const float* __restrict__ Gp, int S, int64_t n, double scale,
+                               double* __restrict__ G) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < S; ++k) s += (double)Gp[(int64_t)k * n + e];
+  G[e] = s * scale;
+}
+}  // namespace
+
+void launch_sum_partials(const float* Gp, int S, int r, double scale, double* G, cudaStream_t st) {
+  const int64_t n = (int64_t)r * r;
+  k_sum_partials<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(Gp, S, n, scale, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,7 +319,10 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
 namespace {
 constexpr int AM = 64, AN = 64, AK = 32;
 
-__global__ void __launch_bounds__(256) k_apply(const float* __restrict__ X, int64_t L, int r,
+// Input layouts of the tall block X: 0 = float row-major (L x r), 1 = bf16
+// row-major (L x r), 2 = bf16 K-blocked (blk_index).
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int64_t ldx, int64_t L, int r,
                                                const float* __restrict__ T, float* __restrict__ Xo,
                                                void* lp_row, int lp_bf16, bf16* __restrict__ outT,
                                                int64_t ldT, double* __restrict__ colsum_part) {
@@ -310,11 +338,25 @@ __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ X, int6
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   for (int k0 = 0; k0 < r; k0 += AK) {
-    for (int e = tid; e < AM * AK; e += 256) {
-      const int row = e / AK, col = e % AK;
-      const int64_t m = m0 + row;
-      const int k = k0 + col;
-      As[col][row] = (m < L && k < r) ? X[m * r + k] : 0.f;
+    if (LAYOUT == 2) {
+      const bf16* X = reinterpret_cast<const bf16*>(Xv);
+      for (int e = tid; e < AM * AK; e += 256) {
+        const int col = e / AM, row = e % AM;  // coalesced along the parameters
+        const int64_t m = m0 + row;
+        const int k = k0 + col;
+        As[col][row] = (m < L && k < r) ? __bfloat162float(X[blk_index(m, k, r)]) : 0.f;
+      }
+    } else {
+      for (int e = tid; e < AM * AK; e += 256) {
+        const int row = e / AK, col = e % AK;
+        const int64_t m = m0 + row;
+        const int k = k0 + col;
+        float v = 0.f;
+        if (m < L && k < r)
+          v = LAYOUT == 1 ? __bfloat162float(reinterpret_cast<const bf16*>(Xv)[m * r + k])
+                          : reinterpret_cast<const float*>(Xv)[m * r + k];
+        As[col][row] = v;
+      }
     }
     for (int e = tid; e < AK * AN; e += 256) {
       const int row = e / AN, col = e % AN;
@@ -371,13 +413,27 @@ __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ X, int6
 }
 }  // namespace
 
+void launch_apply_any(const void* X, int layout, int64_t ldx, int64_t L, int r, const float* T,
+                      float* Xo, void* out_lp_rowmajor, int lp_is_bf16, void* out_bf16_T, int64_t ldT,
+                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(L, AM), (unsigned)ceil_div(r, AN));
+  if (layout == 2)
+    k_apply<2><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
+                                     ldT, colsum_part);
+  else if (layout == 1)
+    k_apply<1><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
+                                     ldT, colsum_part);
+  else
+    k_apply<0><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
+                                     ldT, colsum_part);
+  if (nblocks_out) *nblocks_out = ceil_div(L, AM);
+}
+
 void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
                   int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
                   int64_t* nblocks_out, cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(L, AM), (unsigned)ceil_div(r, AN));
-  k_apply<<<grid, 256, 0, st>>>(X, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T, ldT,
-                                colsum_part);
-  if (nblocks_out) *nblocks_out = ceil_div(L, AM);
+  launch_apply_any(X, 0, r, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, out_bf16_T, ldT, colsum_part,
+                   nblocks_out, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,7 +463,8 @@ __global__ void __launch_bounds__(256) k_cast(const float* __restrict__ X, int64
       const int c = e / 64, rr = e % 64;
       const int64_t m = m0 + rr;
       const int j = j0 + c;
-      if (m < L && j < r) outT[(int64_t)j * ldT + m] = __float2bfloat16_rn(Cs[c][rr]);
+      if (m < L && j < r)
+        outT[ldT > 0 ? (int64_t)j * ldT + m : blk_index(m, j, r)] = __float2bfloat16_rn(Cs[c][rr]);
     }
   }
   if (colsum_part && tid < 64) {

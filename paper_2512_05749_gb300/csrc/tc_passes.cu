@@ -22,6 +22,8 @@
 // kernel records WSSR_ERR_DEVICE_TIMEOUT, lets in-flight copies and MMAs
 // finish (again bounded), frees its TMEM and returns.
 #include <cuda.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -101,6 +103,41 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
       : "memory");
+}
+// Same copy with an L2 eviction-priority policy (from createpolicy).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                                 int y, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(saddr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                                 int y, int z, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(saddr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)),
@@ -209,10 +246,11 @@ __device__ __forceinline__ void producer(Ctl* ctl, uint8_t* base, uint32_t stage
   }
 }
 
-// MMA issuer: for each stage, BK/UK MMAs; commit releases the stage.
-__device__ __forceinline__ void mma_issuer(Ctl* ctl, uint8_t* base, uint32_t stage_bytes,
-                                           int stages, int nk, uint32_t tmem, uint32_t idesc,
-                                           bool a_mn, uint64_t limit_ns, int* status) {
+// MMA issuer: issue(stage_saddr, first) enqueues the MMAs of one stage; the
+// commit after it releases the stage to the producer.
+template <typename IssueFn>
+__device__ __forceinline__ void mma_loop(Ctl* ctl, uint8_t* base, uint32_t stage_bytes, int stages,
+                                         int nk, uint64_t limit_ns, int* status, IssueFn issue) {
   for (int i = 0; i < nk; ++i) {
     const int s = i % stages, u = i / stages;
     if (!mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort)) {
@@ -220,40 +258,49 @@ __device__ __forceinline__ void mma_issuer(Ctl* ctl, uint8_t* base, uint32_t sta
       break;
     }
     tc_fence_after();
-    const uint32_t sa = saddr(base + (size_t)s * stage_bytes);
-    const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-    for (int kk = 0; kk < BK / UK; ++kk) {
-      // A: K-major advances 32 bytes per 16 K; MN-major advances two 8-row groups.
-      const uint64_t da = a_mn ? smem_desc(sa + kk * 2048, 8192, 1024) : smem_desc(sa + kk * 32, 16, 1024);
-      const uint64_t db = smem_desc(sb + kk * 32, 16, 1024);
-      mma_bf16(tmem, da, db, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-    }
+    issue(saddr(base + (size_t)s * stage_bytes), i == 0);
     mma_commit(&ctl->empty[s]);
   }
   // arrives when every MMA issued above has completed
   mma_commit(&ctl->accum);
   // keep TMEM alive until the accumulator is complete even on abort
-  int dummy = 0;
-  mbar_wait(&ctl->accum, 0, limit_ns, (volatile int*)&dummy);
+  int no_abort = 0;
+  mbar_wait(&ctl->accum, 0, limit_ns, (volatile int*)&no_abort);
 }
 
 // ---------------------------------------------------------------------------
 // Pass A
 // ---------------------------------------------------------------------------
+// Each stage holds KB consecutive 64-parameter blocks (KB boxes of O and of
+// the operand), so that every O row is read in KB x 128 contiguous bytes.
+// CTAs are rasterised in groups of `group` sample tiles: a group's tiles run
+// all their splits before the next group starts, which bounds the number of
+// distinct O rows (and pages) in flight.
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passA(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmX,
-               int64_t N, int r, int nmma, int tmem_cols, int stages, int k_chunks, int kc_per_split,
-               float* __restrict__ Yp, uint64_t limit_ns, int* status) {
+               int64_t N, int r, int nmma, int tmem_cols, int stages, int KB, int n_tiles, int splits,
+               int group, int k_chunks, int kc_per_split, int rotate, float* __restrict__ Yp,
+               uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  const uint32_t stage_bytes = A_BYTES + (uint32_t)nmma * BK * 2;
+  const uint32_t a_bytes = A_BYTES * KB;
+  const uint32_t xbox = (uint32_t)nmma * BK * 2;
+  const uint32_t stage_bytes = a_bytes + xbox * KB;
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, split = blockIdx.y;
+  // rasterisation: group of `group` sample tiles x all splits, tile index fastest
+  const int per_group = group * splits;
+  const int gidx = blockIdx.x / per_group, within = blockIdx.x % per_group;
+  const int gsize = (gidx + 1) * group <= n_tiles ? group : n_tiles - gidx * group;
+  const int n_tile = gidx * group + within % gsize;
+  const int split = within / gsize;
+  // k_chunks and kc_per_split count stages (KB blocks of 64 parameters)
   const int kc0 = split * kc_per_split;
   const int kc1 = kc0 + kc_per_split < k_chunks ? kc0 + kc_per_split : k_chunks;
   const int nk = kc1 - kc0;
+  // starting chunk of this tile within the split's range (spreads the
+  // concurrent requests of a wave over the row, see the launcher)
+  const int rot = (rotate && nk > 0) ? (int)(((int64_t)n_tile * 977) % nk) : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&ctl->full[s], 1);
@@ -271,17 +318,31 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0 && nk > 0) {
+      // O is streamed once; the operand slice is re-read by every sample tile
+      const uint64_t pol_o = policy_evict_first(), pol_x = policy_evict_last();
       producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
                [&](int i, uint8_t* st, uint64_t* bar) {
-                 const int k = (kc0 + i) * BK;
-                 tma_load_2d(st, &tmO, bar, k, n_tile * BM);
-                 tma_load_2d(st + A_BYTES, &tmX, bar, k, 0);
+                 int ii = i + rot;
+                 if (ii >= nk) ii -= nk;
+                 const int k = (kc0 + ii) * BK * KB;
+                 for (int b = 0; b < KB; ++b)
+                   tma_load_2d_hint(st + b * A_BYTES, &tmO, bar, k + b * BK, n_tile * BM, pol_o);
+                 for (int b = 0; b < KB; ++b)
+                   tma_load_3d_hint(st + a_bytes + b * xbox, &tmX, bar, 0, 0, (k + b * BK) / BK, pol_x);
                });
     }
   } else if (warp == 1) {
-    if (lane == 0 && nk > 0)
-      mma_issuer(ctl, base, stage_bytes, stages, nk, tmem, make_idesc(BM, nmma, 0, 0), false,
-                 limit_ns, status);
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc = make_idesc(BM, nmma, 0, 0);
+      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
+        for (int b = 0; b < KB; ++b)
+#pragma unroll
+          for (int kk = 0; kk < BK / UK; ++kk)
+            mma_bf16(tmem, smem_desc(sa + b * A_BYTES + kk * 32, 16, 1024),
+                     smem_desc(sa + a_bytes + b * xbox + kk * 32, 16, 1024), idesc,
+                     (!first || b > 0 || kk > 0) ? 1u : 0u);
+      });
+    }
   } else {
     const int q = warp & 3;
     const bool ok = nk > 0 && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
@@ -318,8 +379,8 @@ template <bool WITH_MU>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
                int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
-               const double* __restrict__ ysum, float* __restrict__ Z, float* __restrict__ mu_io,
-               uint64_t limit_ns, int* status) {
+               const double* __restrict__ ysum, float* __restrict__ Z, bf16* __restrict__ ZT,
+               int64_t ldz, float* __restrict__ mu_io, uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t stage_bytes = A_BYTES + (uint32_t)nmma * BK * 2;
@@ -344,18 +405,27 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      const uint64_t pol_o = policy_evict_first(), pol_y = policy_evict_last();
       producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
                [&](int i, uint8_t* st, uint64_t* bar) {
                  const int n = i * BK;
-                 tma_load_2d(st, &tmO, bar, (int)m0, n);
-                 tma_load_2d(st + 8192, &tmO, bar, (int)m0 + 64, n);
-                 tma_load_2d(st + A_BYTES, &tmY, bar, n, 0);
+                 tma_load_2d_hint(st, &tmO, bar, (int)m0, n, pol_o);
+                 tma_load_2d_hint(st + 8192, &tmO, bar, (int)m0 + 64, n, pol_o);
+                 tma_load_2d_hint(st + A_BYTES, &tmY, bar, n, 0, pol_y);
                });
     }
   } else if (warp == 1) {
-    if (lane == 0)
-      mma_issuer(ctl, base, stage_bytes, stages, nk, tmem, make_idesc(BM, nmma, 1, 0), true,
-                 limit_ns, status);
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, nmma, 1, 0);
+      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
+        // A is MN-major: 16 samples = two 8-row groups (SBO 1024), 64-parameter
+        // boxes 8 KB apart (LBO)
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk)
+          mma_bf16(tmem, smem_desc(sa + kk * 2048, 8192, 1024), smem_desc(sa + A_BYTES + kk * 32, 16, 1024),
+                   idesc, (!first || kk > 0) ? 1u : 0u);
+      });
+    }
   } else {
     const int et = threadIdx.x - 64;  // 0..127
     for (int j = et; j < r; j += 128) ctl->ysum[j] = (float)ysum[j];
@@ -413,17 +483,105 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int row = q * 32 + lane;
     const int64_t m = m0 + row;
     const float mu = WITH_MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
-    float* out = Z + m * r;
     for (int c = 0; c < nmma; c += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
       if (ok && m < M) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 4)
-          if (c + i < r)
-            *reinterpret_cast<float4*>(out + c + i) =
-                make_float4(v[i] - mu * ctl->ysum[c + i], v[i + 1] - mu * ctl->ysum[c + i + 1],
-                            v[i + 2] - mu * ctl->ysum[c + i + 2], v[i + 3] - mu * ctl->ysum[c + i + 3]);
+        for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 256 ? c + i : 255];
+        if (ZT) {
+          // K-blocked bf16 operand: for each column the warp writes 32
+          // consecutive parameters (64 contiguous bytes)
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c + i < r) ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(v[i]);
+        } else {
+          float* out = Z + m * r;
+#pragma unroll
+          for (int i = 0; i < 16; i += 4)
+            if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram of a transposed bf16 block: Gp[split] (r x r, FP32) = sum over the
+// split's parameter chunks of X^T X, with X^T given as r rows of bf16 (row
+// pitch ld). The same smem tile (rows x 64 parameters, K-major) is both
+// operands; rows = 128 (one accumulator) or 256 (two, TMEM columns 0 and 256).
+// Products of bf16 values are exact; accumulation is FP32 in TMEM.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gram(const __grid_constant__ CUtensorMap tmX, int r, int nmma, int rows, int tmem_cols,
+              int stages, int k_chunks, int kc_per_split, float* __restrict__ Gp, uint64_t limit_ns,
+              int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  const uint32_t stage_bytes = (uint32_t)rows * BK * 2;
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int split = blockIdx.x;
+  const int kc0 = split * kc_per_split;
+  const int kc1 = kc0 + kc_per_split < k_chunks ? kc0 + kc_per_split : k_chunks;
+  const int nk = kc1 - kc0;
+  const int MT = rows / BM;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    mbar_init(&ctl->accum, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+  if (warp == 0) {
+    if (lane == 0 && nk > 0)
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
+               [&](int i, uint8_t* st, uint64_t* bar) { tma_load_3d(st, &tmX, bar, 0, 0, kc0 + i); });
+  } else if (warp == 1) {
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc = make_idesc(BM, nmma, 0, 0);
+      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          const uint64_t db = smem_desc(sa + kk * 32, 16, 1024);
+          for (int a = 0; a < MT; ++a)
+            mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + a * 16384 + kk * 32, 16, 1024), db, idesc,
+                     (!first || kk > 0) ? 1u : 0u);
+        }
+      });
+    }
+  } else {
+    const int q = warp & 3;
+    const bool ok = nk > 0 && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
+    if (!ok && nk > 0) timeout(ctl, status);
+    tc_fence_after();
+    for (int a = 0; a < MT; ++a) {
+      const int i = a * BM + q * 32 + lane;
+      float* out = Gp + ((int64_t)split * r + i) * r;
+      for (int c = 0; c < nmma; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(a * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (i < r) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            if (c + j < r)
+              *reinterpret_cast<float4*>(out + c + j) =
+                  ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     }
   }
@@ -465,6 +623,20 @@ bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, ui
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(g), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3D bf16 tensor map of a K-blocked operand (blk_index): dims {64, r, blocks},
+// box {64, box_rows, 1}: one box = box_rows contiguous 128-byte rows.
+bool encode_blocked(CUtensorMap* m, const void* g, int64_t L, int r, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {64, (cuuint64_t)r, (cuuint64_t)ceil_div(L, 64)};
+  cuuint64_t strides[2] = {128, (cuuint64_t)r * 128};
+  cuuint32_t box[3] = {64, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(g), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -516,6 +688,10 @@ int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms) {
   if (S > cap) S = cap;
   const int64_t mem_cap = (512LL << 20) / (N * r * 4);
   if (S > mem_cap) S = mem_cap > 1 ? mem_cap : 1;
+  if (const char* env = getenv("WSSR_TUNE_PASSA_SPLITS")) {
+    const int v = atoi(env);
+    if (v >= 1) S = v < k_chunks ? v : k_chunks;
+  }
   if (S > 4096) S = 4096;
   return (int)S;
 }
@@ -524,29 +700,47 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
                     int r, int splits, float* Yp, int64_t wait_us, int* status, cudaStream_t st,
                     int* splits_used) {
   const int nmma = nmma_for(r);
-  const int stages = stages_for(nmma);
+  const int n_tiles = (int)ceil_div(N, BM);
+  // tuning: KB 64-parameter blocks per stage, raster group of sample tiles
+  int KB = 1, group = n_tiles, rotate = 0;
+  if (const char* env = getenv("WSSR_TUNE_PASSA")) {
+    int g = 0, kb = 0, rt = 0;
+    const int n = sscanf(env, "%d,%d,%d", &g, &kb, &rt);
+    if (n >= 2) {
+      if (g >= 1) group = g < n_tiles ? g : n_tiles;
+      if (kb >= 1 && kb <= 4) KB = kb;
+    }
+    if (n == 3) rotate = rt != 0;
+  }
+  size_t stages = 0;
+  for (;; --KB) {
+    const size_t stage = (size_t)KB * (A_BYTES + (size_t)nmma * BK * 2);
+    stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+    if (stages >= 2 || KB == 1) break;
+  }
+  if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmX;
   if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, BM)) return -1;
-  if (!encode_2d(&tmX, XhatT, (uint64_t)M, (uint64_t)r, (uint64_t)ldx * 2, BK, (uint32_t)nmma)) return -1;
-  const int k_chunks = (int)ceil_div(M, BK);
+  if (!encode_blocked(&tmX, XhatT, M, r, (uint32_t)nmma)) return -1;
+  const int k_chunks = (int)ceil_div(M, (int64_t)BK * KB);
   const int kc_per_split = (int)ceil_div(k_chunks, splits);
   const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
-  const size_t smem = smem_for(nmma, stages);
+  const size_t smem = 1024 + stages * (size_t)KB * (A_BYTES + (size_t)nmma * BK * 2) + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tc_passA, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  dim3 grid((unsigned)ceil_div(N, BM), (unsigned)s_eff);
-  k_tc_passA<<<grid, THREADS, smem, st>>>(tmO, tmX, N, r, nmma, tmem_cols_for(nmma), stages, k_chunks,
-                                          kc_per_split, Yp, (uint64_t)wait_us * 1000ull, status);
+  k_tc_passA<<<(unsigned)(n_tiles * s_eff), THREADS, smem, st>>>(
+      tmO, tmX, N, r, nmma, tmem_cols_for(nmma), (int)stages, KB, n_tiles, s_eff, group, k_chunks,
+      kc_per_split, rotate, Yp, (uint64_t)wait_us * 1000ull, status);
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
-                    int r, const double* ysum, float* Z, float* mu_io, int compute_mu,
-                    int64_t wait_us, int* status, cudaStream_t st) {
+                    int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
+                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st) {
   const int nmma = nmma_for(r);
   const int stages = stages_for(nmma);
   CUtensorMap tmO, tmY;
@@ -562,10 +756,44 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   dim3 grid((unsigned)ceil_div(M, BM));
   if (compute_mu)
     k_tc_passB<true><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
-                                                  ysum, Z, mu_io, (uint64_t)wait_us * 1000ull, status);
+                                                  ysum, Z, (bf16*)ZT, ldz, mu_io,
+                                                  (uint64_t)wait_us * 1000ull, status);
   else
     k_tc_passB<false><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
-                                                   ysum, Z, mu_io, (uint64_t)wait_us * 1000ull, status);
+                                                   ysum, Z, (bf16*)ZT, ldz, mu_io,
+                                                   (uint64_t)wait_us * 1000ull, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+}
+
+int tc_gram_splits(int64_t L, int num_sms) {
+  int64_t S = ceil_div(L, BK * 16);  // at least 16 chunks per CTA
+  if (S > num_sms) S = num_sms;
+  if (S < 1) S = 1;
+  return (int)S;
+}
+
+int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                   int* status, cudaStream_t st, int* splits_used) {
+  const int nmma = nmma_for(r);
+  const int rows = r <= 128 ? 128 : 256;
+  const int tmem_cols = rows == 256 ? 512 : tmem_cols_for(nmma);
+  const size_t stage = (size_t)rows * BK * 2;
+  size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+  if (stages > MAX_STAGES) stages = MAX_STAGES;
+  CUtensorMap tm;
+  if (!encode_blocked(&tm, XT, L, r, (uint32_t)rows)) return -1;
+  const int k_chunks = (int)ceil_div(L, BK);
+  const int kc_per_split = (int)ceil_div(k_chunks, splits);
+  const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
+  const size_t smem = 1024 + stages * stage + sizeof(Ctl);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  k_tc_gram<<<s_eff, THREADS, smem, st>>>(tm, r, nmma, rows, tmem_cols, (int)stages, k_chunks, kc_per_split,
+                                          Gp, (uint64_t)wait_us * 1000ull, status);
+  *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -2,14 +2,17 @@
 //
 // One wssr_step enqueues, on the caller's stream and without any host
 // synchronisation (Section 4.2, Algorithm 1, warm-started; Section 4.1,
-// Eq. (updated_sr_1)):
+// Eq. (updated_sr_1)). The basis of the subspace is kept as an operand block
+// Xh (the previous V, then each Z = O_c^T Q_Y in operand precision) together
+// with an r x r factor T_X such that Xh T_X is orthonormal; T_X is folded into
+// the r-dimensional side of the next product instead of forming Xh T_X:
 //   repeat m times:
-//     pass A   Y = O_c X                (X = current subspace, operand precision)
-//     orth(Y)  one Cholesky QR pass     (keeps the next product well conditioned)
-//     pass B   Z = O_c^T Y              (column mean mu accumulated in-pass)
-//     orth(Z)  CholeskyQR2              -> V (FP32) and its operand copy
-//   Rayleigh-Ritz: Y = O_c V, H = Y^T Y / N (FP64), Jacobi H = W L W^T,
-//     V_out = V W, sigma_i^2 = FP64 Rayleigh quotients of Y W
+//     pass A   Y = (O_c Xh) T_X          (centring by the column mean of O Xh)
+//     orth(Y)  Cholesky QR: Q_Y = Y R_Y^-1, operand copy Qh_Y
+//     pass B   Xh = O_c^T Qh_Y           (mu accumulated in-pass; written in operand form)
+//     T_X      = R^-1 with R^T R = Xh^T Xh (Gram of the operand values)
+//   Rayleigh-Ritz: Y = (O_c Xh) T_X, H = Y^T Y / N (FP64), Jacobi H = W L W^T,
+//     V_out = Xh (T_X W), sigma_i^2 = FP64 Rayleigh quotients of Y W
 //   apply:  c = V_out^T g, delta = g / lam + V_out (d * c)
 #include <stdio.h>
 #include <stdlib.h>
@@ -63,6 +66,11 @@ struct wssr_ctx {
   double* c = nullptr;
   double* e = nullptr;
   double* dot_part = nullptr;
+  float* TX = nullptr;         // r x r: Xh TX orthonormal
+  float* TY = nullptr;         // r x r: Cholesky-QR factor of Y
+  float* TW = nullptr;         // r x r: TX W
+  float* tc_gram_part = nullptr;  // tcgen05 Gram partials (splits x r x r)
+  int gram_splits_tc = 1;
 
   // profiling: event pairs around kernel groups
   bool prof = false;
@@ -88,7 +96,8 @@ cudaError_t dalloc(P** p, size_t bytes) {
 void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
-                  h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part};
+                  h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
+                  h->TX, h->TY, h->TW, h->tc_gram_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -126,87 +135,115 @@ struct Timed {
   }
 };
 
-// ---- pass A: Y (N x r, centred) = O_c X; X is the float block, cast as needed ----
-wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const float* X, bool x_cast_ready, float* Y,
-                   cudaStream_t st) {
-  const int64_t N = h->N, M = h->M;
-  const int r = h->r;
-  if (h->use_tc) {
-    if (!x_cast_ready) {
-      launch_cast(X, M, r, nullptr, 1, h->Xhat, h->ldx, nullptr, st);
-      h->launches++;
-    }
-    int nparts = 0;
-    int rc;
-    {
-      Timed tm(h, WSSR_KCAT_PASS_A, st);
-      rc = tc_passA_launch(op->O, op->ld, N, M, h->Xhat, h->ldx, r, h->splits_tc, h->Yp,
-                           h->opt.wait_cap, h->status, st, &nparts);
-      h->launches++;
-    }
-    if (rc != 0) return WSSR_ERR_UNSUPPORTED;
-    int64_t nb = 0;
-    launch_reduce_splits(h->Yp, nparts, N, r, Y, h->csum_part, &nb, st);
-    h->launches++;
-    launch_centre(Y, N, r, h->csum_part, nb, h->mean_r, st);
-    h->launches += 2;
-  } else {
-    const void* Xop = X;
-    if (is_bf16(h)) {
-      if (!x_cast_ready) {
-        launch_cast(X, M, r, h->Xhat, 1, nullptr, 0, nullptr, st);
-        h->launches++;
-      }
-      Xop = h->Xhat;
-    }
-    {
-      Timed tm(h, WSSR_KCAT_PASS_A, st);
-      if (is_bf16(h)) launch_passA_simt<bf16>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
-      else launch_passA_simt<float>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
-      h->launches++;
-    }
-    int64_t nb = 0;
-    launch_reduce_splits(h->Yp, passA_simt_effective_splits(M, h->splits_simt), N, r, Y,
-                         h->csum_part, &nb, st);
-    h->launches++;
-    launch_centre(Y, N, r, h->csum_part, nb, h->mean_r, st);
-    h->launches += 2;
-  }
-  return check_launch(h);
-}
+// Operand layout of the tall blocks for the active engine:
+//   tcgen05: bf16 K-blocked (blk_index);  SIMT + bf16: bf16 row-major;  SIMT + f32: float row-major.
+int operand_layout(const wssr_ctx* h) { return h->use_tc ? 2 : (is_bf16(h) ? 1 : 0); }
 
-// ---- pass B: Z (M x r) = O_c^T Yop where Yop is the operand copy and ysum its column sums ----
-wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float* Z,
-                   cudaStream_t st) {
-  const int64_t N = h->N, M = h->M;
-  const int r = h->r;
-  Timed tm(h, WSSR_KCAT_PASS_B, st);
+// Cast a float M x r block into the pass A operand buffer (no-op for f32 SIMT).
+const void* cast_X_operand(wssr_ctx* h, const float* X, cudaStream_t st) {
   if (h->use_tc) {
-    int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Z, h->mu,
-                             h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st);
-    if (rc != 0) return WSSR_ERR_UNSUPPORTED;
-    h->mu_valid = true;
+    launch_cast(X, h->M, h->r, nullptr, 1, h->Xhat, 0 /* K-blocked */, nullptr, st);
   } else if (is_bf16(h)) {
-    launch_passB_simt<bf16>(op->O, op->ld, N, M, Yop, r, h->ysum, Z, h->mu, st);
+    launch_cast(X, h->M, h->r, h->Xhat, 1, nullptr, 0, nullptr, st);
   } else {
-    launch_passB_simt<float>(op->O, op->ld, N, M, Yop, r, h->ysum, Z, h->mu, st);
+    return X;
   }
   h->launches++;
+  return h->Xhat;
+}
+
+// ---- pass A: Y (N x r, centred) = O_c Xop, Xop in the engine's operand layout ----
+wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const void* Xop, float* Y, cudaStream_t st) {
+  const int64_t N = h->N, M = h->M;
+  const int r = h->r;
+  int nsplit = 0;
+  {
+    Timed tm(h, WSSR_KCAT_PASS_A, st);
+    if (h->use_tc) {
+      int rc = tc_passA_launch(op->O, op->ld, N, M, Xop, h->ldx, r, h->splits_tc, h->Yp,
+                               h->opt.wait_cap, h->status, st, &nsplit);
+      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+    } else {
+      if (is_bf16(h)) launch_passA_simt<bf16>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
+      else launch_passA_simt<float>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
+      nsplit = passA_simt_effective_splits(M, h->splits_simt);
+    }
+    h->launches++;
+  }
+  Timed tm(h, WSSR_KCAT_ORTH, st);
+  int64_t nb = 0;
+  launch_reduce_splits(h->Yp, nsplit, N, r, Y, h->csum_part, &nb, st);
+  launch_centre(Y, N, r, h->csum_part, nb, h->mean_r, st);
+  h->launches += 3;
   return check_launch(h);
 }
 
-// One Cholesky QR pass: Xo = X R^-1 with optional operand copies / column sums.
+// ---- pass B: Z = O_c^T Yop (Yop in operand layout, ysum its column sums).
+// Output: float Z (M x r) when Zf != nullptr, else the pass A operand buffer
+// (bf16 transposed for tcgen05; for SIMT + bf16 the float result in h->Z is
+// cast to bf16 row-major). Returns the operand pointer in *Xop_out. ----
+wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float* Zf,
+                   const void** Xop_out, cudaStream_t st) {
+  const int64_t N = h->N, M = h->M;
+  const int r = h->r;
+  {
+    Timed tm(h, WSSR_KCAT_PASS_B, st);
+    if (h->use_tc) {
+      void* ZT = Zf ? nullptr : h->Xhat;
+      int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Zf, ZT, h->ldx, h->mu,
+                               h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st);
+      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      h->mu_valid = true;
+    } else if (is_bf16(h)) {
+      launch_passB_simt<bf16>(op->O, op->ld, N, M, Yop, r, h->ysum, Zf ? Zf : h->Z, h->mu, st);
+    } else {
+      launch_passB_simt<float>(op->O, op->ld, N, M, Yop, r, h->ysum, Zf ? Zf : h->Z, h->mu, st);
+    }
+    h->launches++;
+  }
+  if (Xop_out) {
+    if (h->use_tc) {
+      *Xop_out = h->Xhat;
+    } else if (is_bf16(h)) {
+      Timed tm(h, WSSR_KCAT_ORTH, st);
+      launch_cast(h->Z, M, r, h->Xhat, 1, nullptr, 0, nullptr, st);
+      h->launches++;
+      *Xop_out = h->Xhat;
+    } else {
+      *Xop_out = h->Z;
+    }
+  }
+  return check_launch(h);
+}
+
+// Gram of the operand block (its exact values) -> T_out = R^-1, R^T R = Xop^T Xop.
+void factor_operand(wssr_ctx* h, const void* Xop, float* T_out, cudaStream_t st) {
+  Timed tm(h, WSSR_KCAT_ORTH, st);
+  const int r = h->r;
+  if (h->use_tc) {
+    int used = 0;
+    tc_gram_launch(Xop, h->ldx, h->M, r, h->gram_splits_tc, h->tc_gram_part, h->opt.wait_cap, h->status,
+                   st, &used);
+    launch_sum_partials(h->tc_gram_part, used, r, 1.0, h->G, st);
+  } else {
+    launch_gram_any(Xop, is_bf16(h) ? 1 : 0, h->M, r, h->gram_part, h->G, 1.0, st);
+  }
+  launch_chol_inv(h->G, r, T_out, h->status, h->status + 1, st);
+  h->launches += 3;
+}
+
+// One Cholesky QR pass on a float block: Xo = X R^-1 (optional operand copies / column sums).
 void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row, void* lpT,
                  int64_t ldT, double* colsum_part, int64_t* nb_out, cudaStream_t st) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_ORTH, st);
   launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
-  launch_chol_inv(h->G, r, h->T, h->status, h->status + 1, st);
-  launch_apply(X, L, r, h->T, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st);
+  launch_chol_inv(h->G, r, h->TY, h->status, h->status + 1, st);
+  launch_apply(X, L, r, h->TY, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st);
   h->launches += 4;
 }
 
-// Orthonormalise Y in place-ish (result in h->Y2) and produce the pass B operand.
+// Orthonormalise Y (one Cholesky QR pass) into h->Y2 and produce the pass B operand.
 const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
   const int64_t N = h->N;
   int64_t nb = 0;
@@ -219,13 +256,12 @@ const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
   return h->Y2;
 }
 
-// CholeskyQR2 of Z (M x r) -> h->V, plus the pass A operand copy of V.
-void orth_Z(wssr_ctx* h, cudaStream_t st) {
-  const int64_t M = h->M;
-  cholqr_pass(h, h->Z, M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
-  void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Xhat : nullptr;
-  void* lpT = h->use_tc ? h->Xhat : nullptr;
-  cholqr_pass(h, h->V2, M, h->V, lp_row, lpT, h->ldx, nullptr, nullptr, st);
+// Y <- Y T (N x r times r x r) through h->Y2.
+void right_multiply_Y(wssr_ctx* h, float* Y, const float* T, cudaStream_t st) {
+  Timed tm(h, WSSR_KCAT_ORTH, st);
+  launch_apply(Y, h->N, h->r, T, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  cudaMemcpyAsync(Y, h->Y2, (size_t)h->N * h->r * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  h->launches++;
 }
 
 // Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
@@ -233,27 +269,31 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
                    double* sigma, cudaStream_t st) {
   const int64_t N = h->N, M = h->M;
   const int r = h->r;
-  const float* X = V_start;
-  bool ready = false;
   wssr_status s;
+  h->mu_valid = false;
+  const void* Xop = cast_X_operand(h, V_start, st);
+  bool have_T = false;
   for (int it = 0; it < m; ++it) {
-    if ((s = pass_A(h, op, X, ready, h->Y, st)) != WSSR_OK) return s;
+    if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
+    if (have_T) right_multiply_Y(h, h->Y, h->TX, st);
     const void* Yop = orth_Y_and_operand(h, h->Y, st);
-    if ((s = pass_B(h, op, Yop, h->Z, st)) != WSSR_OK) return s;
-    orth_Z(h, st);
-    X = h->V;
-    ready = true;
+    if ((s = pass_B(h, op, Yop, nullptr, &Xop, st)) != WSSR_OK) return s;
+    factor_operand(h, Xop, h->TX, st);
+    have_T = true;
   }
-  // Rayleigh-Ritz on span(V)
-  if ((s = pass_A(h, op, X, ready, h->Y, st)) != WSSR_OK) return s;
+  // Rayleigh-Ritz on span(Xh) = span(Xh TX)
+  if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
+  right_multiply_Y(h, h->Y, h->TX, st);
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, N, r, h->gram_part, h->G, 1.0 / (double)N, st);
   launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
   launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->W, st);
-  launch_apply(X, M, r, h->W, V_out, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  launch_apply_any(Xop, operand_layout(h), h->use_tc ? h->ldx : r, M, r, h->TW, V_out, nullptr, 0, nullptr,
+                   0, nullptr, nullptr, st);
   launch_apply(h->Y, N, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   launch_gram(h->Y2, N, r, h->gram_part, h->Hp, 1.0 / (double)N, st);
-  h->launches += 2 + 1 + 1 + 1 + 1 + 2;
+  h->launches += 2 + 1 + 1 + 1 + 1 + 1 + 2;
   double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
   launch_finalize_sigma(h->Hp, r, sig, st);
   h->launches++;
@@ -361,7 +401,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(V, (size_t)M * r * f);
   ALLOC(V2, (size_t)M * r * f);
   if (opt.dtype == WSSR_DTYPE_BF16) {
-    ALLOC(Xhat, (size_t)h->ldx * r * 2);
+    ALLOC(Xhat, (size_t)std::max<int64_t>(blk_elems(M, r), h->ldx * r) * 2);
     ALLOC(Yhat, (size_t)h->ldy * r * 2);
   }
   ALLOC(mu, (size_t)M * f);
@@ -376,6 +416,13 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(c, (size_t)r * d);
   ALLOC(e, (size_t)r * d);
   ALLOC(dot_part, (size_t)dot_part_elems(M, r) * d);
+  ALLOC(TX, (size_t)r * r * f);
+  ALLOC(TY, (size_t)r * r * f);
+  ALLOC(TW, (size_t)r * r * f);
+  if (h->use_tc) {
+    h->gram_splits_tc = tc_gram_splits(M, h->num_sms);
+    ALLOC(tc_gram_part, (size_t)h->gram_splits_tc * r * r * f);
+  }
 #undef ALLOC
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -414,7 +461,7 @@ wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const flo
   h->last_stream = st;
   h->launches = 0;
   // orthonormalise the random block first (Cholesky QR twice), then iterate
-  h->mu_valid = false;
+  // orthonormalise the random block first (CholeskyQR2), then iterate
   cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
   cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
   return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, st);
@@ -428,7 +475,8 @@ wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X,
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
-  return pass_A(h, op, X, false, Y, st);
+  const void* Xop = cast_X_operand(h, X, st);
+  return pass_A(h, op, Xop, Y, st);
 }
 
 wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y, float* Z,
@@ -449,7 +497,7 @@ wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y
   launch_colsum_finalize(h->csum_part, ceil_div(N, 64), r, h->ysum, st);
   h->launches += 2;
   if (is_bf16(h)) Yop = h->Yhat;
-  return pass_B(h, op, Yop, Z, st);
+  return pass_B(h, op, Yop, Z, nullptr, st);
 }
 
 wssr_status wssr_orthonormalize(wssr_handle h, float* X, int64_t L, int32_t passes,

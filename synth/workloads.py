@@ -176,10 +176,18 @@ def gaussian_torch(shape, device, *key, dtype=None):
 
 
 def orthonormal_torch(L: int, K: int, device, *key):
+    """L x K block with orthonormal columns on ``device``: a seeded Gaussian
+    orthonormalised by two Cholesky-QR passes (Gram on the device, the small
+    K x K factor on the host), so that no torch.linalg kernel is needed."""
+    import numpy as np
     import torch
-    q, r = torch.linalg.qr(gaussian_torch((L, K), device, *key))
-    s = torch.where(torch.diagonal(r) < 0, -1.0, 1.0)
-    return q * s[None, :]
+    X = gaussian_torch((L, K), device, *key)
+    for _ in range(2):
+        G = (X.T @ X).double().cpu().numpy()
+        R = np.linalg.cholesky(G).T
+        Rinv = np.linalg.solve(R, np.eye(K))
+        X = X @ torch.from_numpy(Rinv).to(device=device, dtype=X.dtype)
+    return X
 
 
 def planted_O_torch(w: Planted, device, out=None, out_dtype=None, ld: Optional[int] = None,
