@@ -260,6 +260,7 @@ def run_ours(args, w):
     clk = clocks.stop()
     prof = s.profile_end()
     s.check("timed steps")
+    stats = s.stats()
     ms_total = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
@@ -325,6 +326,7 @@ def run_ours(args, w):
         "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
                           "model": f"{2 * w.m + 1} O passes x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

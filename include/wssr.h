@@ -204,6 +204,12 @@ wssr_status wssr_profile_begin(wssr_handle h);
  * and the number of kernel launches. Either output may be NULL. */
 wssr_status wssr_profile_end(wssr_handle h, double* ms, int64_t* launches, int32_t ncat);
 
+/* Diagnostics of the last wssr_step / wssr_init_subspace (synchronises the
+ * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz
+ * eigensolve, out[1] = shifted Cholesky retries since wssr_create,
+ * out[2] = kernel launches it enqueued. Writes min(n, 3) values. */
+wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n);
+
 /* Free the workspace (synchronises the device first). NULL is ignored. */
 void wssr_destroy(wssr_handle h);
 

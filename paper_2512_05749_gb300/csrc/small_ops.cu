@@ -82,8 +82,8 @@ constexpr int GK = 32;          // rows per smem stage
 constexpr int GFLUSH = 256;     // rows per FP32 partial
 
 int gram_nb(int64_t L) {
-  int64_t nb = ceil_div(L, 512);
-  if (nb > 96) nb = 96;
+  int64_t nb = ceil_div(L, 128);
+  if (nb > 256) nb = 256;
   if (nb < 1) nb = 1;
   return (int)nb;
 }
@@ -218,8 +218,10 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
   float* A = reinterpret_cast<float*>(smem_raw + sizeof(double) * 256);
   __shared__ int flag;
   __shared__ float tmp[256];
+  __shared__ int rb[256];  // packed row base: A[i][j] = A[rb[i] + j] for j >= i
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) flag = 0;
+  if (tid < r) rb[tid] = pidx(tid, 0, r);
   __syncthreads();
   if (tid < r) {
     const double gii = G[(int64_t)tid * r + tid];
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
       if (i <= j) {
         const double g = G[e];
         if (!isfinite(g)) flag = 2;
-        A[pidx(i, j, r)] = (float)(g * d[i] * d[j]) + (i == j ? shift : 0.f);
+        A[rb[i] + j] = (float)g * (float)d[i] * (float)d[j] + (i == j ? shift : 0.f);
       }
     }
     __syncthreads();
@@ -247,18 +249,20 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
     if (tid == 0) flag = 0;
     __syncthreads();
     for (int k = 0; k < r; ++k) {
-      const float piv = A[pidx(k, k, r)];
+      const int bk = rb[k];
+      const float piv = A[bk + k];
       if (!(piv > 1e-8f)) {  // uniform: every thread read the same value
         if (tid == 0) flag = 1;
         break;
       }
       const float rho = sqrtf(piv), inv = 1.f / rho;
       __syncthreads();
-      for (int j = k + tid; j < r; j += 1024) A[pidx(k, j, r)] = (j == k) ? rho : A[pidx(k, j, r)] * inv;
+      for (int j = k + tid; j < r; j += 1024) A[bk + j] = (j == k) ? rho : A[bk + j] * inv;
       __syncthreads();
       for (int i = k + 1 + warp; i < r; i += 32) {
-        const float aki = A[pidx(k, i, r)];
-        for (int j = i + lane; j < r; j += 32) A[pidx(i, j, r)] -= aki * A[pidx(k, j, r)];
+        const float aki = A[bk + i];
+        const int bi = rb[i];
+        for (int j = i + lane; j < r; j += 32) A[bi + j] -= aki * A[bk + j];
       }
       __syncthreads();
     }
@@ -275,27 +279,38 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
   }
   // In-place inverse of the upper-triangular factor, one row at a time from
   // the bottom: X[i][j] = (delta_ij - sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i].
-  // Four threads share each column j (r <= 256 columns, 1024 threads).
+  // Four threads share each column j (r <= 256 columns, 1024 threads), each
+  // with four independent partial sums.
   const int jcol = tid >> 2, q = tid & 3;
   for (int i = r - 1; i >= 0; --i) {
     float s = 0.f;
     if (jcol < r && jcol > i) {
-      for (int k = i + 1 + q; k <= jcol; k += 4) s = fmaf(A[pidx(i, k, r)], A[pidx(k, jcol, r)], s);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      const int bi = rb[i];
+      int k = i + 1 + q;
+      for (; k + 12 <= jcol; k += 16) {
+        s0 = fmaf(A[bi + k], A[rb[k] + jcol], s0);
+        s1 = fmaf(A[bi + k + 4], A[rb[k + 4] + jcol], s1);
+        s2 = fmaf(A[bi + k + 8], A[rb[k + 8] + jcol], s2);
+        s3 = fmaf(A[bi + k + 12], A[rb[k + 12] + jcol], s3);
+      }
+      for (; k <= jcol; k += 4) s0 = fmaf(A[bi + k], A[rb[k] + jcol], s0);
+      s = (s0 + s1) + (s2 + s3);
     }
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     if (q == 0 && jcol < r && jcol >= i) tmp[jcol] = s;
     __syncthreads();
     if (tid < r && tid >= i) {
-      const float rii = A[pidx(i, i, r)];
-      A[pidx(i, tid, r)] = (tid == i) ? 1.f / rii : -tmp[tid] / rii;
+      const float rii = A[rb[i] + i];
+      A[rb[i] + tid] = (tid == i) ? 1.f / rii : -tmp[tid] / rii;
     }
     __syncthreads();
   }
   // T = D R'^-1 (rows scaled by d_i), full r x r with zeros below the diagonal.
   for (int e = tid; e < r * r; e += 1024) {
     const int i = e / r, j = e % r;
-    T[e] = (i <= j) ? (float)((double)A[pidx(i, j, r)] * d[i]) : 0.f;
+    T[e] = (i <= j) ? A[rb[i] + j] * (float)d[i] : 0.f;
   }
 }
 }  // namespace
@@ -505,18 +520,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);
   __shared__ float cs_c[128], cs_s[128], cs_t[128];
+  __shared__ int pp[128], qq[128];
+  __shared__ int rb[256];  // packed row base: A[i][j] = A[rb[i] + j] for j >= i
   __shared__ int rot_round, rot_sweep, bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int h = r / 2;
   const float tol = 3e-7f;
   if (tid == 0) bad = 0;
+  if (tid < r) rb[tid] = pidx(tid, 0, r);
   __syncthreads();
   for (int e = tid; e < r * r; e += 1024) {
     const int i = e / r, j = e % r;
     if (i <= j) {
       const double v = H[e];
       if (!isfinite(v)) bad = 1;
-      A[pidx(i, j, r)] = (float)v;
+      A[rb[i] + j] = (float)v;
     }
   }
   __syncthreads();
@@ -527,6 +545,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     }
     return;
   }
+#define AIX(a, b) ((a) <= (b) ? rb[a] + (b) : rb[b] + (a))
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) rot_sweep = 0;
@@ -537,10 +556,16 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
       if (tid < h) {
         int p, q;
         rr_pair(k, tid, r, p, q);
-        const float app = A[pidx(p, p, r)], aqq = A[pidx(q, q, r)];
-        const float apq = A[p < q ? pidx(p, q, r) : pidx(q, p, r)];
+        pp[tid] = p;
+        qq[tid] = q;
+        const float app = A[rb[p] + p], aqq = A[rb[q] + q];
+        const float apq = A[AIX(p, q)];
         float c = 1.f, s = 0.f, t = 0.f;
-        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
+        // rotate when the pair is not yet orthogonal relative to its diagonal
+        // (tol) and a_pq is above the FP32 rounding noise that rotations of
+        // the larger element leave behind (a few ulp of max |a_pp|, |a_qq|)
+        const float noise = 4.f * 5.96e-8f * fmaxf(fabsf(app), fabsf(aqq));
+        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > noise) {
           const float tau = (aqq - app) / (2.f * apq);
           t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
           c = rsqrtf(1.f + t * t);
@@ -554,31 +579,27 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
       }
       __syncthreads();
       if (rot_round) {
-        for (int i1 = warp; i1 < h; i1 += 32) {
-          int p1, q1;
-          rr_pair(k, i1, r, p1, q1);
+        // warp rows in a balanced order (w, 63-w, 64+w, 127-w, ... when h % 64 == 0)
+        for (int t = 0; 32 * t + warp < h; ++t) {
+          const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
+          const int p1 = pp[i1], q1 = qq[i1];
           const float c1 = cs_c[i1], s1 = cs_s[i1];
           for (int i2 = i1 + lane; i2 < h; i2 += 32) {
             if (i2 == i1) {
               const float t1 = cs_t[i1];
-              const int ipq = p1 < q1 ? pidx(p1, q1, r) : pidx(q1, p1, r);
+              const int ipq = AIX(p1, q1);
               const float apq = A[ipq];
-              A[pidx(p1, p1, r)] -= t1 * apq;
-              A[pidx(q1, q1, r)] += t1 * apq;
+              A[rb[p1] + p1] -= t1 * apq;
+              A[rb[q1] + q1] += t1 * apq;
               A[ipq] = 0.f;
             } else {
-              int p2, q2;
-              rr_pair(k, i2, r, p2, q2);
+              const int p2 = pp[i2], q2 = qq[i2];
               const float c2 = cs_c[i2], s2 = cs_s[i2];
-              const int i_pp = p1 < p2 ? pidx(p1, p2, r) : pidx(p2, p1, r);
-              const int i_pq = p1 < q2 ? pidx(p1, q2, r) : pidx(q2, p1, r);
-              const int i_qp = q1 < p2 ? pidx(q1, p2, r) : pidx(p2, q1, r);
-              const int i_qq = q1 < q2 ? pidx(q1, q2, r) : pidx(q2, q1, r);
+              const int i_pp = AIX(p1, p2), i_pq = AIX(p1, q2), i_qp = AIX(q1, p2), i_qq = AIX(q1, q2);
               const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
-              // B J2 (columns p2, q2)
+              // B J2 (columns p2, q2), then J1^T (rows p1, q1)
               const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
               const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
-              // J1^T (rows p1, q1)
               A[i_pp] = c1 * xpp - s1 * xqp;
               A[i_qp] = s1 * xpp + c1 * xqp;
               A[i_pq] = c1 * xpq - s1 * xqq;
@@ -596,8 +617,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
       break;
     }
   }
+#undef AIX
   if (tid == 0) *nsweeps_out = sweep;
-  for (int i = tid; i < r; i += 1024) evals[i] = A[pidx(i, i, r)];
+  for (int i = tid; i < r; i += 1024) evals[i] = A[rb[i] + i];
 }
 
 // Replays the logged rotations on rows of the identity (4 rows per CTA),
@@ -664,6 +686,30 @@ void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float
 }
 
 // ---------------------------------------------------------------------------
+// Three-term bf16 split of a float r x r matrix, transposed
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_split3_T(const float* __restrict__ TW, int r, bf16* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * r) return;
+  const int k = e / r, n = e % r;
+  const float x = TW[e];
+  const bf16 hi = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(hi);
+  const bf16 mid = __float2bfloat16_rn(r1);
+  const bf16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+  const int64_t o = (int64_t)n * r + k;
+  out[o] = hi;
+  out[(int64_t)r * r + o] = mid;
+  out[2 * (int64_t)r * r + o] = lo;
+}
+}  // namespace
+
+void launch_split3_T(const float* TW, int r, void* TWT3, cudaStream_t st) {
+  k_split3_T<<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(TW, r, (bf16*)TWT3);
+}
+
+// ---------------------------------------------------------------------------
 // c = V^T g, sigma from the FP64 Rayleigh quotients, Woodbury apply
 // ---------------------------------------------------------------------------
 namespace {
@@ -681,17 +727,19 @@ __global__ void k_dot_part(const float* __restrict__ V, const float* __restrict_
   const int64_t mb = (int64_t)blockIdx.x * chunk;
   const int64_t me = mb + chunk < M ? mb + chunk : M;
   double s64 = 0.0;
-  float s32 = 0.f;
-  int cnt = 0;
-  for (int64_t m = mb; m < me; ++m) {
-    s32 = fmaf(V[m * r + j], g[m], s32);
-    if (++cnt == 64) {
-      s64 += (double)s32;
-      s32 = 0.f;
-      cnt = 0;
+  int64_t m = mb;
+  // 8 rows in flight per thread; FP32 partial sums over 64 rows, then FP64
+  while (m < me) {
+    const int64_t mend = m + 64 < me ? m + 64 : me;
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (; m + 8 <= mend; m += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = fmaf(V[(m + u) * r + j], g[m + u], a[u]);
     }
+    for (; m < mend; ++m) a[0] = fmaf(V[m * r + j], g[m], a[0]);
+    s64 += (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
   }
-  part[(int64_t)blockIdx.x * r + j] = s64 + (double)s32;
+  part[(int64_t)blockIdx.x * r + j] = s64;
 }
 
 __global__ void k_finalize_sigma(const double* __restrict__ Hp, int r, double* __restrict__ sigma) {

@@ -45,7 +45,7 @@ struct Ctl {
   uint64_t accum;
   uint32_t tmem;
   int abort;
-  float mu[BM];
+  float mu[2 * BM];
   float ysum[256];
   double red[8][BM];
 };
@@ -271,11 +271,12 @@ __device__ __forceinline__ void mma_loop(Ctl* ctl, uint8_t* base, uint32_t stage
 // ---------------------------------------------------------------------------
 // Pass A
 // ---------------------------------------------------------------------------
-// Each stage holds KB consecutive 64-parameter blocks (KB boxes of O and of
-// the operand), so that every O row is read in KB x 128 contiguous bytes.
-// CTAs are rasterised in groups of `group` sample tiles: a group's tiles run
-// all their splits before the next group starts, which bounds the number of
-// distinct O rows (and pages) in flight.
+// Each CTA accumulates MT x 128 sample rows (MT accumulators of 128 x N in
+// TMEM, columns 0 and 256) so that every operand tile it loads serves MT O
+// tiles. Each stage holds KB consecutive 64-parameter blocks. CTAs are
+// rasterised in groups of `group` sample tiles (a group's tiles run all their
+// splits before the next group starts).
+template <int MT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passA(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmX,
                int64_t N, int r, int nmma, int tmem_cols, int stages, int KB, int n_tiles, int splits,
@@ -283,23 +284,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  const uint32_t a_bytes = A_BYTES * KB;
+  const uint32_t a_blk = A_BYTES * MT;  // one 64-parameter block of MT x 128 rows
+  const uint32_t a_bytes = a_blk * KB;
   const uint32_t xbox = (uint32_t)nmma * BK * 2;
   const uint32_t stage_bytes = a_bytes + xbox * KB;
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // rasterisation: group of `group` sample tiles x all splits, tile index fastest
   const int per_group = group * splits;
   const int gidx = blockIdx.x / per_group, within = blockIdx.x % per_group;
   const int gsize = (gidx + 1) * group <= n_tiles ? group : n_tiles - gidx * group;
   const int n_tile = gidx * group + within % gsize;
   const int split = within / gsize;
-  // k_chunks and kc_per_split count stages (KB blocks of 64 parameters)
   const int kc0 = split * kc_per_split;
   const int kc1 = kc0 + kc_per_split < k_chunks ? kc0 + kc_per_split : k_chunks;
   const int nk = kc1 - kc0;
-  // starting chunk of this tile within the split's range (spreads the
-  // concurrent requests of a wave over the row, see the launcher)
   const int rot = (rotate && nk > 0) ? (int)(((int64_t)n_tile * 977) % nk) : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -326,7 +324,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                  if (ii >= nk) ii -= nk;
                  const int k = (kc0 + ii) * BK * KB;
                  for (int b = 0; b < KB; ++b)
-                   tma_load_2d_hint(st + b * A_BYTES, &tmO, bar, k + b * BK, n_tile * BM, pol_o);
+                   tma_load_2d_hint(st + b * a_blk, &tmO, bar, k + b * BK, n_tile * BM * MT, pol_o);
                  for (int b = 0; b < KB; ++b)
                    tma_load_3d_hint(st + a_bytes + b * xbox, &tmX, bar, 0, 0, (k + b * BK) / BK, pol_x);
                });
@@ -337,10 +335,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
         for (int b = 0; b < KB; ++b)
 #pragma unroll
-          for (int kk = 0; kk < BK / UK; ++kk)
-            mma_bf16(tmem, smem_desc(sa + b * A_BYTES + kk * 32, 16, 1024),
-                     smem_desc(sa + a_bytes + b * xbox + kk * 32, 16, 1024), idesc,
-                     (!first || b > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BK / UK; ++kk) {
+            const uint64_t db = smem_desc(sa + a_bytes + b * xbox + kk * 32, 16, 1024);
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+              mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + b * a_blk + a * A_BYTES + kk * 32, 16, 1024),
+                       db, idesc, (!first || b > 0 || kk > 0) ? 1u : 0u);
+          }
       });
     }
   } else {
@@ -348,19 +349,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool ok = nk > 0 && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
     if (!ok && nk > 0) timeout(ctl, status);
     tc_fence_after();
-    const int64_t n = (int64_t)n_tile * BM + q * 32 + lane;
-    float* out = Yp + ((int64_t)split * N + n) * r;
-    for (int c = 0; c < nmma; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-      if (nk == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      }
-      if ((ok || nk == 0) && n < N) {
+    for (int a = 0; a < MT; ++a) {
+      const int64_t n = ((int64_t)n_tile * MT + a) * BM + q * 32 + lane;
+      float* out = Yp + ((int64_t)split * N + n) * r;
+      for (int c = 0; c < nmma; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(a * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (nk == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 4)
-          if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+        if ((ok || nk == 0) && n < N) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4)
+            if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
       }
     }
   }
@@ -375,7 +379,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Pass B
 // ---------------------------------------------------------------------------
-template <bool WITH_MU>
+// Each CTA covers MT x 128 parameters: its stage holds 2 MT 64-parameter O
+// boxes (8 KB apart) and one operand tile; accumulator a uses boxes 2a, 2a+1.
+template <bool WITH_MU, int MT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
                int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
@@ -383,10 +389,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                int64_t ldz, float* __restrict__ mu_io, uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  const uint32_t stage_bytes = A_BYTES + (uint32_t)nmma * BK * 2;
+  const uint32_t a_bytes = A_BYTES * MT;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)nmma * BK * 2;
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t m0 = (int64_t)blockIdx.x * BM * MT;
   const int nk = (int)ceil_div(N, BK);
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -409,9 +416,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
                [&](int i, uint8_t* st, uint64_t* bar) {
                  const int n = i * BK;
-                 tma_load_2d_hint(st, &tmO, bar, (int)m0, n, pol_o);
-                 tma_load_2d_hint(st + 8192, &tmO, bar, (int)m0 + 64, n, pol_o);
-                 tma_load_2d_hint(st + A_BYTES, &tmY, bar, n, 0, pol_y);
+#pragma unroll
+                 for (int b = 0; b < 2 * MT; ++b)
+                   tma_load_2d_hint(st + b * 8192, &tmO, bar, (int)m0 + 64 * b, n, pol_o);
+                 tma_load_2d_hint(st + a_bytes, &tmY, bar, n, 0, pol_y);
                });
     }
   } else if (warp == 1) {
@@ -421,17 +429,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         // A is MN-major: 16 samples = two 8-row groups (SBO 1024), 64-parameter
         // boxes 8 KB apart (LBO)
 #pragma unroll
-        for (int kk = 0; kk < BK / UK; ++kk)
-          mma_bf16(tmem, smem_desc(sa + kk * 2048, 8192, 1024), smem_desc(sa + A_BYTES + kk * 32, 16, 1024),
-                   idesc, (!first || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          const uint64_t db = smem_desc(sa + a_bytes + kk * 32, 16, 1024);
+#pragma unroll
+          for (int a = 0; a < MT; ++a)
+            mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + a * A_BYTES + kk * 2048, 8192, 1024), db,
+                     idesc, (!first || kk > 0) ? 1u : 0u);
+        }
       });
     }
   } else {
     const int et = threadIdx.x - 64;  // 0..127
     for (int j = et; j < r; j += 128) ctl->ysum[j] = (float)ysum[j];
     if (WITH_MU) {
-      // Column sums of the O tiles: thread = (8 parameters, 8 samples of each stage).
-      const int pg = et & 15, sg = et >> 4;
+      // Column sums of the O tiles: thread = 8 parameters (16 B chunk `c` of
+      // box `box`) over SG-sample runs of every stage.
+      constexpr int PG = 16 * MT;          // parameter groups of 8
+      constexpr int NSG = 128 / PG;        // sample groups
+      constexpr int RPS = 64 / NSG;        // rows per sample group and stage
+      const int pg = et % PG, sg = et / PG;
       const int box = pg >> 3, c = pg & 7;
       float acc[8];
       double acc64[8];
@@ -443,9 +459,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint8_t* sa = base + (size_t)s * stage_bytes + box * 8192;
         if (got) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int row = sg * 8 + j;
-            const uint4 v = *reinterpret_cast<const uint4*>(sa + row * 128 + ((c ^ j) << 4));
+          for (int j = 0; j < RPS; ++j) {
+            const int row = sg * RPS + j;
+            const uint4 v = *reinterpret_cast<const uint4*>(sa + row * 128 + ((c ^ (row & 7)) << 4));
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -465,41 +481,46 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int e = 0; e < 8; ++e) acc64[e] += (double)acc[e], acc[e] = 0.f;
         }
       }
+      double* red = &ctl->red[0][0];  // [NSG][PG * 8]
 #pragma unroll
-      for (int e = 0; e < 8; ++e) ctl->red[sg][pg * 8 + e] = acc64[e] + (double)acc[e];
+      for (int e = 0; e < 8; ++e) red[sg * (PG * 8) + pg * 8 + e] = acc64[e] + (double)acc[e];
       epi_bar();
-      double sum = 0.0;
-#pragma unroll
-      for (int g = 0; g < 8; ++g) sum += ctl->red[g][et];
-      const float mu = (float)(sum / (double)N);
-      ctl->mu[et] = mu;
-      if (m0 + et < M) mu_io[m0 + et] = mu;
+      for (int p = et; p < PG * 8; p += 128) {
+        double sum = 0.0;
+        for (int gq = 0; gq < NSG; ++gq) sum += red[gq * (PG * 8) + p];
+        const float mu = (float)(sum / (double)N);
+        ctl->mu[p] = mu;
+        if (m0 + p < M) mu_io[m0 + p] = mu;
+      }
     }
     epi_bar();
     const int q = warp & 3;
     const bool ok = mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
     if (!ok) timeout(ctl, status);
     tc_fence_after();
-    const int row = q * 32 + lane;
-    const int64_t m = m0 + row;
-    const float mu = WITH_MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
-    for (int c = 0; c < nmma; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-      if (ok && m < M) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 256 ? c + i : 255];
-        if (ZT) {
-          // K-blocked bf16 operand: for each column the warp writes 32
-          // consecutive parameters (64 contiguous bytes)
+    for (int a = 0; a < MT; ++a) {
+      const int row = a * BM + q * 32 + lane;
+      const int64_t m = m0 + row;
+      const float mu = WITH_MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
+      for (int c = 0; c < nmma; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(a * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (ok && m < M) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c + i < r) ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(v[i]);
-        } else {
-          float* out = Z + m * r;
+          for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 256 ? c + i : 255];
+          if (ZT) {
+            // K-blocked bf16 operand: for each column the warp writes 32
+            // consecutive parameters (64 contiguous bytes)
 #pragma unroll
-          for (int i = 0; i < 16; i += 4)
-            if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            for (int i = 0; i < 16; ++i)
+              if (c + i < r) ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(v[i]);
+          } else {
+            float* out = Z + m * r;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+              if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          }
         }
       }
     }
@@ -583,6 +604,108 @@ __global__ void __launch_bounds__(THREADS, 1)
                   ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rotation of the basis: V (M x r, FP32) = Xh (K-blocked bf16) * TW, with TW
+// (r x r) given as three bf16 terms of its transpose (TW^T = hi + mid + lo,
+// 24 significant bits), so the product is FP32-accurate with exact bf16 A.
+// A tile: 128 parameters x 64 basis columns, MN-major (two 64-parameter
+// boxes of the blocked layout, 8 KB apart); B tiles: NB output columns x 64,
+// K-major. Optionally fuses cpart[tile][n] = sum over the tile's rows of
+// V[m][n] g[m] (the Woodbury c = V^T g without re-reading V).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_rotate(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmHi,
+                const __grid_constant__ CUtensorMap tmMid, const __grid_constant__ CUtensorMap tmLo,
+                int64_t M, int r, int NB, int tmem_cols, int stages, float* __restrict__ V,
+                const float* __restrict__ g, double* __restrict__ cpart, uint64_t limit_ns, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  const uint32_t bbytes = (uint32_t)NB * BK * 2;
+  const uint32_t stage_bytes = A_BYTES + 3 * bbytes;
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int n0 = blockIdx.y * NB;
+  const int nk = (r + BK - 1) / BK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    mbar_init(&ctl->accum, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+  if (warp == 0) {
+    if (lane == 0)
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](int i, uint8_t* st, uint64_t* bar) {
+        const int k = i * BK;
+        tma_load_3d(st, &tmX, bar, 0, k, (int)(m0 >> 6));
+        tma_load_3d(st + 8192, &tmX, bar, 0, k, (int)(m0 >> 6) + 1);
+        tma_load_2d(st + A_BYTES, &tmHi, bar, k, n0);
+        tma_load_2d(st + A_BYTES + bbytes, &tmMid, bar, k, n0);
+        tma_load_2d(st + A_BYTES + 2 * bbytes, &tmLo, bar, k, n0);
+      });
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, NB, 1, 0);
+      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          const uint64_t da = smem_desc(sa + kk * 2048, 8192, 1024);
+          for (int t = 0; t < 3; ++t)
+            mma_bf16(tmem, da, smem_desc(sa + A_BYTES + t * bbytes + kk * 32, 16, 1024), idesc,
+                     (!first || kk > 0 || t > 0) ? 1u : 0u);
+        }
+      });
+    }
+  } else {
+    const int q = warp & 3, et = threadIdx.x - 64;
+    const bool ok = mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
+    if (!ok) timeout(ctl, status);
+    tc_fence_after();
+    const int row = q * 32 + lane;
+    const int64_t m = m0 + row;
+    const float gm = (g && m < M) ? g[m] : 0.f;
+    for (int c = 0; c < NB; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+      if (ok && m < M) {
+        float* out = V + m * r + n0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          if (n0 + c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+      if (cpart) {
+        // column sums of V * g over the tile's 128 rows: warp shuffle, then smem
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float x = (ok && m < M) ? v[i] * gm : 0.f;
+          x = warp_sum(x);
+          if (lane == 0) ctl->red[q][c + i] = (double)x;  // red[4][128] used as [warp][column]
+        }
+      }
+    }
+    if (cpart) {
+      epi_bar();
+      for (int n = et; n < NB; n += 128)
+        if (n0 + n < r)
+          cpart[(int64_t)blockIdx.x * r + n0 + n] = ((ctl->red[0][n] + ctl->red[1][n]) + ctl->red[2][n]) + ctl->red[3][n];
     }
   }
   tc_fence_before();
@@ -680,7 +803,7 @@ bool tc_supported(int dev) {
 }
 
 int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms) {
-  const int64_t n_tiles = ceil_div(N, BM), k_chunks = ceil_div(M, BK);
+  const int64_t n_tiles = ceil_div(N, 2 * BM), k_chunks = ceil_div(M, BK);
   int64_t S = num_sms / gcd64(n_tiles, num_sms);
   while (n_tiles * S < 2 * num_sms) S *= 2;
   int64_t cap = k_chunks / 8;
@@ -712,27 +835,30 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
     }
     if (n == 3) rotate = rt != 0;
   }
+  const int MT = 2;
+  const int n_tiles2 = (int)ceil_div(N, (int64_t)BM * MT);
+  if (group > n_tiles2) group = n_tiles2;
   size_t stages = 0;
   for (;; --KB) {
-    const size_t stage = (size_t)KB * (A_BYTES + (size_t)nmma * BK * 2);
+    const size_t stage = (size_t)KB * (A_BYTES * MT + (size_t)nmma * BK * 2);
     stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
     if (stages >= 2 || KB == 1) break;
   }
   if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmX;
-  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, BM)) return -1;
+  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, (uint32_t)(BM * MT))) return -1;
   if (!encode_blocked(&tmX, XhatT, M, r, (uint32_t)nmma)) return -1;
   const int k_chunks = (int)ceil_div(M, (int64_t)BK * KB);
   const int kc_per_split = (int)ceil_div(k_chunks, splits);
   const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
-  const size_t smem = 1024 + stages * (size_t)KB * (A_BYTES + (size_t)nmma * BK * 2) + sizeof(Ctl);
+  const size_t smem = 1024 + stages * (size_t)KB * (A_BYTES * MT + (size_t)nmma * BK * 2) + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_passA, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passA<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  k_tc_passA<<<(unsigned)(n_tiles * s_eff), THREADS, smem, st>>>(
-      tmO, tmX, N, r, nmma, tmem_cols_for(nmma), (int)stages, KB, n_tiles, s_eff, group, k_chunks,
+  k_tc_passA<2><<<(unsigned)(n_tiles2 * s_eff), THREADS, smem, st>>>(
+      tmO, tmX, N, r, nmma, 512, (int)stages, KB, n_tiles2, s_eff, group, k_chunks,
       kc_per_split, rotate, Yp, (uint64_t)wait_us * 1000ull, status);
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
@@ -741,27 +867,30 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
                     int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
                     int compute_mu, int64_t wait_us, int* status, cudaStream_t st) {
+  constexpr int MT = 2;
   const int nmma = nmma_for(r);
-  const int stages = stages_for(nmma);
+  const size_t stage = (size_t)A_BYTES * MT + (size_t)nmma * BK * 2;
+  size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+  if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmY;
   if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, 64, BK)) return -1;
   if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)nmma)) return -1;
-  const size_t smem = smem_for(nmma, stages);
+  const size_t smem = 1024 + stages * stage + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_passB<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_tc_passB<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<true, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<false, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  dim3 grid((unsigned)ceil_div(M, BM));
+  dim3 grid((unsigned)ceil_div(M, (int64_t)BM * MT));
   if (compute_mu)
-    k_tc_passB<true><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
-                                                  ysum, Z, (bf16*)ZT, ldz, mu_io,
-                                                  (uint64_t)wait_us * 1000ull, status);
+    k_tc_passB<true, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
+                                                      (bf16*)ZT, ldz, mu_io, (uint64_t)wait_us * 1000ull,
+                                                      status);
   else
-    k_tc_passB<false><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, tmem_cols_for(nmma), stages,
-                                                   ysum, Z, (bf16*)ZT, ldz, mu_io,
-                                                   (uint64_t)wait_us * 1000ull, status);
+    k_tc_passB<false, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
+                                                       (bf16*)ZT, ldz, mu_io, (uint64_t)wait_us * 1000ull,
+                                                       status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -796,5 +925,35 @@ int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, flo
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
+
+int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, const float* g,
+                     double* cpart, int64_t wait_us, int* status, cudaStream_t st) {
+  const int nmma = nmma_for(r);
+  const int NB = nmma <= 128 ? nmma : 128;
+  const uint32_t bbytes = (uint32_t)NB * BK * 2;
+  const size_t stage = A_BYTES + 3 * (size_t)bbytes;
+  size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+  if (stages > 4) stages = 4;
+  const bf16* T3 = reinterpret_cast<const bf16*>(TWT3);
+  CUtensorMap tmX, tmHi, tmMid, tmLo;
+  if (!encode_blocked(&tmX, Xblk, M, r, 64)) return -1;
+  for (int t = 0; t < 3; ++t) {
+    CUtensorMap* mp = t == 0 ? &tmHi : (t == 1 ? &tmMid : &tmLo);
+    if (!encode_2d(mp, T3 + (size_t)t * r * r, (uint64_t)r, (uint64_t)r, (uint64_t)r * 2, BK, (uint32_t)NB))
+      return -1;
+  }
+  const size_t smem = 1024 + stages * stage + sizeof(Ctl);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(nmma, NB));
+  k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, M, r, NB, tmem_cols_for(NB), (int)stages,
+                                           V, g, cpart, (uint64_t)wait_us * 1000ull, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+}
+
+int64_t tc_rotate_cpart_rows(int64_t M) { return ceil_div(M, BM); }
 
 }  // namespace wssr

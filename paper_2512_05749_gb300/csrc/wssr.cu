@@ -70,6 +70,9 @@ struct wssr_ctx {
   float* TY = nullptr;         // r x r: Cholesky-QR factor of Y
   float* TW = nullptr;         // r x r: TX W
   float* tc_gram_part = nullptr;  // tcgen05 Gram partials (splits x r x r)
+  void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
+  double* cpart = nullptr;        // per-tile partials of V^T g fused into the rotation
+  bool c_ready = false;           // h->c already holds V_out^T g
   int gram_splits_tc = 1;
 
   // profiling: event pairs around kernel groups
@@ -97,7 +100,7 @@ void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part};
+                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -266,7 +269,7 @@ void right_multiply_Y(wssr_ctx* h, float* Y, const float* T, cudaStream_t st) {
 
 // Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
 wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, int m, float* V_out,
-                   double* sigma, cudaStream_t st) {
+                   double* sigma, const float* g, cudaStream_t st) {
   const int64_t N = h->N, M = h->M;
   const int r = h->r;
   wssr_status s;
@@ -289,8 +292,20 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
   launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
   launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
-  launch_apply_any(Xop, operand_layout(h), h->use_tc ? h->ldx : r, M, r, h->TW, V_out, nullptr, 0, nullptr,
-                   0, nullptr, nullptr, st);
+  h->c_ready = false;
+  if (h->use_tc) {
+    // V_out = Xh (T W) on the tensor cores (c = V_out^T g is a separate,
+    // bandwidth-bound pass: fusing its column sums into this epilogue costs
+    // more warp shuffles than re-reading V_out)
+    (void)g;
+    launch_split3_T(h->TW, r, h->TWT3, st);
+    if (tc_rotate_launch(Xop, M, r, h->TWT3, V_out, nullptr, nullptr, h->opt.wait_cap, h->status, st) != 0)
+      return WSSR_ERR_UNSUPPORTED;
+    h->launches += 2;
+  } else {
+    launch_apply_any(Xop, operand_layout(h), r, M, r, h->TW, V_out, nullptr, 0, nullptr, 0, nullptr,
+                     nullptr, st);
+  }
   launch_apply(h->Y, N, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   launch_gram(h->Y2, N, r, h->gram_part, h->Hp, 1.0 / (double)N, st);
   h->launches += 2 + 1 + 1 + 1 + 1 + 1 + 2;
@@ -304,7 +319,8 @@ wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const flo
                      cudaStream_t st) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_APPLY, st);
-  launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
+  if (!h->c_ready) launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
+  h->c_ready = false;
   const double lam_eff = (h->opt.apply_mode == WSSR_APPLY_CUTOFF) ? h->opt.sigma_floor : h->lam;
   launch_woodbury_coeffs(sigma, h->c, r, h->lam, h->opt.apply_mode, h->opt.sigma_floor, h->e,
                          h->status, st);
@@ -422,6 +438,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (h->use_tc) {
     h->gram_splits_tc = tc_gram_splits(M, h->num_sms);
     ALLOC(tc_gram_part, (size_t)h->gram_splits_tc * r * r * f);
+    ALLOC(TWT3, (size_t)3 * r * r * 2);
+    ALLOC(cpart, (size_t)tc_rotate_cpart_rows(M) * r * d);
   }
 #undef ALLOC
   if (e != cudaSuccess) {
@@ -430,7 +448,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
     delete h;
     return e == cudaErrorMemoryAllocation ? WSSR_ERR_OOM : WSSR_ERR_CUDA;
   }
-  if (cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->nsweeps, 0, sizeof(int)) != cudaSuccess) {
     free_all(h);
     delete h;
     return WSSR_ERR_CUDA;
@@ -448,7 +467,7 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   h->last_stream = st;
   h->launches = 0;
   h->mu_valid = false;
-  if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, st)) != WSSR_OK) return s;
+  if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g, st)) != WSSR_OK) return s;
   return woodbury(h, V_out, sigma, g, delta, st);
 }
 
@@ -464,7 +483,7 @@ wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const flo
   // orthonormalise the random block first (CholeskyQR2), then iterate
   cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
   cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
-  return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, st);
+  return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, nullptr, st);
 }
 
 wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X, float* Y,
@@ -524,6 +543,7 @@ wssr_status wssr_woodbury(wssr_handle h, const float* V, const double* sigma, co
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
+  h->c_ready = false;
   return woodbury(h, V, sigma, g, delta, st);
 }
 
@@ -545,6 +565,18 @@ wssr_status wssr_sync(wssr_handle h) {
 }
 
 int64_t wssr_last_launch_count(wssr_handle h) { return h ? h->launches : -1; }
+
+wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n) {
+  if (!h || !out || n < 0) return WSSR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return WSSR_ERR_CUDA;
+  int dev_vals[2] = {0, 0};
+  if (cudaMemcpy(&dev_vals[0], h->nsweeps, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&dev_vals[1], h->status + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return WSSR_ERR_CUDA;
+  const int64_t vals[3] = {dev_vals[0], dev_vals[1], h->launches};
+  for (int i = 0; i < n && i < 3; ++i) out[i] = vals[i];
+  return WSSR_OK;
+}
 
 wssr_status wssr_profile_begin(wssr_handle h) {
   if (!h) return WSSR_ERR_INVALID_ARG;

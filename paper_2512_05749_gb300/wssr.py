@@ -37,7 +37,7 @@ EXPORTED = [
     "wssr_default_options", "wssr_create", "wssr_step", "wssr_init_subspace", "wssr_apply_O",
     "wssr_apply_Ot", "wssr_orthonormalize", "wssr_woodbury", "wssr_sync", "wssr_get_status",
     "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
-    "wssr_profile_end", "wssr_woodbury_noalloc",
+    "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats",
 ]
 
 KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply"]
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_profile_begin": (i32, [vp]),
         "wssr_profile_end": (i32, [vp, P(f64), P(i64), i32]),
         "wssr_woodbury_noalloc": (i32, [vp, vp, vp, vp, i64, i32, f64, i32, f64, vp]),
+        "wssr_get_stats": (i32, [vp, P(i64), i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +228,13 @@ def wssr_profile_end(h: int):
     return {KCAT_NAMES[i]: (ms[i], la[i]) for i in range(n)}
 
 
+def wssr_get_stats(h: int) -> dict:
+    """{'jacobi_sweeps', 'cholesky_shifts', 'launches'} of the last step (synchronises)."""
+    out = (ctypes.c_int64 * 3)()
+    _check(load().wssr_get_stats(h, out, 3), "wssr_get_stats")
+    return {"jacobi_sweeps": out[0], "cholesky_shifts": out[1], "launches": out[2]}
+
+
 def wssr_destroy(h: int):
     if h:
         load().wssr_destroy(h)
@@ -322,6 +330,9 @@ class WSSR:
 
     def last_launch_count(self) -> int:
         return wssr_last_launch_count(self.handle)
+
+    def stats(self) -> dict:
+        return wssr_get_stats(self.handle)
 
     def profile_begin(self):
         wssr_profile_begin(self.handle)
