@@ -210,18 +210,45 @@ __device__ __forceinline__ int pidx(int i, int j, int r) {  // i <= j
   return i * r - (i * (i - 1)) / 2 + (j - i);
 }
 
+// Blocked algorithm with 32 x 32 blocks (nb = ceil(r / 32) <= 8):
+//   factor:   for each K, one warp factors the diagonal block A_KK = R_KK^T R_KK
+//             and inverts it (T_KK); the panel R_KJ = T_KK^T A_KJ and the
+//             trailing update A_IJ -= R_KI^T R_KJ run as strip GEMMs on all
+//             threads;
+//   inverse:  block rows from the bottom, T_IJ = -T_II sum_{K=I+1..J} R_IK T_KJ.
+// Upper-triangle blocks are stored packed, each 32 x 33 floats; a partial last
+// block is padded with the identity (the Gram is equilibrated to unit diagonal).
+constexpr int CB = 32, CBP = 33, CBE = CB * CBP;
+
+__device__ __forceinline__ int blk_id(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
+
+// Strip GEMM task: acc[t] = sum_k L(k, i0 + t) * Rm[k][c] (LT) or
+// L[i0 + t][k] * Rm[k][c] (LN), t = 0..7, for 32 x 32 blocks.
+template <bool LT>
+__device__ __forceinline__ void strip(const float* L, const float* Rm, int i0, int c, float (&acc)[8]) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < CB; ++k) {
+    const float x = Rm[k * CBP + c];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = fmaf(LT ? L[k * CBP + i0 + t] : L[(i0 + t) * CBP + k], x, acc[t]);
+  }
+}
+
 __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int r,
                                                    float* __restrict__ T, int* status,
                                                    int* shift_count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* d = reinterpret_cast<double*>(smem_raw);
-  float* A = reinterpret_cast<float*>(smem_raw + sizeof(double) * 256);
+  const int nb = (r + CB - 1) / CB;
+  const int nblk = nb * (nb + 1) / 2;
+  double* d = reinterpret_cast<double*>(smem_raw);                 // 256 doubles
+  float* B = reinterpret_cast<float*>(smem_raw + 256 * sizeof(double));  // nblk blocks
+  float* TMP = B + (size_t)nblk * CBE;                               // nb - 1 blocks
+  float* TKK = TMP + (size_t)(nb - 1 > 0 ? nb - 1 : 1) * CBE;         // nb blocks
   __shared__ int flag;
-  __shared__ float tmp[256];
-  __shared__ int rb[256];  // packed row base: A[i][j] = A[rb[i] + j] for j >= i
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) flag = 0;
-  if (tid < r) rb[tid] = pidx(tid, 0, r);
   __syncthreads();
   if (tid < r) {
     const double gii = G[(int64_t)tid * r + tid];
@@ -236,33 +263,91 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     const float shift = attempt ? 1e-5f : 0.f;
-    for (int e = tid; e < r * r; e += 1024) {
-      const int i = e / r, j = e % r;
-      if (i <= j) {
-        const double g = G[e];
+    // load the equilibrated upper blocks; identity padding beyond r
+    for (int e = tid; e < nblk * CB * CB; e += 1024) {
+      const int bidx = e / (CB * CB), w = e % (CB * CB), i = w / CB, c = w % CB;
+      int I = 0, rem = bidx;
+      while (rem >= nb - I) rem -= nb - I, ++I;
+      const int J = I + rem;
+      const int gi = I * CB + i, gj = J * CB + c;
+      float v;
+      if (gi < r && gj < r) {
+        const double g = G[(int64_t)gi * r + gj];
         if (!isfinite(g)) flag = 2;
-        A[rb[i] + j] = (float)g * (float)d[i] * (float)d[j] + (i == j ? shift : 0.f);
+        v = (float)g * (float)d[gi] * (float)d[gj] + (gi == gj ? shift : 0.f);
+      } else {
+        v = (gi == gj) ? 1.f : 0.f;
       }
+      B[bidx * CBE + i * CBP + c] = v;
     }
     __syncthreads();
     if (flag == 2) break;
     if (tid == 0) flag = 0;
     __syncthreads();
-    for (int k = 0; k < r; ++k) {
-      const int bk = rb[k];
-      const float piv = A[bk + k];
-      if (!(piv > 1e-8f)) {  // uniform: every thread read the same value
-        if (tid == 0) flag = 1;
-        break;
+    for (int K = 0; K < nb; ++K) {
+      float* AKK = B + blk_id(K, K, nb) * CBE;
+      float* TK = TKK + K * CBE;
+      if (warp == 0) {
+        // lane j holds column j of the diagonal block (upper part)
+        float a[CB];
+#pragma unroll
+        for (int i = 0; i < CB; ++i) a[i] = AKK[i * CBP + lane];
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          const float piv = __shfl_sync(0xffffffffu, a[k], k);
+          bad |= !(piv > 1e-8f);
+          const float rho = sqrtf(fmaxf(piv, 1e-30f));
+          a[k] = (lane == k) ? rho : a[k] / rho;  // row k of R (valid for lanes >= k)
+          AKK[k * CBP + lane] = lane >= k ? a[k] : 0.f;
+          __syncwarp();
+#pragma unroll
+          for (int i = k + 1; i < CB; ++i) a[i] = fmaf(-AKK[k * CBP + i], a[k], a[i]);
+          __syncwarp();
+        }
+        // column j of T_KK = R_KK^-1 by back substitution (R read from smem)
+        float t[CB];
+#pragma unroll
+        for (int i = CB - 1; i >= 0; --i) {
+          float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+          for (int k = i + 1; k < CB; ++k) s = fmaf(-AKK[i * CBP + k], t[k], s);
+          t[i] = (i <= lane) ? s / AKK[i * CBP + i] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) TK[i * CBP + lane] = t[i];
+        if (lane == 0 && bad) flag = 1;
       }
-      const float rho = sqrtf(piv), inv = 1.f / rho;
       __syncthreads();
-      for (int j = k + tid; j < r; j += 1024) A[bk + j] = (j == k) ? rho : A[bk + j] * inv;
+      if (flag) break;
+      // panel: R_KJ = T_KK^T A_KJ  (into TMP slot J - K - 1)
+      const int np = nb - 1 - K;
+      for (int task = tid; task < np * 128; task += 1024) {
+        const int jb = task >> 7, w = task & 127, c = w & 31, i0 = (w >> 5) * 8;
+        float acc[8];
+        strip<true>(TK, B + blk_id(K, K + 1 + jb, nb) * CBE, i0, c, acc);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) TMP[jb * CBE + (i0 + t) * CBP + c] = acc[t];
+      }
       __syncthreads();
-      for (int i = k + 1 + warp; i < r; i += 32) {
-        const float aki = A[bk + i];
-        const int bi = rb[i];
-        for (int j = i + lane; j < r; j += 32) A[bi + j] -= aki * A[bk + j];
+      // trailing: A_IJ -= R_KI^T R_KJ for K < I <= J
+      const int ntr = np * (np + 1) / 2;
+      for (int task = tid; task < ntr * 128; task += 1024) {
+        const int tb = task >> 7, w = task & 127, c = w & 31, i0 = (w >> 5) * 8;
+        int ii = 0, rem = tb;
+        while (rem >= np - ii) rem -= np - ii, ++ii;
+        const int jj = ii + rem;  // TMP indices of R_KI, R_KJ
+        float acc[8];
+        strip<true>(TMP + ii * CBE, TMP + jj * CBE, i0, c, acc);
+        float* C = B + blk_id(K + 1 + ii, K + 1 + jj, nb) * CBE;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) C[(i0 + t) * CBP + c] -= acc[t];
+      }
+      __syncthreads();
+      // the panel becomes row K of R
+      for (int e = tid; e < np * CB * CB; e += 1024) {
+        const int jb = e / (CB * CB), w = e % (CB * CB), i = w / CB, c = w % CB;
+        B[blk_id(K, K + 1 + jb, nb) * CBE + i * CBP + c] = TMP[jb * CBE + i * CBP + c];
       }
       __syncthreads();
     }
@@ -277,52 +362,64 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
     if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
     return;
   }
-  // In-place inverse of the upper-triangular factor, one row at a time from
-  // the bottom: X[i][j] = (delta_ij - sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i].
-  // Four threads share each column j (r <= 256 columns, 1024 threads), each
-  // with four independent partial sums.
-  const int jcol = tid >> 2, q = tid & 3;
-  for (int i = r - 1; i >= 0; --i) {
-    float s = 0.f;
-    if (jcol < r && jcol > i) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      const int bi = rb[i];
-      int k = i + 1 + q;
-      for (; k + 12 <= jcol; k += 16) {
-        s0 = fmaf(A[bi + k], A[rb[k] + jcol], s0);
-        s1 = fmaf(A[bi + k + 4], A[rb[k + 4] + jcol], s1);
-        s2 = fmaf(A[bi + k + 8], A[rb[k + 8] + jcol], s2);
-        s3 = fmaf(A[bi + k + 12], A[rb[k + 12] + jcol], s3);
+  // inverse, block rows from the bottom: T_II = TKK[I]; T_IJ = -T_II S_IJ,
+  // S_IJ = sum_{K=I+1..J} R_IK T_KJ (rows K > I already hold T)
+  for (int I = nb - 1; I >= 0; --I) {
+    const int np = nb - 1 - I;
+    for (int task = tid; task < np * 128; task += 1024) {
+      const int jb = task >> 7, w = task & 127, c = w & 31, i0 = (w >> 5) * 8;
+      const int J = I + 1 + jb;
+      float acc[8], part[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+      for (int K = I + 1; K <= J; ++K) {
+        strip<false>(B + blk_id(I, K, nb) * CBE, B + blk_id(K, J, nb) * CBE, i0, c, part);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] += part[t];
       }
-      for (; k <= jcol; k += 4) s0 = fmaf(A[bi + k], A[rb[k] + jcol], s0);
-      s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) TMP[jb * CBE + (i0 + t) * CBP + c] = acc[t];
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (q == 0 && jcol < r && jcol >= i) tmp[jcol] = s;
     __syncthreads();
-    if (tid < r && tid >= i) {
-      const float rii = A[rb[i] + i];
-      A[rb[i] + tid] = (tid == i) ? 1.f / rii : -tmp[tid] / rii;
+    for (int task = tid; task < np * 128; task += 1024) {
+      const int jb = task >> 7, w = task & 127, c = w & 31, i0 = (w >> 5) * 8;
+      float acc[8];
+      strip<false>(TKK + I * CBE, TMP + jb * CBE, i0, c, acc);
+      float* C = B + blk_id(I, I + 1 + jb, nb) * CBE;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) C[(i0 + t) * CBP + c] = -acc[t];
+    }
+    for (int e = tid; e < CB * CB; e += 1024) {
+      const int i = e / CB, c = e % CB;
+      B[blk_id(I, I, nb) * CBE + i * CBP + c] = TKK[I * CBE + i * CBP + c];
     }
     __syncthreads();
   }
-  // T = D R'^-1 (rows scaled by d_i), full r x r with zeros below the diagonal.
+  // T = D T' (rows scaled by d_i), full r x r with zeros below the diagonal
   for (int e = tid; e < r * r; e += 1024) {
     const int i = e / r, j = e % r;
-    T[e] = (i <= j) ? A[rb[i] + j] * (float)d[i] : 0.f;
+    const int I = i / CB, J = j / CB;
+    T[e] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + (i % CB) * CBP + (j % CB)] * (float)d[i] : 0.f;
   }
 }
 }  // namespace
 
-size_t chol_inv_smem(int r) { return sizeof(double) * 256 + sizeof(float) * (size_t)r * (r + 1) / 2; }
+size_t chol_inv_smem(int r) {
+  const int nb = (r + CB - 1) / CB;
+  const int nblk = nb * (nb + 1) / 2;
+  const int ntmp = nb - 1 > 0 ? nb - 1 : 1;
+  return 256 * sizeof(double) + (size_t)(nblk + ntmp + nb) * CBE * sizeof(float);
+}
 
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
                      cudaStream_t st) {
   const size_t sm = chol_inv_smem(r);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // the largest request (r = 256); the kernel also has a few bytes of static shared memory
+    if (cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_inv_smem(256)) != cudaSuccess)
+      return;  // the error stays pending and is reported by the caller's launch check
     attr_set = true;
   }
   k_chol_inv<<<1, 1024, sm, st>>>(G, r, T, status, shift_count);
