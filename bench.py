@@ -195,6 +195,28 @@ def roofline_for(w, args, prof, steps, peaks, engine_name):
             "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
 
 
+def measured_traffic(w, kernel):
+    """dram read+write bytes per launch of `kernel` from the committed ncu summary
+    (profiles/roofline_traffic.txt), or None when the tcgen05 kernel source
+    changed since the capture or the workload is not the one it was scaled to."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2512_05749_gb300", "csrc", "tc_passes.cu")
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    kv = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and "=" in line:
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("tc_passes_sha") != sha:
+        return None
+    key = f"{kernel}_traffic_bytes_M{w.M}_N{w.N}_r{w.r}"
+    return float(kv[key]) if key in kv else None
+
+
 def step_roofline_ms(w, args, peaks):
     esz = 2 if args.dtype == "bf16" else 4
     passes = 2 * w.m + 1
@@ -305,6 +327,8 @@ def run_ours(args, w):
     peaks, src = load_peaks()
     roof = roofline_for(w, args, prof, args.steps, peaks, engine_name)
     roof["peak_source"] += f" ({src})"
+    if engine_name == "tcgen05":
+        roof["traffic"] = measured_traffic(w, roof["kernel"])
     step_roof = step_roofline_ms(w, args, peaks)
     s.close()
 

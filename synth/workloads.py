@@ -109,6 +109,11 @@ WORKLOADS = {
     "planted-n16384-m1m-r256": Planted(
         "planted-n16384-m1m-r256", N=16384, M=1_000_000, r=256, lam=1e-4, m=2, steps=20,
         sigma_power=1.2, K=1024, noise=1e-3, dtype="bf16"),
+    # Same shape family at 1/7.6 of the parameters (O = 4.3 GB, above L2): the
+    # case ncu captures of the O-pass kernels run on.
+    "planted-n16384-m131k-r256": Planted(
+        "planted-n16384-m131k-r256", N=16384, M=131_072, r=256, lam=1e-4, m=2, steps=20,
+        sigma_power=1.2, K=1024, noise=1e-3, dtype="bf16"),
     "mlp-75-256-256-1": MLPWorkload(
         "mlp-75-256-256-1", widths=(75, 256, 256, 1), N=4096, r=64, lam=1e-3, m=2, steps=20),
     "mlp-75-1024x3-1": MLPWorkload(
