@@ -204,6 +204,43 @@ wssr_status wssr_profile_begin(wssr_handle h);
  * and the number of kernel launches. Either output may be NULL. */
 wssr_status wssr_profile_end(wssr_handle h, double* ms, int64_t* launches, int32_t ncat);
 
+/* ---- Neural log-amplitude ansatz (rows of O from a per-sample backward pass) ----
+ * log|Psi_theta(x)| = f(x) for x = n_e electron positions (3 n_e floats):
+ * features h0 = [coordinates, |r_i - r_j| for i < j in lexicographic order]
+ * (widths[0] = 3 n_e + n_e (n_e - 1) / 2), hidden layers a_l = tanh(W_l a_{l-1} + b_l),
+ * scalar output f = W_L a_{L-1} + b_L (widths[L] = 1). Parameters theta (floats) in
+ * the order [W_1 (widths[1] x widths[0], row-major), b_1, ..., W_L, b_L]. The rows
+ * of the WSSR matrix O are the per-sample log-derivatives d f(x_n) / d theta
+ * (Section 2.2, Eq. (gradient:vmc); Section 3.1, Eq. (Osr)). Widths <= 1024. */
+#define WSSR_MLP_MAX_LAYERS 8
+typedef struct wssr_mlp_ctx* wssr_mlp_handle;
+typedef struct {
+  int32_t nlayers;                          /* L, number of weight layers (1..8) */
+  int32_t n_electrons;                      /* n_e >= 2 */
+  int32_t widths[WSSR_MLP_MAX_LAYERS + 1];  /* widths[0..L] */
+} wssr_mlp_desc;
+
+/* Number of parameters M, or -1 for an invalid description. */
+int64_t wssr_mlp_param_count(const wssr_mlp_desc* desc);
+
+/* Allocate the activation/adjoint workspace for up to N_max samples. */
+wssr_status wssr_mlp_create(const wssr_mlp_desc* desc, int64_t N_max, wssr_mlp_handle* out);
+void wssr_mlp_destroy(wssr_mlp_handle h);
+
+/* f[n] = log|Psi_theta(x_n)| for N samples x (N x 3 n_e floats). */
+wssr_status wssr_mlp_forward(wssr_mlp_handle h, const float* theta, const float* x, int64_t N,
+                             float* f, wssr_stream_t stream);
+
+/* The per-sample Jacobian O[n, :] = d f(x_n) / d theta into an N x ld block
+ * (ld >= M), float (o_dtype = WSSR_DTYPE_F32) or bf16 (WSSR_DTYPE_BF16). */
+wssr_status wssr_mlp_jacobian(wssr_mlp_handle h, const float* theta, const float* x, int64_t N,
+                              void* O, int64_t ld, int32_t o_dtype, wssr_stream_t stream);
+
+/* grad (M floats) = sum_n w[n] d f(x_n) / d theta, i.e. O^T w without forming O
+ * (the backward pass of f for the output cotangent w). */
+wssr_status wssr_mlp_vjp(wssr_mlp_handle h, const float* theta, const float* x, int64_t N,
+                         const float* w, float* grad, wssr_stream_t stream);
+
 /* Diagnostics of the last wssr_step / wssr_init_subspace (synchronises the
  * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz
  * eigensolve, out[1] = shifted Cholesky retries since wssr_create,

@@ -37,8 +37,11 @@ EXPORTED = [
     "wssr_default_options", "wssr_create", "wssr_step", "wssr_init_subspace", "wssr_apply_O",
     "wssr_apply_Ot", "wssr_orthonormalize", "wssr_woodbury", "wssr_sync", "wssr_get_status",
     "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
-    "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats",
+    "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
+    "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
 ]
+
+WSSR_MLP_MAX_LAYERS = 8
 
 KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply"]
 
@@ -63,6 +66,23 @@ class wssr_operator(ctypes.Structure):
         ("O", ctypes.c_void_p),
         ("ld", ctypes.c_int64),
     ]
+
+
+class wssr_mlp_desc(ctypes.Structure):
+    _fields_ = [
+        ("nlayers", ctypes.c_int32),
+        ("n_electrons", ctypes.c_int32),
+        ("widths", ctypes.c_int32 * (WSSR_MLP_MAX_LAYERS + 1)),
+    ]
+
+
+def mlp_desc(widths, n_electrons: int = 10) -> wssr_mlp_desc:
+    d = wssr_mlp_desc()
+    d.nlayers = len(widths) - 1
+    d.n_electrons = n_electrons
+    for i, w in enumerate(widths):
+        d.widths[i] = int(w)
+    return d
 
 
 class WSSRError(RuntimeError):
@@ -110,6 +130,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_profile_end": (i32, [vp, P(f64), P(i64), i32]),
         "wssr_woodbury_noalloc": (i32, [vp, vp, vp, vp, i64, i32, f64, i32, f64, vp]),
         "wssr_get_stats": (i32, [vp, P(i64), i32]),
+        "wssr_mlp_param_count": (i64, [P(wssr_mlp_desc)]),
+        "wssr_mlp_create": (i32, [P(wssr_mlp_desc), i64, P(vp)]),
+        "wssr_mlp_destroy": (None, [vp]),
+        "wssr_mlp_forward": (i32, [vp, vp, vp, i64, vp, vp]),
+        "wssr_mlp_jacobian": (i32, [vp, vp, vp, i64, vp, i64, i32, vp]),
+        "wssr_mlp_vjp": (i32, [vp, vp, vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +259,36 @@ def wssr_get_stats(h: int) -> dict:
     out = (ctypes.c_int64 * 3)()
     _check(load().wssr_get_stats(h, out, 3), "wssr_get_stats")
     return {"jacobi_sweeps": out[0], "cholesky_shifts": out[1], "launches": out[2]}
+
+
+def wssr_mlp_param_count(desc: wssr_mlp_desc) -> int:
+    return int(load().wssr_mlp_param_count(ctypes.byref(desc)))
+
+
+def wssr_mlp_create(desc: wssr_mlp_desc, N_max: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().wssr_mlp_create(ctypes.byref(desc), N_max, ctypes.byref(h)), "wssr_mlp_create")
+    return h.value
+
+
+def wssr_mlp_destroy(h: int):
+    if h:
+        load().wssr_mlp_destroy(h)
+
+
+def wssr_mlp_forward(h: int, theta, x, N: int, f, stream=None):
+    _check(load().wssr_mlp_forward(h, _ptr(theta), _ptr(x), N, _ptr(f), _stream(stream)),
+           "wssr_mlp_forward")
+
+
+def wssr_mlp_jacobian(h: int, theta, x, N: int, O, ld: int, o_dtype: int, stream=None):
+    _check(load().wssr_mlp_jacobian(h, _ptr(theta), _ptr(x), N, _ptr(O), ld, o_dtype,
+                                    _stream(stream)), "wssr_mlp_jacobian")
+
+
+def wssr_mlp_vjp(h: int, theta, x, N: int, w, grad, stream=None):
+    _check(load().wssr_mlp_vjp(h, _ptr(theta), _ptr(x), N, _ptr(w), _ptr(grad), _stream(stream)),
+           "wssr_mlp_vjp")
 
 
 def wssr_destroy(h: int):

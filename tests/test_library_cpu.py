@@ -76,3 +76,16 @@ def test_null_handle_calls_are_rejected():
     assert lib.wssr_step(None, None, None, None, None, None, None, None) == W.WSSR_ERR_INVALID_ARG
     assert lib.wssr_last_launch_count(None) == -1
     lib.wssr_destroy(None)
+
+
+def test_mlp_param_count_and_validation():
+    assert W.wssr_mlp_param_count(W.mlp_desc((75, 256, 256, 1), 10)) == 85_505
+    assert W.wssr_mlp_param_count(W.mlp_desc((75, 1024, 1024, 1024, 1), 10)) == 2_178_049
+    assert W.wssr_mlp_param_count(W.mlp_desc((18, 40, 24, 1), 4)) == 18 * 40 + 40 + 40 * 24 + 24 + 24 + 1
+    # features must match the electron count; output must be scalar; widths <= 1024
+    assert W.wssr_mlp_param_count(W.mlp_desc((74, 256, 1), 10)) == -1
+    assert W.wssr_mlp_param_count(W.mlp_desc((75, 256, 2), 10)) == -1
+    assert W.wssr_mlp_param_count(W.mlp_desc((75, 2048, 1), 10)) == -1
+    with pytest.raises(W.WSSRError) as ei:
+        W.wssr_mlp_create(W.mlp_desc((74, 256, 1), 10), 16)
+    assert ei.value.code == W.WSSR_ERR_INVALID_ARG
