@@ -242,7 +242,10 @@ def run_ours(args, w):
     # ---- inputs, resident in HBM before the timed region ----
     dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
     ld = w.M + ((-w.M) % 8)
-    O = wl.planted_O_torch(w, dev, out_dtype=dt, ld=ld)
+    master = None
+    if args.compare_f32 > 0 and args.dtype == "bf16":
+        master = torch.zeros((w.N, ld), dtype=torch.float32, device=dev)
+    O = wl.planted_O_torch(w, dev, out_dtype=dt, ld=ld, master=master)
     gs = [wl.gradient_torch(w.M, t, dev, "bench") for t in range(max(1, args.steps))]
     V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
     torch.cuda.synchronize()
@@ -324,6 +327,39 @@ def run_ours(args, w):
                "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
         del O_host
 
+    compare = None
+    if master is not None:
+        # the plain FP32 SIMT path on the FP32 master of the same matrix, same start
+        d_bf = delta.clone()
+        s32 = WSSR(w.N, w.M, w.r, w.lam, m=w.m, dtype="f32", engine="simt")
+        d32 = torch.empty_like(delta)
+        sg32 = torch.empty_like(sigma)
+        V32 = torch.empty_like(V)
+        Vin = Vb.clone()  # the start the last BF16 step used
+        s.step(O, gs[0], Vin, out=(delta, sigma, Vb))
+        d_bf = delta.clone()
+        s32.step(master, gs[0], Vin, out=(d32, sg32, V32))  # warm-up
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for t in range(args.compare_f32):
+            s32.step(master, gs[0], Vin, out=(d32, sg32, V32))
+        e5.record(stream)
+        torch.cuda.synchronize()
+        s32.check("fp32 steps")
+        ms32 = e4.elapsed_time(e5) / args.compare_f32
+        rel = float((d_bf.double() - d32.double()).norm() / d32.double().norm())
+        lr_bf = d_bf.double() - gs[0].double() / w.lam
+        lr_32 = d32.double() - gs[0].double() / w.lam
+        rel_lr = float((lr_bf - lr_32).norm() / lr_32.norm())
+        sig_rel = float(((sigma - sg32).abs() / sg32).max())
+        compare = {"fp32_simt_ms_per_step": ms32, "bf16_tcgen05_ms_per_step": ms_step,
+                   "speedup": ms32 / ms_step, "delta_rel_diff_bf16_vs_fp32": rel,
+                   "low_rank_part_rel_diff": rel_lr, "sigma_max_rel_diff": sig_rel,
+                   "steps": args.compare_f32}
+        s32.close()
+        del master
+
     peaks, src = load_peaks()
     roof = roofline_for(w, args, prof, args.steps, peaks, engine_name)
     roof["peak_source"] += f" ({src})"
@@ -351,9 +387,71 @@ def run_ours(args, w):
                           "model": f"{2 * w.m + 1} O passes x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
+        "bf16_vs_fp32": compare,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_mlp(args, w):
+    """Neural-ansatz workload: each step builds O with the per-sample Jacobian
+    kernel (fresh electron samples, FP32 or BF16 O) and runs one WSSR step on it."""
+    import torch
+
+    from paper_2512_05749_gb300 import WSSR
+    from paper_2512_05749_gb300.mlp import MLPAnsatz
+    from synth import workloads as wl
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ans = MLPAnsatz(w.widths, w.n_electrons, N_max=w.N)
+    theta = torch.from_numpy(wl.mlp_theta_np(w.widths, "bench").astype("float32")).to(dev)
+    xs = [wl.electrons_torch(w.N, dev, w.n_electrons, w.coord_std, "bench", t)
+          for t in range(args.steps + args.warmup + 1)]
+    dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    ld = w.M + ((-w.M) % 8)
+    O = torch.empty(w.N, ld, dtype=dt, device=dev)
+    g = wl.gradient_torch(w.M, 0, dev, "bench")
+    s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, dtype=args.dtype, engine=args.engine)
+    ans.per_sample_jacobian(theta, xs[0], out=O, dtype=args.dtype, ld=ld)
+    V, _ = s.init_subspace(O, wl.start_subspace_torch(w.M, w.r, dev, "bench"))
+    delta = torch.empty(w.M, device=dev)
+    sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
+    Vb = torch.empty_like(V)
+    for t in range(args.warmup):
+        ans.per_sample_jacobian(theta, xs[1 + t], out=O, dtype=args.dtype, ld=ld)
+        s.step(O, g, V, out=(delta, sigma, Vb))
+        V, Vb = Vb, V
+    s.check("warmup")
+    stream = torch.cuda.current_stream()
+    e0, e1, ej = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    jac_ms = 0.0
+    for t in range(args.steps):
+        ja, jb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ja.record(stream)
+        ans.per_sample_jacobian(theta, xs[1 + args.warmup + t], out=O, dtype=args.dtype, ld=ld)
+        jb.record(stream)
+        s.step(O, g, V, out=(delta, sigma, Vb))
+        V, Vb = Vb, V
+        torch.cuda.synchronize()
+        jac_ms += ja.elapsed_time(jb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.check("steps")
+    ms = e0.elapsed_time(e1) / args.steps
+    jac = jac_ms / args.steps
+    line = {"metric": "WSSR step ms (per-sample Jacobian of a tanh MLP + step)", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic",
+            "config": {"workload": w.name, "widths": list(w.widths), "N": w.N, "M": w.M, "r": w.r,
+                       "lambda": w.lam, "m": w.m, "o_bytes": w.N * ld * (2 if args.dtype == "bf16" else 4)},
+            "jacobian_ms_per_step": jac,
+            "jacobian_write_GBps": w.N * w.M * (2 if args.dtype == "bf16" else 4) / jac / 1e6}
+    print(json.dumps(line), flush=True)
+    s.close()
+    ans.close()
 
 
 def _uses_tc(s) -> bool:
@@ -380,9 +478,21 @@ def main():
     ap.add_argument("--m-init", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-cols", type=int, default=2048)
+    ap.add_argument("--compare-f32", type=int, default=0,
+                    help="also time this many steps of the plain FP32 (SIMT) path on the FP32 master "
+                         "of the same planted matrix and report the speedup and the delta difference")
     args = ap.parse_args()
     from synth import workloads as wl
     w = wl.WORKLOADS[args.workload]
+    if isinstance(w, wl.MLPWorkload):
+        if args.dtype is None:
+            args.dtype = "f32"
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined on the "
+                              "planted-matrix workloads"}))
+            return
+        run_mlp(args, w)
+        return
     if args.dtype is None:
         args.dtype = w.dtype
     if args.impl == "reference":
