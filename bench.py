@@ -4,8 +4,8 @@
 Default workload: planted-spectrum O with N=16384 samples, M=1,000,000
 parameters, rank r=256, lambda=1e-4, m=2 subspace iterations, O stored and
 multiplied in BF16 (33 GB resident in HBM). A "step" is one wssr_step call:
-m x (pass A, Cholesky QR of Y, pass B, CholeskyQR2 of Z), the Rayleigh-Ritz
-finish (one more pass A) and the Woodbury apply.
+m x (pass A, Cholesky QR of Y, pass B, Gram + r x r factor of the new
+basis), the Rayleigh-Ritz finish (one more pass A) and the Woodbury apply.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--dtype bf16|f32] [--engine auto|simt|tcgen05] [--impl ours|reference]
