@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["features", "unpack", "forward", "per_sample_jacobian", "param_count"]
+__all__ = ["features", "unpack", "forward", "adjoints", "per_sample_jacobian", "param_count"]
 
 
 def param_count(widths) -> int:
@@ -69,6 +69,23 @@ def forward(theta: np.ndarray, widths, x: np.ndarray):
         else:
             a = z
     return a[:, 0], acts
+
+
+def adjoints(theta: np.ndarray, widths, x: np.ndarray):
+    """[delta_1, ..., delta_L] per sample (delta_l = d f / d z_l, N x widths[l];
+    delta_L = 1), from the reverse-mode recursion above."""
+    layers = unpack(theta, widths)
+    _, acts = forward(theta, widths, x)
+    N = acts[0].shape[0]
+    L = len(layers)
+    out = [None] * L
+    delta = np.ones((N, 1))
+    for l in reversed(range(L)):
+        out[l] = delta
+        if l > 0:
+            W, _ = layers[l]
+            delta = (delta @ W) * (1.0 - acts[l] ** 2)
+    return out
 
 
 def per_sample_jacobian(theta: np.ndarray, widths, x: np.ndarray) -> np.ndarray:
