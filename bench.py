@@ -123,34 +123,57 @@ def cpu_sample(w, cols: int):
     return ws, O, g, V0
 
 
-def time_oracle(w, cols: int, steps: int = 1):
+def oracle_step_s(w, cols: int) -> float:
+    """Seconds of one oracle step on the `cols`-parameter sample of w."""
     from oracle import wssr_oracle as orc
     ws, O, g, V0 = cpu_sample(w, cols)
     Vp = orc.orth(V0)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        _, _, Vp = orc.wssr_step(O, g, Vp, w.lam, w.m)
-        times.append(time.perf_counter() - t0)
-    scale = w.M / cols
-    ms = [t * 1e3 * scale for t in times]
+    t0 = time.perf_counter()
+    orc.wssr_step(O, g, Vp, w.lam, w.m)
+    return time.perf_counter() - t0
+
+
+def linear_fit(t1: float, c1: int, t2: float, c2: int, M: int) -> float:
+    """t(M) from t = a + b cols through (c1, t1), (c2, t2): the oracle step has an
+    M-independent part (the N x r QR and the r x r Jacobi SVD of the
+    Rayleigh-Ritz finish) and a part linear in M (products, M x r QRs)."""
+    b = max(t2 - t1, 0.0) / (c2 - c1)
+    return t1 + b * (M - c1)
+
+
+def time_oracle(w, cols: int):
+    c2 = 4 * cols
+    t1, t2 = oracle_step_s(w, cols), oracle_step_s(w, c2)
+    ms = linear_fit(t1, cols, t2, c2, w.M) * 1e3
     return ms, {"kind": "oracle", "cores": os.cpu_count(),
-                "sample": f"N={w.N}, M={cols} of {w.M} parameters, r={w.r}, m={w.m}; "
-                          f"time x {scale:.1f} (cost linear in M)"}
+                "sample": f"N={w.N}, r={w.r}, m={w.m}; oracle steps on the first {cols} and {c2} of "
+                          f"{w.M} parameter columns ({t1:.1f} s, {t2:.1f} s), extrapolated linearly in M"}
 
 
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cols = args.cpu_cols
-    for _ in range(args.warmup if args.warmup <= 1 else 1):
-        time_oracle(w, cols, 1)
-    ms, info = time_oracle(w, cols, args.steps)
+    cols = max(w.r, args.cpu_cols // 4)
+    c2 = 4 * cols
+    if args.warmup > 0:
+        oracle_step_s(w, cols)
+    t2 = oracle_step_s(w, c2)
+    # K steps at the small sample, each extrapolated with the slope of the
+    # (cols, c2) pair; stops early (and says so) past ~4 minutes of oracle time
+    ms, t_start = [], time.perf_counter()
+    for _ in range(args.steps):
+        t1 = oracle_step_s(w, cols)
+        ms.append(linear_fit(t1, cols, t2, c2, w.M) * 1e3)
+        if time.perf_counter() - t_start > 240:
+            break
     v = sum(ms) / len(ms)
-    info["value"] = v
+    info = {"kind": "oracle", "cores": os.cpu_count(), "value": v,
+            "sample": f"N={w.N}, r={w.r}, m={w.m}; {len(ms)} oracle steps on {cols} of {w.M} parameter "
+                      f"columns, each extrapolated linearly in M with the slope from one step on {c2} "
+                      f"columns ({t2:.1f} s)"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "steps": len(ms), "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, args, "fp64 numpy oracle"),
             "cpu_baseline": info,
@@ -372,8 +395,8 @@ def run_ours(args, w):
         return
     cpu = None
     if world == 1 and args.cpu_cols > 0:
-        ms, info = time_oracle(w, args.cpu_cols, 1)
-        info["value"] = ms[0]
+        ms, info = time_oracle(w, max(w.r, args.cpu_cols // 4))
+        info["value"] = ms
         info["unit"] = "ms"
         cpu = info
     line = {
@@ -454,6 +477,210 @@ def run_mlp(args, w):
     ans.close()
 
 
+def mlp_cpu_sample(w, cols: int):
+    """Oracle time of one step of the network workload: the oracle's FP64
+    forward pass and adjoints of all N samples (timed whole), plus oracle steps
+    on two column samples of O (`cols` and 4 `cols` parameters spread evenly
+    over the weight blocks of every layer, built from those activations and
+    adjoints), extrapolated linearly in M."""
+    import numpy as np
+
+    from oracle import mlp_oracle as mo
+    from oracle import wssr_oracle as orc
+    from synth import workloads as wl
+    theta = wl.mlp_theta_np(w.widths, "bench").astype(np.float32).astype(np.float64)
+    x = wl.electrons_np(w.N, w.n_electrons, w.coord_std, "bench-cpu").astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    _, acts = mo.forward(theta, w.widths, x)
+    dl = mo.adjoints(theta, w.widths, x)
+    t_fb = time.perf_counter() - t0
+    L = len(w.widths) - 1
+
+    def step_s(c):
+        per = c // L
+        blocks = []
+        for l in range(L):
+            dout, din = w.widths[l + 1], w.widths[l]
+            flat = np.linspace(0, dout * din - 1, per).astype(np.int64)
+            blocks.append(dl[l][:, flat // din] * acts[l][:, flat % din])
+        O = np.concatenate(blocks, axis=1)
+        g = wl.gradient_np(O.shape[1], 0, "bench")
+        V0 = orc.orth(wl.start_subspace_np(O.shape[1], w.r, "bench"))
+        t = time.perf_counter()
+        orc.wssr_step(O, g, V0, w.lam, w.m)
+        return time.perf_counter() - t, O.shape[1]
+
+    (t1, c1), (t2, c2) = step_s(cols), step_s(4 * cols)
+    ms = (t_fb + linear_fit(t1, c1, t2, c2, w.M)) * 1e3
+    return ms, {"kind": "oracle", "cores": os.cpu_count(), "value": ms, "unit": "ms",
+                "sample": f"N={w.N}: oracle forward + adjoints of all samples ({t_fb:.1f} s) + oracle steps "
+                          f"on {c1} and {c2} of {w.M} parameter columns ({t1:.1f} s, {t2:.1f} s), "
+                          f"extrapolated linearly in M"}
+
+
+def run_mlp_mf(args, w):
+    """Matrix-free workload: each step recomputes the activations and adjoints
+    of fresh electron samples and runs one WSSR step with O applied on the
+    tensor cores from them (O never formed)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_05749_gb300 import WSSR
+    from paper_2512_05749_gb300.mlp import MLPAnsatz
+    from synth import workloads as wl
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ans = MLPAnsatz(w.widths, w.n_electrons, N_max=w.N)
+    theta = torch.from_numpy(wl.mlp_theta_np(w.widths, "bench").astype("float32")).to(dev)
+    nsteps = args.warmup + args.steps
+    xs = [wl.electrons_torch(w.N, dev, w.n_electrons, w.coord_std, "bench", t) for t in range(nsteps + 1)]
+    g_user = wl.gradient_torch(w.M, 0, dev, "bench")
+    g = ans.pad(g_user)
+    s = WSSR(w.N, ans.Mp, w.r, w.lam, m=w.m, m_init=args.m_init, dtype="bf16", engine="tcgen05")
+    V, _ = s.init_subspace(ans.operator(theta, xs[0]), ans.pad(wl.start_subspace_torch(w.M, w.r, dev, "bench")))
+    s.check("init_subspace")
+    delta = torch.empty(ans.Mp, device=dev)
+    sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
+    Vb = torch.empty_like(V)
+    for t in range(args.warmup):
+        s.step(ans.operator(theta, xs[1 + t]), g, V, out=(delta, sigma, Vb))
+        V, Vb = Vb, V
+    s.check("warmup")
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.profile_begin()
+    launches = 0
+    e0.record(stream)
+    for t in range(args.steps):
+        s.step(ans.operator(theta, xs[1 + args.warmup + t]), g, V, out=(delta, sigma, Vb))
+        launches += s.last_launch_count()
+        V, Vb = Vb, V
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = s.profile_end()
+    s.check("timed steps")
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # ---- end to end: theta and the samples from pinned host memory, delta (user order) back ----
+    e2e = None
+    if args.e2e_steps > 0:
+        th_host = theta.cpu().pin_memory()
+        x_host = [xs[t].cpu().pin_memory() for t in range(args.e2e_steps)]
+        d_host = torch.empty(w.M, pin_memory=True)
+        s_host = torch.empty(w.r, dtype=torch.float64, pin_memory=True)
+        th_dev, x_dev = torch.empty_like(theta), torch.empty_like(xs[0])
+        torch.cuda.synchronize()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for t in range(args.e2e_steps):
+            th_dev.copy_(th_host, non_blocking=True)
+            x_dev.copy_(x_host[t], non_blocking=True)
+            s.step(ans.operator(th_dev, x_dev), g, V, out=(delta, sigma, Vb))
+            V, Vb = Vb, V
+            d_host.copy_(ans.unpad(delta), non_blocking=True)
+            s_host.copy_(sigma, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        s.check("e2e")
+        e2e = {"value": e2.elapsed_time(e3) / args.e2e_steps, "unit": "ms",
+               "h2d_bytes_per_step": int(4 * w.M + xs[0].numel() * 4),
+               "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
+
+    compare = None
+    if args.compare_f32 > 0:
+        # materialised FP32 O (per-sample Jacobian kernel) + the plain FP32 SIMT
+        # step, from the same start on the same samples
+        Vin = Vb.clone()
+        x0 = xs[1 + args.warmup]
+        s.step(ans.operator(theta, x0), g, Vin, out=(delta, sigma, Vb))
+        d_mf = ans.unpad(delta).double()
+        sig_mf = sigma.clone()
+        ld = w.M + ((-w.M) % 8)
+        O32 = torch.empty(w.N, ld, dtype=torch.float32, device=dev)
+        s32 = WSSR(w.N, w.M, w.r, w.lam, m=w.m, dtype="f32", engine="simt")
+        V32in = ans.unpad(Vin)
+        d32 = torch.empty(w.M, device=dev)
+        sg32 = torch.empty_like(sigma)
+        V32 = torch.empty_like(V32in)
+        ans.per_sample_jacobian(theta, x0, out=O32, dtype="f32", ld=ld)
+        s32.step(O32, g_user, V32in, out=(d32, sg32, V32))
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for t in range(args.compare_f32):
+            ans.per_sample_jacobian(theta, x0, out=O32, dtype="f32", ld=ld)
+            s32.step(O32, g_user, V32in, out=(d32, sg32, V32))
+        e5.record(stream)
+        torch.cuda.synchronize()
+        s32.check("materialised fp32")
+        ms32 = e4.elapsed_time(e5) / args.compare_f32
+        rel = float((d_mf - d32.double()).norm() / d32.double().norm())
+        lr_mf = d_mf - g_user.double() / w.lam
+        lr_32 = d32.double() - g_user.double() / w.lam
+        compare = {"materialised_fp32_ms_per_step": ms32, "matrix_free_bf16_ms_per_step": ms_step,
+                   "speedup": ms32 / ms_step, "o_fp32_bytes": w.N * ld * 4,
+                   "delta_rel_diff_vs_materialised_fp32": rel,
+                   "low_rank_part_rel_diff": float((lr_mf - lr_32).norm() / lr_32.norm()),
+                   "sigma_max_rel_diff": float(((sig_mf - sg32).abs() / sg32).max()),
+                   "steps": args.compare_f32}
+        s32.close()
+        del O32
+
+    peaks, src = load_peaks()
+    flops = 2.0 * w.N * w.M * w.r
+    ms_a, n_a = prof["pass_A"]
+    ms_b, n_b = prof["pass_B"]
+    ta, tb = ms_a / max(1, n_a), ms_b / max(1, n_b)
+    name, t = ("pass_A (forward product, JVP)", ta) if ta >= tb else ("pass_B (reverse product, VJP)", tb)
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = flops / (t * 1e-3) / 1e12
+    roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "ms_per_launch": t, "algorithmic_per_launch": flops,
+            "peak_source": f"cuBLAS bf16 sustained ({src})",
+            "other_product": {"ms_per_launch": tb if t == ta else ta,
+                              "tflops": flops / ((tb if t == ta else ta) * 1e-3) / 1e12}}
+    passes = 2 * w.m + 1
+    step_roof = passes * flops / (peak * 1e12) * 1e3
+    s.close()
+    ans.close()
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and args.cpu_cols > 0:
+        _, cpu = mlp_cpu_sample(w, max(w.r, args.cpu_cols // 4))
+    line = {"metric": "WSSR step ms, matrix-free O (JVP/VJP on tcgen05) for a 2.2M-parameter tanh MLP",
+            "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": w.name, "widths": list(w.widths), "N": w.N, "M": w.M, "M_padded": ans.Mp,
+                       "r": w.r, "lambda": w.lam, "m": w.m, "engine": "tcgen05 matrix-free",
+                       "parallelism": f"replicas{world}",
+                       "l2": "operand source (activations+adjoints, ~104 MB bf16) is L2-resident by design; "
+                             "the basis blocks (1.1 GB) exceed L2"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
+                              "model": f"{passes} products x 2NMr / bf16 sustained peak"},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "vs_materialised_fp32": compare, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def _uses_tc(s) -> bool:
     from paper_2512_05749_gb300 import wssr as W
     import ctypes
@@ -481,6 +708,9 @@ def main():
     ap.add_argument("--compare-f32", type=int, default=0,
                     help="also time this many steps of the plain FP32 (SIMT) path on the FP32 master "
                          "of the same planted matrix and report the speedup and the delta difference")
+    ap.add_argument("--materialise", action="store_true",
+                    help="MLP workloads: form O with the per-sample Jacobian kernel instead of the "
+                         "matrix-free operator")
     args = ap.parse_args()
     from synth import workloads as wl
     w = wl.WORKLOADS[args.workload]
@@ -491,7 +721,10 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined on the "
                               "planted-matrix workloads"}))
             return
-        run_mlp(args, w)
+        if w.matrix_free and not args.materialise:
+            run_mlp_mf(args, w)
+        else:
+            run_mlp(args, w)
         return
     if args.dtype is None:
         args.dtype = w.dtype

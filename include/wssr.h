@@ -64,7 +64,7 @@ typedef enum {
 
 enum { WSSR_DTYPE_F32 = 0, WSSR_DTYPE_BF16 = 1 };
 enum { WSSR_APPLY_DAMPED = 0, WSSR_APPLY_CUTOFF = 1 };
-enum { WSSR_OP_DENSE = 0 };
+enum { WSSR_OP_DENSE = 0, WSSR_OP_MLP = 1 };
 /* Product engines for the two O passes. AUTO = tcgen05 tensor cores for
  * BF16 when the shape allows it, SIMT FMA otherwise. */
 enum { WSSR_ENGINE_AUTO = 0, WSSR_ENGINE_SIMT = 1, WSSR_ENGINE_TCGEN05 = 2 };
@@ -82,15 +82,29 @@ typedef struct {
   int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
 } wssr_options;
 
-/* O given as a dense matrix. O points to N rows of `ld` elements
- * (ld >= M; only the first M are read). For the tensor-core engine the
- * row pitch ld * sizeof(elem) must be a multiple of 16 bytes and O must be
- * 16-byte aligned. */
+struct wssr_mlp_ctx;
+
+/* The operator O of a step.
+ * WSSR_OP_DENSE: O points to N rows of `ld` elements (ld >= M; only the
+ *   first M are read). For the tensor-core engine the row pitch
+ *   ld * sizeof(elem) must be a multiple of 16 bytes and O 16-byte aligned.
+ * WSSR_OP_MLP (matrix-free: Section 4.2, Algorithm 1 touches O only through
+ *   the block products O X and O^T Y): O is the per-sample Jacobian of the network `mlp`
+ *   at parameters `theta` (device, user order) on the N samples `x` (device,
+ *   N x 3 n_e). It is never formed: each call recomputes the activations and
+ *   adjoints and applies O and O^T on the tensor cores from them. The handle
+ *   must use the tcgen05 engine (BF16) with M = wssr_mlp_padded_count(desc),
+ *   and every M-sized argument (g, V_prev, delta, V_out) lives in that padded
+ *   parameter space (wssr_mlp_pad / wssr_mlp_unpad convert); O has zero
+ *   columns at the padding positions. O and ld are ignored. */
 typedef struct {
-  int32_t kind;        /* WSSR_OP_DENSE */
+  int32_t kind;        /* WSSR_OP_DENSE or WSSR_OP_MLP */
   int32_t reserved;
-  const void* O;       /* device, N x ld, element type = options.dtype */
+  const void* O;       /* DENSE: device, N x ld, element type = options.dtype */
   int64_t ld;
+  struct wssr_mlp_ctx* mlp;  /* MLP: network handle (N <= its N_max) */
+  const float* theta;        /* MLP: parameters, wssr_mlp_param_count floats */
+  const float* x;            /* MLP: samples, N x 3 n_e floats */
 } wssr_operator;
 
 /* Fill `opt` with the defaults listed above. */
@@ -192,7 +206,8 @@ enum {
   WSSR_KCAT_ORTH = 2,   /* Gram, factor and apply kernels of Cholesky QR, casts, centring */
   WSSR_KCAT_RR = 3,     /* Rayleigh-Ritz Gram, Jacobi, rotations */
   WSSR_KCAT_APPLY = 4,  /* V^T g and the Woodbury apply */
-  WSSR_KCAT_COUNT = 5
+  WSSR_KCAT_SOURCE = 5, /* matrix-free operator: forward/backward pass of the network, packing */
+  WSSR_KCAT_COUNT = 6
 };
 
 /* Start recording an event pair around every kernel group enqueued on `h`
@@ -223,7 +238,12 @@ typedef struct {
 /* Number of parameters M, or -1 for an invalid description. */
 int64_t wssr_mlp_param_count(const wssr_mlp_desc* desc);
 
-/* Allocate the activation/adjoint workspace for up to N_max samples. */
+/* Parameter count of the padded parameter space of the matrix-free operator
+ * (each weight row and each bias block padded to a multiple of 64), or -1. */
+int64_t wssr_mlp_padded_count(const wssr_mlp_desc* desc);
+
+/* Allocate the activation/adjoint workspace for up to N_max samples, and the
+ * source/scale matrices and schedules of the matrix-free operator. */
 wssr_status wssr_mlp_create(const wssr_mlp_desc* desc, int64_t N_max, wssr_mlp_handle* out);
 void wssr_mlp_destroy(wssr_mlp_handle h);
 
@@ -240,6 +260,14 @@ wssr_status wssr_mlp_jacobian(wssr_mlp_handle h, const float* theta, const float
  * (the backward pass of f for the output cotangent w). */
 wssr_status wssr_mlp_vjp(wssr_mlp_handle h, const float* theta, const float* x, int64_t N,
                          const float* w, float* grad, wssr_stream_t stream);
+
+/* Row maps between the user parameter order (M rows) and the padded space
+ * (Mp = wssr_mlp_padded_count rows), for row-major blocks of `cols` floats:
+ * pad writes all Mp rows (zeros at padding positions); unpad gathers M rows. */
+wssr_status wssr_mlp_pad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst,
+                         wssr_stream_t stream);
+wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst,
+                           wssr_stream_t stream);
 
 /* Diagnostics of the last wssr_step / wssr_init_subspace (synchronises the
  * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz

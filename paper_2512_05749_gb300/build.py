@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwssr.so")
-SOURCES = ["wssr.cu", "simt_passes.cu", "small_ops.cu", "tc_passes.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["wssr.cu", "simt_passes.cu", "small_ops.cu", "tc_passes.cu", "tc_mlp.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

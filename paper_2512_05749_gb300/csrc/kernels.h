@@ -4,7 +4,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct wssr_mlp_ctx;
+
 namespace wssr {
+
+// ---- matrix-free MLP operator (mlp.cu, tc_mlp.cu) ----
+struct MlpSource {
+  const void* S;        // bf16 source matrix, N x Cs
+  int64_t Cs;
+  const void* ST;       // bf16 scale rows, nscale x ldst (samples contiguous)
+  int64_t ldst, nscale;
+  const int2* chunks;   // per 64-parameter chunk: {source column, scale row}
+  const int4* sched;    // forward order: {chunk, source column, scale row, 0}
+  const int4* groups;   // reverse groups: up to 4 chunks sharing a source tile
+  int64_t nchunks, ngroups;
+  int64_t Mp;           // padded parameter count (= 64 nchunks)
+};
+int64_t mlp_M(const wssr_mlp_ctx* h);
+int64_t mlp_Mp(const wssr_mlp_ctx* h);
+int64_t mlp_Nmax(const wssr_mlp_ctx* h);
+MlpSource mlp_source(const wssr_mlp_ctx* h);
+wssr_status mlp_prepare_source(wssr_mlp_ctx* h, const float* theta, const float* x, int64_t N,
+                               cudaStream_t st, int* launches);
+// Forward product Yp[split] = O_p Xhat over the padded space (Xhat K-blocked).
+int tc_mf_jvp_splits(int64_t N, int64_t nchunks, int r, int num_sms);
+int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, int splits, float* Yp,
+                     int64_t wait_us, int* status, cudaStream_t st, int* splits_used);
+// Reverse product Z = O_p^T Yhat - mu (1^T Yhat) over the padded space; mu
+// computed in the pass (compute_mu) or read from mu_io.
+int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t ldy, int r,
+                     const double* ysum, float* Z, void* ZT, float* mu_io, int compute_mu, int64_t wait_us,
+                     int* status, cudaStream_t st);
+
 
 // ---- O passes, SIMT engine (simt_passes.cu) ----
 template <typename T>

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -33,6 +34,33 @@ struct wssr_mlp_ctx {
   float* dels = nullptr;   // N_max x del_cols: delta_1 .. delta_{L-1}
   float* wtmp = nullptr;   // N_max x max width: weighted adjoints for the VJP
   int* meta = nullptr;     // per-layer metadata of the Jacobian writer (8 ints per layer)
+
+  // ---- matrix-free operator: padded parameter space ----
+  // Every weight row of layer l is padded from d_{l-1} to a multiple of 64
+  // and every bias block starts on a multiple of 64, so that each 64-parameter
+  // chunk of O is one 64-column tile of activations (or adjoints) scaled per
+  // sample by one adjoint column (or by 1). Padding parameters have zero
+  // columns in O.
+  int64_t Mp = 0;                       // padded parameter count (multiple of 64)
+  int64_t poff_w[WSSR_MLP_MAX_LAYERS] = {0}, poff_b[WSSR_MLP_MAX_LAYERS] = {0};
+  int dpad[WSSR_MLP_MAX_LAYERS + 1] = {0};  // widths rounded up to multiples of 64
+  // Source matrix S (bf16, N_max x Cs), zero padded:
+  //   [a_0 | a_1 | ... | a_{L-1} | delta_1 | ... | delta_{L-1} | (1, 0, ..., 0)]
+  int64_t Cs = 0;
+  int64_t s_act[WSSR_MLP_MAX_LAYERS] = {0}, s_del[WSSR_MLP_MAX_LAYERS + 1] = {0}, s_ones = 0;
+  bf16* S = nullptr;
+  // Scale matrix ST (bf16, nscale x ldst): row t_del[l] + i = delta_l[:, i]
+  // over the samples, last row all ones (chunks without a per-sample scale).
+  int64_t nscale = 0, ldst = 0, t_del[WSSR_MLP_MAX_LAYERS + 1] = {0}, t_ones = 0;
+  bf16* ST = nullptr;
+  int64_t nchunks = 0, ngroups = 0;
+  int2* chunks = nullptr;   // per chunk: {source column in S, scale row in ST}
+  int4* sched = nullptr;    // forward-product order: {chunk, source column, scale row, 0}, source-major
+  int4* groups = nullptr;   // reverse-product groups: up to 4 chunks sharing one source tile (-1 = empty)
+  int* pmap = nullptr;      // padded parameter -> user parameter index (or -1)
+  int* umap = nullptr;      // user parameter -> padded parameter index
+  int* segs = nullptr;      // packing segments of S (5 ints each)
+  int nseg = 0;
 };
 
 namespace {
@@ -208,6 +236,64 @@ __global__ void k_colsum_rows(const float* __restrict__ s, int64_t lds, int64_t 
   out[i] = (float)acc;
 }
 
+// S[n][col] for the activations/adjoints of one sample, bf16, zero padded.
+__global__ void k_pack_source(const float* __restrict__ acts, int64_t acols, const float* __restrict__ dels,
+                              int64_t dcols, int64_t N, const int* __restrict__ segs, int nseg,
+                              bf16* __restrict__ S, int64_t Cs) {
+  // segs: nseg x {dst column, src kind (0 acts, 1 dels, 2 ones), src column, width, padded width}
+  const int64_t n = blockIdx.x;
+  if (n >= N) return;
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int* q = segs + sg * 5;
+    const int dst = q[0], kind = q[1], src = q[2], w = q[3], pw = q[4];
+    for (int c = threadIdx.x; c < pw; c += blockDim.x) {
+      float v = 0.f;
+      if (kind == 2) v = (c == 0) ? 1.f : 0.f;
+      else if (c < w) v = kind == 0 ? acts[n * acols + src + c] : dels[n * dcols + src + c];
+      S[n * Cs + dst + c] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// ST[t_del[l] + i][n] = delta_l[n][i] (bf16) through a 32 x 32 shared tile;
+// rows of ST beyond the adjoints are written elsewhere.
+__global__ void k_pack_scales(const float* __restrict__ dels, int64_t dcols, int64_t N,
+                              bf16* __restrict__ ST, int64_t ldst) {
+  __shared__ float tile[32][33];
+  const int64_t n0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t n = n0 + y, c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (n < N && c < dcols) ? dels[n * dcols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + y, n = n0 + threadIdx.x;
+    if (c < dcols && n < N) ST[c * ldst + n] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
+}
+
+__global__ void k_fill_bf16(bf16* __restrict__ p, int64_t n, float v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_pad_rows(const float* __restrict__ src, int64_t cols, const int* __restrict__ pmap,
+                           int64_t Mp, float* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Mp * cols) return;
+  const int64_t p = e / cols, c = e % cols;
+  const int u = pmap[p];
+  dst[e] = u >= 0 ? src[(int64_t)u * cols + c] : 0.f;
+}
+
+__global__ void k_unpad_rows(const float* __restrict__ src, int64_t cols, const int* __restrict__ umap,
+                             int64_t M, float* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * cols) return;
+  const int64_t u = e / cols, c = e % cols;
+  dst[e] = src[(int64_t)umap[u] * cols + c];
+}
+
 bool valid_desc(const wssr_mlp_desc* d) {
   if (!d || d->nlayers < 1 || d->nlayers > WSSR_MLP_MAX_LAYERS || d->n_electrons < 2) return false;
   const int ne = d->n_electrons;
@@ -264,6 +350,103 @@ wssr_status run_forward_backward(wssr_mlp_ctx* h, const float* theta, const floa
   return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
 
+
+void mlp_free_mf(wssr_mlp_ctx* h) {
+  void* ptrs[] = {h->S, h->ST, h->chunks, h->sched, h->groups, h->pmap, h->umap, h->segs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Offsets of the padded parameter space and of the source and scale matrices.
+void mlp_layout(wssr_mlp_ctx* h) {
+  const int L = h->L;
+  const int* w = h->desc.widths;
+  int64_t po = 0;
+  for (int l = 0; l <= L; ++l) h->dpad[l] = (w[l] + 63) / 64 * 64;
+  for (int l = 1; l <= L; ++l) {
+    h->poff_w[l - 1] = po;
+    po += (int64_t)w[l] * h->dpad[l - 1];
+    h->poff_b[l - 1] = po;
+    po += h->dpad[l];
+  }
+  h->Mp = po;
+  h->nchunks = po / 64;
+  int64_t c = 0;
+  for (int l = 0; l < L; ++l) h->s_act[l] = c, c += h->dpad[l];
+  for (int l = 1; l < L; ++l) h->s_del[l] = c, c += h->dpad[l];
+  h->s_ones = c;
+  h->Cs = c + 64;
+  int64_t t = 0;
+  for (int l = 1; l < L; ++l) h->t_del[l] = t, t += w[l];
+  h->t_ones = t;
+  h->nscale = t + 1;
+  h->ldst = (h->N_max + 7) / 8 * 8;
+  // packing segments: {S column, kind (0 activation, 1 adjoint, 2 ones), source column, width, padded width}
+  h->nseg = 0;
+}
+
+// Host-built tables of the matrix-free operator, copied to the device.
+cudaError_t mlp_tables(wssr_mlp_ctx* h) {
+  const int L = h->L;
+  const int* w = h->desc.widths;
+  std::vector<int2> ch(h->nchunks, make_int2(-1, -1));
+  std::vector<int4> sched;
+  std::vector<int4> grp;
+  std::vector<int> pm(h->Mp, -1), um(h->M, 0);
+  sched.reserve(h->nchunks);
+  for (int l = 1; l <= L; ++l) {
+    const int dp = w[l - 1], dpp = h->dpad[l - 1], dout = w[l];
+    const int scale0 = l < L ? (int)h->t_del[l] : -1;
+    for (int q = 0; q < dpp / 64; ++q) {
+      const int src = (int)h->s_act[l - 1] + 64 * q;
+      for (int i = 0; i < dout; ++i) {
+        const int64_t c = (h->poff_w[l - 1] + (int64_t)i * dpp) / 64 + q;
+        const int sr = scale0 >= 0 ? scale0 + i : (int)h->t_ones;
+        ch[c] = make_int2(src, sr);
+        sched.push_back(make_int4((int)c, src, sr, 0));
+      }
+      // reverse-product groups: 4 rows i sharing the activation tile q (one
+      // per chunk when there is no per-sample scale: the output layer)
+      const int gsz = scale0 >= 0 ? 4 : 1;
+      for (int i = 0; i < dout; i += gsz) {
+        int cc[4] = {-1, -1, -1, -1};
+        for (int k = 0; k < gsz && i + k < dout; ++k) cc[k] = (int)((h->poff_w[l - 1] + (int64_t)(i + k) * dpp) / 64 + q);
+        grp.push_back(make_int4(cc[0], cc[1], cc[2], cc[3]));
+      }
+    }
+    for (int q = 0; q < h->dpad[l] / 64; ++q) {
+      const int64_t c = h->poff_b[l - 1] / 64 + q;
+      const int src = l < L ? (int)h->s_del[l] + 64 * q : (int)h->s_ones;
+      ch[c] = make_int2(src, (int)h->t_ones);
+      sched.push_back(make_int4((int)c, src, (int)h->t_ones, 0));
+      grp.push_back(make_int4((int)c, -1, -1, -1));
+    }
+    for (int i = 0; i < dout; ++i) {
+      for (int j = 0; j < dp; ++j) {
+        const int64_t pu = h->off_w[l - 1] + (int64_t)i * dp + j, pp = h->poff_w[l - 1] + (int64_t)i * dpp + j;
+        pm[pp] = (int)pu;
+        um[pu] = (int)pp;
+      }
+      const int64_t pu = h->off_b[l - 1] + i, pp = h->poff_b[l - 1] + i;
+      pm[pp] = (int)pu;
+      um[pu] = (int)pp;
+    }
+  }
+  h->ngroups = (int64_t)grp.size();
+  std::vector<int> sg;
+  for (int l = 0; l < L; ++l) sg.insert(sg.end(), {(int)h->s_act[l], 0, (int)h->act_off[l], w[l], h->dpad[l]});
+  for (int l = 1; l < L; ++l) sg.insert(sg.end(), {(int)h->s_del[l], 1, (int)h->del_off[l], w[l], h->dpad[l]});
+  sg.insert(sg.end(), {(int)h->s_ones, 2, 0, 1, 64});
+  h->nseg = (int)sg.size() / 5;
+  cudaError_t e = cudaMemcpy(h->chunks, ch.data(), ch.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->sched, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->groups, grp.data(), grp.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->pmap, pm.data(), pm.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->umap, um.data(), um.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->segs, sg.data(), sg.size() * sizeof(int), cudaMemcpyHostToDevice);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -307,6 +490,17 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
   if (e == cudaSuccess) e = cudaMalloc(&h->dels, (size_t)N_max * h->del_cols * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->wtmp, (size_t)N_max * wmax * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->meta, WSSR_MLP_MAX_LAYERS * 8 * sizeof(int));
+  // ---- padded parameter space, source and scale matrices, schedules ----
+  mlp_layout(h);
+  if (e == cudaSuccess) e = cudaMalloc(&h->S, (size_t)N_max * h->Cs * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ST, (size_t)h->nscale * h->ldst * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMalloc(&h->chunks, (size_t)h->nchunks * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMalloc(&h->sched, (size_t)h->nchunks * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMalloc(&h->groups, (size_t)h->nchunks * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMalloc(&h->pmap, (size_t)h->Mp * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->umap, (size_t)h->M * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->segs, (size_t)(2 * WSSR_MLP_MAX_LAYERS + 1) * 5 * sizeof(int));
+  if (e == cudaSuccess) e = mlp_tables(h);
   if (e == cudaSuccess) {
     int meta[WSSR_MLP_MAX_LAYERS * 8] = {0};
     layer_meta(h, meta);
@@ -318,6 +512,7 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
     if (h->dels) cudaFree(h->dels);
     if (h->wtmp) cudaFree(h->wtmp);
     if (h->meta) cudaFree(h->meta);
+    mlp_free_mf(h);
     delete h;
     return e == cudaErrorMemoryAllocation ? WSSR_ERR_OOM : WSSR_ERR_CUDA;
   }
@@ -332,7 +527,32 @@ void wssr_mlp_destroy(wssr_mlp_handle h) {
   cudaFree(h->dels);
   cudaFree(h->wtmp);
   cudaFree(h->meta);
+  mlp_free_mf(h);
   delete h;
+}
+
+int64_t wssr_mlp_padded_count(const wssr_mlp_desc* d) {
+  if (!valid_desc(d)) return -1;
+  int64_t Mp = 0;
+  for (int l = 1; l <= d->nlayers; ++l) {
+    const int64_t dpp = (d->widths[l - 1] + 63) / 64 * 64, dop = (d->widths[l] + 63) / 64 * 64;
+    Mp += (int64_t)d->widths[l] * dpp + dop;
+  }
+  return Mp;
+}
+
+wssr_status wssr_mlp_pad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst, wssr_stream_t stream) {
+  if (!h || !src || !dst || cols < 1) return WSSR_ERR_INVALID_ARG;
+  const int64_t n = h->Mp * cols;
+  k_pad_rows<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(src, cols, h->pmap, h->Mp, dst);
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
+wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst, wssr_stream_t stream) {
+  if (!h || !src || !dst || cols < 1) return WSSR_ERR_INVALID_ARG;
+  const int64_t n = h->M * cols;
+  k_unpad_rows<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(src, cols, h->umap, h->M, dst);
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
 
 wssr_status wssr_mlp_forward(wssr_mlp_handle h, const float* theta, const float* x, int64_t N, float* f,
@@ -386,3 +606,47 @@ wssr_status wssr_mlp_vjp(wssr_mlp_handle h, const float* theta, const float* x, 
 }
 
 }  // extern "C"
+
+// ---- internal interface of the matrix-free operator (used by wssr.cu) ----
+namespace wssr {
+
+int64_t mlp_M(const wssr_mlp_ctx* h) { return h->M; }
+int64_t mlp_Mp(const wssr_mlp_ctx* h) { return h->Mp; }
+int64_t mlp_Nmax(const wssr_mlp_ctx* h) { return h->N_max; }
+
+MlpSource mlp_source(const wssr_mlp_ctx* h) {
+  MlpSource s;
+  s.S = h->S;
+  s.Cs = h->Cs;
+  s.ST = h->ST;
+  s.ldst = h->ldst;
+  s.nscale = h->nscale;
+  s.chunks = h->chunks;
+  s.sched = h->sched;
+  s.groups = h->groups;
+  s.nchunks = h->nchunks;
+  s.ngroups = h->ngroups;
+  s.Mp = h->Mp;
+  return s;
+}
+
+// Recompute activations and adjoints of the N samples (forward and backward
+// pass from theta) and pack them into S and ST.
+wssr_status mlp_prepare_source(wssr_mlp_ctx* h, const float* theta, const float* x, int64_t N,
+                               cudaStream_t st, int* launches) {
+  if (N < 1 || N > h->N_max) return WSSR_ERR_INVALID_ARG;
+  // features, L layer GEMMs, last adjoint + L - 2 adjoint GEMMs, S, ST, ones row
+  *launches = 1 + h->L + (h->L > 1 ? h->L - 1 : 0) + 1 + (h->L > 1 ? 1 : 0) + 1;
+  wssr_status s = run_forward_backward(h, theta, x, N, true, st);
+  if (s != WSSR_OK) return s;
+  k_pack_source<<<(unsigned)N, 256, 0, st>>>(h->acts, h->act_cols, h->dels, h->del_cols, N, h->segs, h->nseg,
+                                             h->S, h->Cs);
+  if (h->L > 1) {
+    dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(h->t_ones, 32));
+    k_pack_scales<<<grid, dim3(32, 8), 0, st>>>(h->dels, h->del_cols, N, h->ST, h->ldst);
+  }
+  k_fill_bf16<<<(unsigned)ceil_div(h->ldst, 256), 256, 0, st>>>(h->ST + h->t_ones * h->ldst, h->ldst, 1.f);
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
+}  // namespace wssr

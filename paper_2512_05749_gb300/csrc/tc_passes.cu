@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace wssr {
 namespace {
@@ -49,172 +50,6 @@ struct Ctl {
   float ysum[256];
   double red[8][BM];
 };
-
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity to complete.
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns,
-                                       volatile int* abort_flag) {
-  if (mbar_test(b, parity)) return true;
-  const uint64_t t0 = gtimer();
-  for (;;) {
-    if (mbar_test(b, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > limit_ns) return false;
-  }
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
-      : "memory");
-}
-// Same copy with an L2 eviction-priority policy (from createpolicy).
-__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                                 int y, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(saddr(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar)), "l"(policy)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                                 int y, int z, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(saddr(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar)), "l"(policy)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
-      : "memory");
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          saddr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t x[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
-      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
-        "=r"(x[7]), "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]),
-        "=r"(x[14]), "=r"(x[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(x[i]);
-}
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-// Barrier over the 128 epilogue threads that also ANDs a per-thread flag.
-__device__ __forceinline__ bool epi_bar_and(bool v) {
-  uint32_t out;
-  asm volatile(
-      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, 1, 128, pi;\n"
-      " selp.u32 %0, 1, 0, po;\n}\n"
-      : "=r"(out)
-      : "r"((uint32_t)v)
-      : "memory");
-  return out != 0;
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (>> 4), version 1, 128-byte swizzle (layout type 2).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-  return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
-}
 
 __device__ __forceinline__ void timeout(Ctl* ctl, int* status) {
   *(volatile int*)&ctl->abort = 1;
@@ -719,6 +554,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+int nmma_for(int r) { return (r + 15) / 16 * 16; }
+int tmem_cols_for(int nmma) {
+  int c = 32;
+  while (c < nmma) c <<= 1;
+  return c;
+}
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
@@ -736,9 +588,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D bf16 tensor map: inner x outer elements, row pitch in bytes, box in elements.
+// 2D bf16 tensor map: inner x outer elements, row pitch in bytes, box in
+// elements; 128-byte swizzle (swizzle = true) or plain row-major boxes.
 bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
-               uint32_t box_inner, uint32_t box_outer) {
+               uint32_t box_inner, uint32_t box_outer, bool swizzle) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
@@ -746,7 +599,7 @@ bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, ui
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(g), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -763,34 +616,6 @@ bool encode_blocked(CUtensorMap* m, const void* g, int64_t L, int r, uint32_t bo
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-int nmma_for(int r) { return (r + 15) / 16 * 16; }
-int tmem_cols_for(int nmma) {
-  int c = 32;
-  while (c < nmma) c <<= 1;
-  return c;
-}
-int stages_for(int nmma) {
-  const size_t stage = A_BYTES + (size_t)nmma * BK * 2;
-  const size_t avail = 227 * 1024 - 1024 - sizeof(Ctl);
-  size_t s = avail / stage;
-  if (s > MAX_STAGES) s = MAX_STAGES;
-  return (int)s;
-}
-size_t smem_for(int nmma, int stages) {
-  return 1024 + (size_t)stages * (A_BYTES + (size_t)nmma * BK * 2) + sizeof(Ctl);
-}
-
-int64_t gcd64(int64_t a, int64_t b) {
-  while (b) {
-    int64_t t = a % b;
-    a = b;
-    b = t;
-  }
-  return a;
-}
-
-}  // namespace
 
 bool tc_supported(int dev) {
   int major = 0, minor = 0;
@@ -846,7 +671,7 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   }
   if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmX;
-  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, (uint32_t)(BM * MT))) return -1;
+  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, (uint32_t)(BM * MT), true)) return -1;
   if (!encode_blocked(&tmX, XhatT, M, r, (uint32_t)nmma)) return -1;
   const int k_chunks = (int)ceil_div(M, (int64_t)BK * KB);
   const int kc_per_split = (int)ceil_div(k_chunks, splits);
@@ -873,8 +698,8 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
   if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmY;
-  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, 64, BK)) return -1;
-  if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)nmma)) return -1;
+  if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, 64, BK, true)) return -1;
+  if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)nmma, true)) return -1;
   const size_t smem = 1024 + stages * stage + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
@@ -939,7 +764,7 @@ int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float
   if (!encode_blocked(&tmX, Xblk, M, r, 64)) return -1;
   for (int t = 0; t < 3; ++t) {
     CUtensorMap* mp = t == 0 ? &tmHi : (t == 1 ? &tmMid : &tmLo);
-    if (!encode_2d(mp, T3 + (size_t)t * r * r, (uint64_t)r, (uint64_t)r, (uint64_t)r * 2, BK, (uint32_t)NB))
+    if (!encode_2d(mp, T3 + (size_t)t * r * r, (uint64_t)r, (uint64_t)r, (uint64_t)r * 2, BK, (uint32_t)NB, true))
       return -1;
   }
   const size_t smem = 1024 + stages * stage + sizeof(Ctl);

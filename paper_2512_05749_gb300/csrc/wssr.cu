@@ -42,6 +42,7 @@ struct wssr_ctx {
   int64_t yp_elems = 0;
   int splits_simt = 1;
   int splits_tc = 1;           // pass A splits of the tcgen05 engine
+  int splits_mf = 1;           // forward-product splits of the matrix-free operator
   int64_t ldx = 0, ldy = 0;    // row pitch of the transposed bf16 operand copies
   bool mu_valid = false;       // tcgen05 pass B: mu of the current O already in h->mu
   float* Y = nullptr;
@@ -162,7 +163,11 @@ wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const void* Xop, float*
   int nsplit = 0;
   {
     Timed tm(h, WSSR_KCAT_PASS_A, st);
-    if (h->use_tc) {
+    if (op->kind == WSSR_OP_MLP) {
+      const MlpSource src = mlp_source(op->mlp);
+      int rc = tc_mf_jvp_launch(src, N, Xop, r, h->splits_mf, h->Yp, h->opt.wait_cap, h->status, st, &nsplit);
+      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+    } else if (h->use_tc) {
       int rc = tc_passA_launch(op->O, op->ld, N, M, Xop, h->ldx, r, h->splits_tc, h->Yp,
                                h->opt.wait_cap, h->status, st, &nsplit);
       if (rc != 0) return WSSR_ERR_UNSUPPORTED;
@@ -191,7 +196,14 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
   const int r = h->r;
   {
     Timed tm(h, WSSR_KCAT_PASS_B, st);
-    if (h->use_tc) {
+    if (op->kind == WSSR_OP_MLP) {
+      void* ZT = Zf ? nullptr : h->Xhat;
+      const MlpSource src = mlp_source(op->mlp);
+      int rc = tc_mf_vjp_launch(src, N, Yop, h->ldy, r, h->ysum, Zf, ZT, h->mu, h->mu_valid ? 0 : 1,
+                                h->opt.wait_cap, h->status, st);
+      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      h->mu_valid = true;
+    } else if (h->use_tc) {
       void* ZT = Zf ? nullptr : h->Xhat;
       int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Zf, ZT, h->ldx, h->mu,
                                h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st);
@@ -330,12 +342,30 @@ wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const flo
 }
 
 wssr_status check_op(const wssr_ctx* h, const wssr_operator* op) {
-  if (!op || op->kind != WSSR_OP_DENSE || !op->O || op->ld < h->M) return WSSR_ERR_INVALID_ARG;
+  if (!op) return WSSR_ERR_INVALID_ARG;
+  if (op->kind == WSSR_OP_MLP) {
+    if (!op->mlp || !op->theta || !op->x) return WSSR_ERR_INVALID_ARG;
+    if (mlp_Mp(op->mlp) != h->M || h->N > mlp_Nmax(op->mlp)) return WSSR_ERR_INVALID_ARG;
+    if (!h->use_tc) return WSSR_ERR_UNSUPPORTED;
+    return WSSR_OK;
+  }
+  if (op->kind != WSSR_OP_DENSE || !op->O || op->ld < h->M) return WSSR_ERR_INVALID_ARG;
   if (h->use_tc) {
     const size_t esz = 2;
     if (((uintptr_t)op->O) % 16 != 0 || ((size_t)op->ld * esz) % 16 != 0) return WSSR_ERR_INVALID_ARG;
   }
   return WSSR_OK;
+}
+
+// Matrix-free operator: recompute the activations and adjoints of the N
+// samples at theta (the operand source of both products) once per call.
+wssr_status prepare_op(wssr_ctx* h, const wssr_operator* op, cudaStream_t st) {
+  if (op->kind != WSSR_OP_MLP) return WSSR_OK;
+  Timed tm(h, WSSR_KCAT_SOURCE, st);
+  int n = 0;
+  const wssr_status s = mlp_prepare_source(op->mlp, op->theta, op->x, h->N, st, &n);
+  h->launches += n;
+  return s;
 }
 
 }  // namespace
@@ -397,10 +427,11 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   const size_t f = sizeof(float), d = sizeof(double);
   h->splits_simt = passA_simt_splits(N, M, r, h->num_sms);
   h->splits_tc = h->use_tc ? tc_passA_splits(N, M, r, h->num_sms) : 1;
+  h->splits_mf = (h->use_tc && M % 64 == 0) ? tc_mf_jvp_splits(N, M / 64, r, h->num_sms) : 1;
   h->ldx = (M + 7) / 8 * 8;
   h->ldy = (N + 7) / 8 * 8;
   // pass A partials: one N x r block per split
-  h->yp_elems = (int64_t)(h->use_tc ? h->splits_tc : h->splits_simt) * N * r;
+  h->yp_elems = (int64_t)std::max(h->use_tc ? h->splits_tc : h->splits_simt, h->splits_mf) * N * r;
   const int64_t blocks64 = ceil_div(std::max(N, M), 64);
   const int64_t gpart = std::max(gram_part_elems(N, r), gram_part_elems(M, r));
   cudaError_t e = cudaSuccess;
@@ -467,6 +498,7 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   h->last_stream = st;
   h->launches = 0;
   h->mu_valid = false;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g, st)) != WSSR_OK) return s;
   return woodbury(h, V_out, sigma, g, delta, st);
 }
@@ -479,7 +511,7 @@ wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const flo
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
-  // orthonormalise the random block first (Cholesky QR twice), then iterate
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   // orthonormalise the random block first (CholeskyQR2), then iterate
   cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
   cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
@@ -494,6 +526,7 @@ wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X,
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   const void* Xop = cast_X_operand(h, X, st);
   return pass_A(h, op, Xop, Y, st);
 }
@@ -506,6 +539,7 @@ wssr_status wssr_apply_Ot(wssr_handle h, const wssr_operator* op, const float* Y
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   h->launches = 0;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   const int64_t N = h->N;
   const int r = h->r;
   const void* Yop = Y;

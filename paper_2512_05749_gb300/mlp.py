@@ -24,6 +24,7 @@ class MLPAnsatz:
         self.M = W.wssr_mlp_param_count(self.desc)
         if self.M < 0:
             raise ValueError(f"invalid MLP description {self.widths} for {n_electrons} electrons")
+        self.Mp = W.wssr_mlp_padded_count(self.desc)
         self.N_max = N_max
         self.handle = W.wssr_mlp_create(self.desc, N_max)
 
@@ -72,8 +73,40 @@ class MLPAnsatz:
         W.wssr_mlp_vjp(self.handle, theta, x, x.shape[0], w.contiguous().float(), g)
         return g
 
+    def operator(self, theta, x) -> "MatrixFreeO":
+        """The matrix-free O at theta on the samples x, for a WSSR context
+        created with M = self.Mp and dtype "bf16" (padded parameter space)."""
+        theta, x = self._check_inputs(theta, x)
+        return MatrixFreeO(self, theta, x)
+
+    def pad(self, v):
+        """User-order rows (M or M x cols) -> padded space (Mp rows, zeros at padding)."""
+        v = v.contiguous().float()
+        cols = 1 if v.dim() == 1 else v.shape[1]
+        out = torch.empty((self.Mp,) + tuple(v.shape[1:]), device=v.device, dtype=torch.float32)
+        W.wssr_mlp_pad(self.handle, v, cols, out)
+        return out
+
+    def unpad(self, v):
+        """Padded-space rows (Mp or Mp x cols) -> user order (M rows)."""
+        v = v.contiguous().float()
+        cols = 1 if v.dim() == 1 else v.shape[1]
+        out = torch.empty((self.M,) + tuple(v.shape[1:]), device=v.device, dtype=torch.float32)
+        W.wssr_mlp_unpad(self.handle, v, cols, out)
+        return out
+
     def log_amplitude(self, theta, x):
         return LogAmplitude.apply(theta, x, self)
+
+
+class MatrixFreeO:
+    """O = d log|Psi| / d theta at (theta, x) as a WSSR operator (never formed)."""
+
+    def __init__(self, ansatz: MLPAnsatz, theta, x):
+        self.ansatz, self.theta, self.x = ansatz, theta, x  # keep the tensors alive
+
+    def wssr_operator(self):
+        return W.make_mlp_operator(self.ansatz.handle, self.theta, self.x)
 
 
 class LogAmplitude(torch.autograd.Function):

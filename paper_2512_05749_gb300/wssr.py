@@ -28,6 +28,7 @@ WSSR_DTYPE_BF16 = 1
 WSSR_APPLY_DAMPED = 0
 WSSR_APPLY_CUTOFF = 1
 WSSR_OP_DENSE = 0
+WSSR_OP_MLP = 1
 WSSR_ENGINE_AUTO = 0
 WSSR_ENGINE_SIMT = 1
 WSSR_ENGINE_TCGEN05 = 2
@@ -39,11 +40,12 @@ EXPORTED = [
     "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
     "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
+    "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
 
-KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply"]
+KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply", "source"]
 
 
 class wssr_options(ctypes.Structure):
@@ -65,6 +67,9 @@ class wssr_operator(ctypes.Structure):
         ("reserved", ctypes.c_int32),
         ("O", ctypes.c_void_p),
         ("ld", ctypes.c_int64),
+        ("mlp", ctypes.c_void_p),
+        ("theta", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
     ]
 
 
@@ -136,6 +141,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_mlp_forward": (i32, [vp, vp, vp, i64, vp, vp]),
         "wssr_mlp_jacobian": (i32, [vp, vp, vp, i64, vp, i64, i32, vp]),
         "wssr_mlp_vjp": (i32, [vp, vp, vp, i64, vp, vp, vp]),
+        "wssr_mlp_padded_count": (i64, [P(wssr_mlp_desc)]),
+        "wssr_mlp_pad": (i32, [vp, vp, i64, vp, vp]),
+        "wssr_mlp_unpad": (i32, [vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -179,6 +187,16 @@ def make_operator(O, ld: Optional[int] = None) -> wssr_operator:
     op.kind = WSSR_OP_DENSE
     op.O = _ptr(O)
     op.ld = int(ld if ld is not None else O.stride(0))
+    return op
+
+
+def make_mlp_operator(mlp_handle: int, theta, x) -> wssr_operator:
+    """Describe the matrix-free O of a network at theta on the samples x."""
+    op = wssr_operator()
+    op.kind = WSSR_OP_MLP
+    op.mlp = mlp_handle
+    op.theta = _ptr(theta)
+    op.x = _ptr(x)
     return op
 
 
@@ -291,6 +309,18 @@ def wssr_mlp_vjp(h: int, theta, x, N: int, w, grad, stream=None):
            "wssr_mlp_vjp")
 
 
+def wssr_mlp_padded_count(desc: wssr_mlp_desc) -> int:
+    return int(load().wssr_mlp_padded_count(ctypes.byref(desc)))
+
+
+def wssr_mlp_pad(h: int, src, cols: int, dst, stream=None):
+    _check(load().wssr_mlp_pad(h, _ptr(src), cols, _ptr(dst), _stream(stream)), "wssr_mlp_pad")
+
+
+def wssr_mlp_unpad(h: int, src, cols: int, dst, stream=None):
+    _check(load().wssr_mlp_unpad(h, _ptr(src), cols, _ptr(dst), _stream(stream)), "wssr_mlp_unpad")
+
+
 def wssr_destroy(h: int):
     if h:
         load().wssr_destroy(h)
@@ -329,6 +359,8 @@ class WSSR:
 
     def _op(self, O):
         import torch
+        if hasattr(O, "wssr_operator"):  # matrix-free operator (e.g. MLPAnsatz.operator)
+            return O.wssr_operator()
         want = torch.bfloat16 if self.dtype == "bf16" else torch.float32
         if O.dtype != want or not O.is_cuda or O.stride(1) != 1 or O.shape[0] != self.N:
             raise ValueError(f"O must be a CUDA {want} tensor of shape ({self.N}, >= {self.M}) "

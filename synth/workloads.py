@@ -89,6 +89,7 @@ class MLPWorkload:
     steps: int
     n_electrons: int = 10
     coord_std: float = 1.5
+    matrix_free: bool = False   # O applied from activations/adjoints, never formed
 
     @property
     def M(self) -> int:
@@ -118,7 +119,7 @@ WORKLOADS = {
         "mlp-75-256-256-1", widths=(75, 256, 256, 1), N=4096, r=64, lam=1e-3, m=2, steps=20),
     "mlp-75-1024x3-1": MLPWorkload(
         "mlp-75-1024x3-1", widths=(75, 1024, 1024, 1024, 1), N=8192, r=256, lam=1e-4, m=2,
-        steps=50),
+        steps=50, matrix_free=True),
 }
 
 

@@ -31,7 +31,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_options_layout_and_defaults():
     assert ctypes.sizeof(W.wssr_options) == 40
-    assert ctypes.sizeof(W.wssr_operator) == 24
+    assert ctypes.sizeof(W.wssr_operator) == 48
     opt = W.wssr_default_options()
     assert (opt.m, opt.m_init, opt.dtype, opt.apply_mode, opt.engine, opt.jacobi_sweeps) == \
         (2, 20, W.WSSR_DTYPE_F32, W.WSSR_APPLY_DAMPED, W.WSSR_ENGINE_AUTO, 12)
@@ -82,6 +82,15 @@ def test_mlp_param_count_and_validation():
     assert W.wssr_mlp_param_count(W.mlp_desc((75, 256, 256, 1), 10)) == 85_505
     assert W.wssr_mlp_param_count(W.mlp_desc((75, 1024, 1024, 1024, 1), 10)) == 2_178_049
     assert W.wssr_mlp_param_count(W.mlp_desc((18, 40, 24, 1), 4)) == 18 * 40 + 40 + 40 * 24 + 24 + 24 + 1
+    # padded space of the matrix-free operator: rows of W_l padded to 64 (d_{l-1} -> ceil64),
+    # bias blocks padded to 64
+    def padded(ws):
+        c = lambda v: -(-v // 64) * 64
+        return sum(ws[l + 1] * c(ws[l]) + c(ws[l + 1]) for l in range(len(ws) - 1))
+    for ws, ne in [((75, 1024, 1024, 1024, 1), 10), ((18, 40, 24, 1), 4), ((75, 130, 70, 1), 10), ((75, 1), 10)]:
+        assert W.wssr_mlp_padded_count(W.mlp_desc(ws, ne)) == padded(ws)
+    assert W.wssr_mlp_padded_count(W.mlp_desc((75, 1024, 1024, 1024, 1), 10)) == 2_232_384
+    assert W.wssr_mlp_padded_count(W.mlp_desc((75, 1024, 1), 9)) == -1
     # features must match the electron count; output must be scalar; widths <= 1024
     assert W.wssr_mlp_param_count(W.mlp_desc((74, 256, 1), 10)) == -1
     assert W.wssr_mlp_param_count(W.mlp_desc((75, 256, 2), 10)) == -1
