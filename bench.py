@@ -410,6 +410,7 @@ def run_ours(args, w):
                           "model": f"{2 * w.m + 1} O passes x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
+        "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
         "bf16_vs_fp32": compare,
         "cpu_baseline": cpu,
     }
@@ -571,6 +572,7 @@ def run_mlp_mf(args, w):
     clk = clocks.stop()
     prof = s.profile_end()
     s.check("timed steps")
+    stats = s.stats()
     ms_step = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t = torch.tensor([ms_step], device=dev)
@@ -677,6 +679,8 @@ def run_mlp_mf(args, w):
             "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
                               "model": f"{passes} products x 2NMr / bf16 sustained peak"},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
+            "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
             "vs_materialised_fp32": compare, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 

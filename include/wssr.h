@@ -272,7 +272,8 @@ wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, fl
 /* Diagnostics of the last wssr_step / wssr_init_subspace (synchronises the
  * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz
  * eigensolve, out[1] = shifted Cholesky retries since wssr_create,
- * out[2] = kernel launches it enqueued. Writes min(n, 3) values. */
+ * out[2] = kernel launches it enqueued, out[3 + s] = plane rotations applied
+ * in sweep s (0 past the last sweep). Writes n values (n >= 0). */
 wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n);
 
 /* Free the workspace (synchronises the device first). NULL is ignored. */

@@ -118,7 +118,7 @@ int64_t jacobi_log_elems(int r, int max_sweeps);
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
                    float* evals, int* status, cudaStream_t st);
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
-                           float* W, cudaStream_t st);
+                           int max_sweeps, float* W, cudaStream_t st);
 // c = V^T g (FP64), M x r V.
 int64_t dot_part_elems(int64_t M, int r);
 void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, double* c,

@@ -17,23 +17,53 @@ namespace wssr {
 // Split-K reduction and centring
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int RED_ROWS = 64;
+constexpr int RED_ROWS = 16;  // rows per CTA of the split reduction (one column-sum partial each)
 
-__global__ void k_reduce_splits(const float* __restrict__ Yp, int nsplit, int64_t N, int r,
-                                float* __restrict__ Y, double* __restrict__ csum_part) {
-  const int j = threadIdx.x;
-  const int64_t nb = (int64_t)blockIdx.x * RED_ROWS;
-  if (j >= r) return;
-  double cs = 0.0;
-  for (int i = 0; i < RED_ROWS; ++i) {
-    const int64_t n = nb + i;
-    if (n >= N) break;
-    float y = 0.f;
-    for (int s = 0; s < nsplit; ++s) y += Yp[((int64_t)s * N + n) * r + j];
-    Y[n * r + j] = y;
-    cs += (double)y;
+// Y = sum over splits of Yp[s]; thread = one float4 column group of one row
+// (r/4 threads per row, 256 / (r/4) rows in flight per CTA), split loads
+// unrolled 4 deep; per-CTA column sums in FP64 for the centring.
+__global__ void __launch_bounds__(256) k_reduce_splits(const float* __restrict__ Yp, int nsplit, int64_t N,
+                                                       int r, float* __restrict__ Y,
+                                                       double* __restrict__ csum_part) {
+  __shared__ double part[256 * 4];
+  const int tpr = r / 4;                 // threads per row
+  const int groups = 256 / tpr;          // rows processed at once
+  const int c4 = threadIdx.x % tpr, g = threadIdx.x / tpr;
+  const int64_t n0 = (int64_t)blockIdx.x * RED_ROWS;
+  const int64_t sstride = N * r / 4;
+  const float4* src = reinterpret_cast<const float4*>(Yp);
+  double cs[4] = {0.0, 0.0, 0.0, 0.0};
+  if (g < groups) {
+    for (int i = g; i < RED_ROWS; i += groups) {
+      const int64_t n = n0 + i;
+      if (n >= N) break;
+      const int64_t e = n * tpr + c4;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      int s = 0;
+      for (; s + 4 <= nsplit; s += 4) {
+        const float4 a = __ldg(src + e + (int64_t)s * sstride), b = __ldg(src + e + (int64_t)(s + 1) * sstride);
+        const float4 c = __ldg(src + e + (int64_t)(s + 2) * sstride), d = __ldg(src + e + (int64_t)(s + 3) * sstride);
+        acc.x += (a.x + b.x) + (c.x + d.x);
+        acc.y += (a.y + b.y) + (c.y + d.y);
+        acc.z += (a.z + b.z) + (c.z + d.z);
+        acc.w += (a.w + b.w) + (c.w + d.w);
+      }
+      for (; s < nsplit; ++s) {
+        const float4 a = __ldg(src + e + (int64_t)s * sstride);
+        acc.x += a.x, acc.y += a.y, acc.z += a.z, acc.w += a.w;
+      }
+      reinterpret_cast<float4*>(Y)[e] = acc;
+      cs[0] += acc.x, cs[1] += acc.y, cs[2] += acc.z, cs[3] += acc.w;
+    }
   }
-  csum_part[(int64_t)blockIdx.x * r + j] = cs;
+  for (int k = 0; k < 4; ++k) part[threadIdx.x * 4 + k] = (g < groups) ? cs[k] : 0.0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < r; j += 256) {
+    const int cj = j / 4, k = j % 4;
+    double t = 0.0;
+    for (int gg = 0; gg < groups; ++gg) t += part[(gg * tpr + cj) * 4 + k];
+    csum_part[(int64_t)blockIdx.x * r + j] = t;
+  }
 }
 
 __global__ void k_colsum_finalize(const double* __restrict__ part, int64_t nblocks, int r,
@@ -590,9 +620,62 @@ __global__ void __launch_bounds__(256) k_cast(const float* __restrict__ X, int64
 }
 }  // namespace
 
+namespace {
+// X (L x r float, row-major) -> K-blocked bf16 (blk_index): CTA = 64 rows x
+// 64 columns; float4 loads (a row's 64 columns = 256 contiguous bytes), a
+// transposed shared tile, and bf16x2 stores (a column's 64 rows = 128
+// contiguous bytes of the block). Rows past L in the last block are zeroed.
+__global__ void __launch_bounds__(256) k_cast_blocked(const float* __restrict__ X, int64_t L, int r,
+                                                      bf16* __restrict__ out) {
+  __shared__ float T[64][65];
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.x * 64;
+  const int j0 = blockIdx.y * 64;
+  const bool vec = (r % 4) == 0 && j0 + 64 <= r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int idx = tid + 256 * i;  // 1024 float4 of the tile
+    const int row = idx >> 4, c4 = idx & 15;
+    const int64_t m = m0 + row;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < L) {
+      if (vec) {
+        v = __ldg(reinterpret_cast<const float4*>(X + m * r + j0) + c4);
+      } else {
+        const int j = j0 + 4 * c4;
+        if (j < r) v.x = X[m * r + j];
+        if (j + 1 < r) v.y = X[m * r + j + 1];
+        if (j + 2 < r) v.z = X[m * r + j + 2];
+        if (j + 3 < r) v.w = X[m * r + j + 3];
+      }
+    }
+    T[4 * c4][row] = v.x;
+    T[4 * c4 + 1][row] = v.y;
+    T[4 * c4 + 2][row] = v.z;
+    T[4 * c4 + 3][row] = v.w;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int idx = tid + 256 * i;  // 2048 bf16 pairs
+    const int c = idx >> 5, pr = idx & 31;
+    const int j = j0 + c;
+    if (j < r) {  // rows past L inside the last block get zeros
+      const __nv_bfloat162 v = __floats2bfloat162_rn(T[c][2 * pr], T[c][2 * pr + 1]);
+      *reinterpret_cast<__nv_bfloat162*>(out + blk_index(m0 + 2 * pr, j, r)) = v;
+    }
+  }
+}
+}  // namespace
+
 void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf16, void* out_T,
                  int64_t ldT, double* colsum_part, cudaStream_t st) {
   if (!to_bf16 && !colsum_part) return;  // nothing to produce for the float engine
+  if (out_T && ldT == 0 && !out_rowmajor && !colsum_part && to_bf16) {
+    dim3 grid((unsigned)ceil_div(L, 64), (unsigned)ceil_div(r, 64));
+    k_cast_blocked<<<grid, 256, 0, st>>>(X, L, r, (bf16*)out_T);
+    return;
+  }
   dim3 grid((unsigned)ceil_div(L, 64), (unsigned)ceil_div(r, 64));
   k_cast<<<grid, 256, 0, st>>>(X, L, r, to_bf16, (bf16*)out_rowmajor, (bf16*)out_T, ldT, colsum_part);
 }
@@ -616,9 +699,12 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
                                                  float* __restrict__ evals, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);
+  // per-round rotation counts, stored after the rotation log
+  int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * (r - 1) * (r / 2));
   __shared__ float cs_c[128], cs_s[128], cs_t[128];
   __shared__ int pp[128], qq[128];
-  __shared__ int rb[256];  // packed row base: A[i][j] = A[rb[i] + j] for j >= i
+  __shared__ int act[128];  // indices of the pairs that rotate in this round
+  __shared__ int rb[256];   // packed row base: A[i][j] = A[rb[i] + j] for j >= i
   __shared__ int rot_round, rot_sweep, bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int h = r / 2;
@@ -649,7 +735,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     __syncthreads();
     for (int k = 0; k < r - 1; ++k) {
       if (tid == 0) rot_round = 0;
-      __syncthreads();
+      __syncthreads();  // also orders the previous round's reads of rot_round
       if (tid < h) {
         int p, q;
         rr_pair(k, tid, r, p, q);
@@ -667,21 +753,30 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
           t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
           c = rsqrtf(1.f + t * t);
           s = t * c;
-          rot_round = 1;  // benign race: every writer stores 1
         }
         cs_c[tid] = c;
         cs_s[tid] = s;
         cs_t[tid] = t;
+        if (s != 0.f) act[atomicAdd(&rot_round, 1)] = tid;
         rot_log[((int64_t)sweep * (r - 1) + k) * h + tid] = make_float2(c, s);
       }
       __syncthreads();
-      if (rot_round) {
+      const int nact = rot_round;
+      if (tid == 0) round_nact[sweep * (r - 1) + k] = nact;
+      if (nact) {
+        // Blocks (i1, i2), i1 <= i2, change only when pair i1 or pair i2
+        // rotates: a rotating i1 updates its whole block row; an idle i1 only
+        // the blocks of rotating pairs i2 > i1.
         // warp rows in a balanced order (w, 63-w, 64+w, 127-w, ... when h % 64 == 0)
         for (int t = 0; 32 * t + warp < h; ++t) {
           const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
           const int p1 = pp[i1], q1 = qq[i1];
           const float c1 = cs_c[i1], s1 = cs_s[i1];
-          for (int i2 = i1 + lane; i2 < h; i2 += 32) {
+          const bool full_row = s1 != 0.f;
+          const int n_inner = full_row ? h - i1 : nact;
+          for (int e = lane; e < n_inner; e += 32) {
+            const int i2 = full_row ? i1 + e : act[e];
+            if (!full_row && i2 <= i1) continue;
             if (i2 == i1) {
               const float t1 = cs_t[i1];
               const int ipq = AIX(p1, q1);
@@ -722,7 +817,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
 // Replays the logged rotations on rows of the identity (4 rows per CTA),
 // then writes W with columns sorted by descending eigenvalue.
 __global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* __restrict__ nsweeps,
-                                 const float* __restrict__ evals, int r, float* __restrict__ W) {
+                                 const float* __restrict__ evals, int r, int max_sweeps, float* __restrict__ W) {
   __shared__ float Wr[4][256];
   __shared__ int rank_of[256];
   const int tid = threadIdx.x;
@@ -744,7 +839,9 @@ __global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* 
   }
   __syncthreads();
   const int total = nsweeps[0] * (r - 1);
+  const int* round_nact = reinterpret_cast<const int*>(rot_log + (int64_t)max_sweeps * (r - 1) * h);
   for (int t = 0; t < total; ++t) {
+    if (round_nact[t] == 0) continue;  // uniform over the CTA
     const int k = t % (r - 1);
     int p, q;
     rr_pair(k, pi, r, p, q);
@@ -763,7 +860,10 @@ __global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* 
 }  // namespace
 
 size_t jacobi_smem(int r) { return sizeof(float) * (size_t)r * (r + 1) / 2; }
-int64_t jacobi_log_elems(int r, int max_sweeps) { return (int64_t)max_sweeps * (r - 1) * (r / 2); }
+// rotation log: max_sweeps x (r - 1) rounds x r/2 (c, s) pairs, then one int per round
+int64_t jacobi_log_elems(int r, int max_sweeps) {
+  return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + 1) / 2;
+}
 
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
                    float* evals, int* status, cudaStream_t st) {
@@ -777,9 +877,9 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
 }
 
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
-                           float* W, cudaStream_t st) {
+                           int max_sweeps, float* W, cudaStream_t st) {
   k_jacobi_vectors<<<(unsigned)ceil_div(r, 4), 4 * (r / 2), 0, st>>>((const float2*)rot_log, nsweeps,
-                                                                     evals, r, W);
+                                                                     evals, r, max_sweeps, W);
 }
 
 // ---------------------------------------------------------------------------

@@ -42,17 +42,22 @@ namespace wssr {
 namespace {
 
 constexpr int MF_THREADS = 320;
-constexpr int MF_MAX_STAGES = 4;
+constexpr int MF_MAX_RING = 4;
 constexpr uint32_t MF_A_SUB = 16384;  // one 128 x 64 bf16 operand tile (SW128 K-major or 2 MN-major boxes)
+// ring depths: TMA-fed inputs (basis / Yhat tiles, source tile, scale rows) and
+// transformed operand tiles
+constexpr int JVP_NX = 4, JVP_NA = 2;
+constexpr int VJP_NI = 3, VJP_NA = 3;
 
 struct MfCtl {
-  uint64_t loaded[MF_MAX_STAGES];
-  uint64_t full[MF_MAX_STAGES];
-  uint64_t empty[MF_MAX_STAGES];
+  uint64_t in_full[MF_MAX_RING];   // TMA bytes of an input slot landed
+  uint64_t in_empty[MF_MAX_RING];  // the MMAs reading an input slot retired
+  uint64_t a_full[MF_MAX_RING];    // the 8 transform warps wrote an operand slot
+  uint64_t a_empty[MF_MAX_RING];   // the MMAs reading an operand slot retired
   uint64_t accum;
   uint32_t tmem;
   int abort;
-  int src[MF_MAX_STAGES];  // forward product: source column of each stage's chunk
+  int src[MF_MAX_RING];  // forward product: source column of each input slot's chunk
 };
 
 __device__ __forceinline__ void mf_timeout(MfCtl* c, int* status) {
@@ -74,9 +79,7 @@ __device__ __forceinline__ void help_bar() { asm volatile("bar.sync 1, 256;" :::
 // Generic-proxy shared-memory writes -> visible to the tensor core (async proxy).
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Two packed bf16 values times s, rounded back to bf16 (round to nearest even).
-__device__ __forceinline__ uint32_t scale2(uint32_t w, float s) {
-  const float lo = __uint_as_float(w << 16) * s, hi = __uint_as_float(w & 0xFFFF0000u) * s;
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&p);
 }
@@ -88,46 +91,53 @@ __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, uint64_t
 }
 
 // Producer epilogue on abort: wait (bounded) for the copies already issued.
-__device__ __forceinline__ void drain_loads(MfCtl* ctl, int issued, int stages, uint64_t limit_ns) {
+__device__ __forceinline__ void drain_loads(MfCtl* ctl, int issued, int ring, uint64_t limit_ns) {
   int no_abort = 0;
-  const int j0 = issued > stages ? issued - stages : 0;
+  const int j0 = issued > ring ? issued - ring : 0;
   for (int j = j0; j < issued; ++j)
-    mbar_wait(&ctl->loaded[j % stages], (j / stages) & 1, limit_ns, (volatile int*)&no_abort);
+    mbar_wait(&ctl->in_full[j % ring], (j / ring) & 1, limit_ns, (volatile int*)&no_abort);
 }
 
-__device__ __forceinline__ void mf_init(MfCtl* ctl, int stages) {
-  for (int s = 0; s < stages; ++s) {
-    mbar_init(&ctl->loaded[s], 1);
-    mbar_init(&ctl->full[s], 8);
-    mbar_init(&ctl->empty[s], 1);
+__device__ __forceinline__ void mf_init(MfCtl* ctl, int n_in, int n_a) {
+  for (int s = 0; s < n_in; ++s) {
+    mbar_init(&ctl->in_full[s], 1);
+    mbar_init(&ctl->in_empty[s], 1);
+  }
+  for (int s = 0; s < n_a; ++s) {
+    mbar_init(&ctl->a_full[s], 8);
+    mbar_init(&ctl->a_empty[s], 1);
   }
   mbar_init(&ctl->accum, 1);
   ctl->abort = 0;
   fence_barrier_init();
 }
 
+__host__ __device__ constexpr uint32_t round1k(uint32_t b) { return (b + 1023u) & ~1023u; }
+
 // ---------------------------------------------------------------------------
-// Forward product. Stage: [A: 2 x 16 KB, K-major SW128, rows = samples]
-// [Xhat block: nmma rows x 128 B, K-major SW128][scale row: 256 bf16].
-// CTA = 256 samples (two accumulators) x one split of the chunk schedule.
+// Forward product. Input slot: [Xhat block: nmma rows x 128 B, K-major SW128]
+// [scale row: 256 bf16]; operand slot: [A: 2 x 16 KB, K-major SW128, rows =
+// samples]. CTA = 256 samples (two accumulators) x one split of the chunk
+// schedule.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(MF_THREADS, 1)
     k_mf_jvp(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT,
              const bf16* __restrict__ S, int64_t Cs, const int4* __restrict__ sched, int64_t N, int r,
-             int nmma, int stages, int n_tiles, int splits, int nchunks, int per_split,
-             float* __restrict__ Yp, uint64_t limit_ns, int* status) {
+             int nmma, int n_tiles, int nchunks, int per_split, float* __restrict__ Yp, uint64_t limit_ns,
+             int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t xbytes = (uint32_t)nmma * 128;
-  const uint32_t stage_bytes = (2 * MF_A_SUB + xbytes + 512 + 1023) & ~1023u;
-  MfCtl* ctl = reinterpret_cast<MfCtl*>(base + (size_t)stages * stage_bytes);
+  const uint32_t in_bytes = round1k(xbytes + 512);
+  uint8_t* a_base = base + (size_t)JVP_NX * in_bytes;
+  MfCtl* ctl = reinterpret_cast<MfCtl*>(a_base + (size_t)JVP_NA * 2 * MF_A_SUB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the n_tiles sample tiles of one split are consecutive CTAs (they share the Xhat blocks in L2)
   const int n_tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int k0 = split * per_split;
   const int nk = max(min(k0 + per_split, nchunks) - k0, 0);
   const int64_t n0 = (int64_t)n_tile * 256;
-  if (threadIdx.x == 0) mf_init(ctl, stages);
+  if (threadIdx.x == 0) mf_init(ctl, JVP_NX, JVP_NA);
   if (warp == 1) tmem_alloc(&ctl->tmem, 512u);
   tc_fence_before();
   __syncthreads();
@@ -140,94 +150,102 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
       int issued = 0;
       int4 nxt = sched[k0];
       for (int i = 0; i < nk; ++i) {
-        const int s = i % stages, u = i / stages;
+        const int s = i % JVP_NX, u = i / JVP_NX;
         const int4 e = nxt;
         if (i + 1 < nk) nxt = sched[k0 + i + 1];
-        if (u > 0 && !mbar_wait(&ctl->empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
+        if (u > 0 && !mbar_wait(&ctl->in_empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
           mf_timeout(ctl, status);
           break;
         }
-        uint8_t* st = base + (size_t)s * stage_bytes;
+        uint8_t* st = base + (size_t)s * in_bytes;
         ctl->src[s] = e.y;  // published by the arrive below (release)
-        mbar_expect_tx(&ctl->loaded[s], xbytes + 512);
-        tma_load_3d_hint(st + 2 * MF_A_SUB, &tmX, &ctl->loaded[s], 0, 0, e.x, pol_x);
-        tma_load_2d(st + 2 * MF_A_SUB + xbytes, &tmT, &ctl->loaded[s], (int)n0, e.z);
+        mbar_expect_tx(&ctl->in_full[s], xbytes + 512);
+        tma_load_3d_hint(st, &tmX, &ctl->in_full[s], 0, 0, e.x, pol_x);
+        tma_load_2d(st + xbytes, &tmT, &ctl->in_full[s], (int)n0, e.z);
         issued = i + 1;
       }
-      if (ctl->abort) drain_loads(ctl, issued, stages, limit_ns);
+      if (ctl->abort) drain_loads(ctl, issued, JVP_NX, limit_ns);
     }
   } else if (warp == 1) {
     if (lane == 0 && nk > 0) {
       const uint32_t idesc = make_idesc(128, nmma, 0, 0);
       for (int i = 0; i < nk; ++i) {
-        const int s = i % stages, u = i / stages;
-        if (!mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort) ||
-            !mbar_wait(&ctl->loaded[s], u & 1, limit_ns, &ctl->abort)) {
+        const int sx = i % JVP_NX, sa = i % JVP_NA;
+        if (!mbar_wait(&ctl->a_full[sa], (i / JVP_NA) & 1, limit_ns, &ctl->abort) ||
+            !mbar_wait(&ctl->in_full[sx], (i / JVP_NX) & 1, limit_ns, &ctl->abort)) {
           mf_timeout(ctl, status);
           break;
         }
         tc_fence_after();
-        const uint32_t sa = saddr(base + (size_t)s * stage_bytes);
+        const uint32_t xa = saddr(base + (size_t)sx * in_bytes);
+        const uint32_t aa = saddr(a_base + (size_t)sa * 2 * MF_A_SUB);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t db = smem_desc(sa + 2 * MF_A_SUB + kk * 32, 16, 1024);
+          const uint64_t db = smem_desc(xa + kk * 32, 16, 1024);
 #pragma unroll
           for (int a = 0; a < 2; ++a)
-            mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + a * MF_A_SUB + kk * 32, 16, 1024), db, idesc,
+            mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(aa + a * MF_A_SUB + kk * 32, 16, 1024), db, idesc,
                      (i > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&ctl->empty[s]);
+        mma_commit(&ctl->in_empty[sx]);
+        mma_commit(&ctl->a_empty[sa]);
       }
       mma_commit(&ctl->accum);
       int no_abort = 0;
       mbar_wait(&ctl->accum, 0, limit_ns, (volatile int*)&no_abort);
     }
   } else {
-    // ---- transform: row ht of the 256-sample tile ----
+    // ---- transform: row ht of the 256-sample tile, source row kept in FP32 registers ----
     const int ht = threadIdx.x - 64;
     const int64_t n = n0 + ht;
     const bool vrow = n < N;
     const int a = ht >> 7, R = ht & 127;
-    uint32_t row[32];
+    float row[64];
     int cur = -1;
     bool ok_loop = true;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % stages, u = i / stages;
-      if (!warp_wait(&ctl->loaded[s], u & 1, limit_ns, &ctl->abort)) {
+      const int sx = i % JVP_NX, sa = i % JVP_NA;
+      if ((i >= JVP_NA && !warp_wait(&ctl->a_empty[sa], ((i / JVP_NA) - 1) & 1, limit_ns, &ctl->abort)) ||
+          !warp_wait(&ctl->in_full[sx], (i / JVP_NX) & 1, limit_ns, &ctl->abort)) {
         if (lane == 0) mf_timeout(ctl, status);
         ok_loop = false;
         break;
       }
-      uint8_t* st = base + (size_t)s * stage_bytes;
-      const int src = ctl->src[s];
+      const uint8_t* xs = base + (size_t)sx * in_bytes;
+      const int src = ctl->src[sx];
       if (src != cur) {
         if (vrow) {
           const uint4* p = reinterpret_cast<const uint4*>(S + n * Cs + src);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const uint4 v = __ldg(p + k);
-            row[4 * k] = v.x, row[4 * k + 1] = v.y, row[4 * k + 2] = v.z, row[4 * k + 3] = v.w;
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              row[8 * k + 2 * e] = __uint_as_float(w[e] << 16);
+              row[8 * k + 2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+            }
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 32; ++k) row[k] = 0u;
+          for (int k = 0; k < 64; ++k) row[k] = 0.f;
         }
         cur = src;
       }
-      const float sc = __bfloat162float(reinterpret_cast<const bf16*>(st + 2 * MF_A_SUB + xbytes)[ht]);
-      uint8_t* arow = st + a * MF_A_SUB + R * 128;
+      const float sc = __bfloat162float(reinterpret_cast<const bf16*>(xs + nmma * 128)[ht]);
+      uint8_t* arow = a_base + (size_t)sa * 2 * MF_A_SUB + a * MF_A_SUB + R * 128;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         uint4 o;
-        o.x = scale2(row[4 * k], sc);
-        o.y = scale2(row[4 * k + 1], sc);
-        o.z = scale2(row[4 * k + 2], sc);
-        o.w = scale2(row[4 * k + 3], sc);
+        o.x = pack_bf16x2(row[8 * k] * sc, row[8 * k + 1] * sc);
+        o.y = pack_bf16x2(row[8 * k + 2] * sc, row[8 * k + 3] * sc);
+        o.z = pack_bf16x2(row[8 * k + 4] * sc, row[8 * k + 5] * sc);
+        o.w = pack_bf16x2(row[8 * k + 6] * sc, row[8 * k + 7] * sc);
         *reinterpret_cast<uint4*>(arow + ((k ^ (R & 7)) << 4)) = o;
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->full[s]);
+      if (lane == 0) mbar_arrive(&ctl->a_full[sa]);
     }
     // ---- epilogue: warps 2-5 drain accumulator 0, warps 6-9 accumulator 1 ----
     const int q = warp & 3, acc = (warp - 2) >> 2;
@@ -259,31 +277,35 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Reverse product. Stage: [A: 4 boxes of 64 samples x 64 parameters, MN-major
-// SW128, 8 KB apart][Yhat^T tile: nmma rows x 64 samples, K-major SW128]
-// [source tile: 64 samples x 64 columns of S, SW128][4 scale rows: 64 bf16].
-// CTA = one group of up to 4 chunks sharing the source tile, all samples.
+// Reverse product. Input slot: [Yhat^T tile: nmma rows x 64 samples, K-major
+// SW128][source tile: 64 samples x 64 columns of S, SW128][4 scale rows: 64
+// bf16]; operand slot: [A: 4 boxes of 64 samples x 64 parameters, MN-major
+// SW128, 8 KB apart]. CTA = one group of up to 4 chunks sharing the source
+// tile, all samples. Transform thread = (sample row, quarter of the 64
+// columns): it reads its 16 source values once and writes them under each of
+// the 4 chunk scales.
 // ---------------------------------------------------------------------------
 template <bool WITH_MU>
 __global__ void __launch_bounds__(MF_THREADS, 1)
     k_mf_vjp(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmT,
              const __grid_constant__ CUtensorMap tmY, const int2* __restrict__ chunks,
-             const int4* __restrict__ groups, int64_t N, int r, int nmma, int stages,
-             const double* __restrict__ ysum, float* __restrict__ Z, bf16* __restrict__ ZT,
-             float* __restrict__ mu_io, uint64_t limit_ns, int* status) {
+             const int4* __restrict__ groups, int64_t N, int r, int nmma, const double* __restrict__ ysum,
+             float* __restrict__ Z, bf16* __restrict__ ZT, float* __restrict__ mu_io, uint64_t limit_ns,
+             int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t ybytes = (uint32_t)nmma * 128;
-  const uint32_t off_y = 4 * 8192, off_s = off_y + ybytes, off_t = off_s + 8192;
-  const uint32_t stage_bytes = (off_t + 512 + 1023) & ~1023u;
-  MfCtl* ctl = reinterpret_cast<MfCtl*>(base + (size_t)stages * stage_bytes);
+  const uint32_t off_s = ybytes, off_t = off_s + 8192;
+  const uint32_t in_bytes = round1k(off_t + 512);
+  uint8_t* a_base = base + (size_t)VJP_NI * in_bytes;
+  MfCtl* ctl = reinterpret_cast<MfCtl*>(a_base + (size_t)VJP_NA * 4 * 8192);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 grp = groups[blockIdx.x];
   const int cid[4] = {grp.x, grp.y, grp.z, grp.w};
   const int nvalid = (cid[0] >= 0) + (cid[1] >= 0) + (cid[2] >= 0) + (cid[3] >= 0);
   const bool act1 = cid[2] >= 0;  // second accumulator (boxes 2, 3) in use
   const int nk = (int)ceil_div(N, 64);
-  if (threadIdx.x == 0) mf_init(ctl, stages);
+  if (threadIdx.x == 0) mf_init(ctl, VJP_NI, VJP_NA);
   if (warp == 1) tmem_alloc(&ctl->tmem, 512u);
   tc_fence_before();
   __syncthreads();
@@ -299,105 +321,113 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
       for (int b = 0; b < 4; ++b) srow[b] = cid[b] >= 0 ? chunks[cid[b]].y : 0;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % stages, u = i / stages;
-        if (u > 0 && !mbar_wait(&ctl->empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
+        const int s = i % VJP_NI, u = i / VJP_NI;
+        if (u > 0 && !mbar_wait(&ctl->in_empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
           mf_timeout(ctl, status);
           break;
         }
-        uint8_t* st = base + (size_t)s * stage_bytes;
-        mbar_expect_tx(&ctl->loaded[s], ybytes + 8192 + 128 * nvalid);
-        tma_load_2d_hint(st + off_y, &tmY, &ctl->loaded[s], i * 64, 0, pol_y);
-        tma_load_2d(st + off_s, &tmS, &ctl->loaded[s], src, i * 64);
-        for (int b = 0; b < nvalid; ++b) tma_load_2d(st + off_t + b * 128, &tmT, &ctl->loaded[s], i * 64, srow[b]);
+        uint8_t* st = base + (size_t)s * in_bytes;
+        mbar_expect_tx(&ctl->in_full[s], ybytes + 8192 + 128 * nvalid);
+        tma_load_2d_hint(st, &tmY, &ctl->in_full[s], i * 64, 0, pol_y);
+        tma_load_2d(st + off_s, &tmS, &ctl->in_full[s], src, i * 64);
+        for (int b = 0; b < nvalid; ++b) tma_load_2d(st + off_t + b * 128, &tmT, &ctl->in_full[s], i * 64, srow[b]);
         issued = i + 1;
       }
-      if (ctl->abort) drain_loads(ctl, issued, stages, limit_ns);
+      if (ctl->abort) drain_loads(ctl, issued, VJP_NI, limit_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = make_idesc(128, nmma, 1, 0);
       for (int i = 0; i < nk; ++i) {
-        const int s = i % stages, u = i / stages;
-        if (!mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort) ||
-            !mbar_wait(&ctl->loaded[s], u & 1, limit_ns, &ctl->abort)) {
+        const int si = i % VJP_NI, sa = i % VJP_NA;
+        if (!mbar_wait(&ctl->a_full[sa], (i / VJP_NA) & 1, limit_ns, &ctl->abort) ||
+            !mbar_wait(&ctl->in_full[si], (i / VJP_NI) & 1, limit_ns, &ctl->abort)) {
           mf_timeout(ctl, status);
           break;
         }
         tc_fence_after();
-        const uint32_t sa = saddr(base + (size_t)s * stage_bytes);
+        const uint32_t ya = saddr(base + (size_t)si * in_bytes);
+        const uint32_t aa = saddr(a_base + (size_t)sa * 4 * 8192);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t db = smem_desc(sa + off_y + kk * 32, 16, 1024);
+          const uint64_t db = smem_desc(ya + kk * 32, 16, 1024);
           // 16 samples = two 8-row groups (SBO 1024); boxes 2a, 2a+1 8 KB apart (LBO)
-          mma_bf16(tmem, smem_desc(sa + kk * 2048, 8192, 1024), db, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, smem_desc(aa + kk * 2048, 8192, 1024), db, idesc, (i > 0 || kk > 0) ? 1u : 0u);
           if (act1)
-            mma_bf16(tmem + 256u, smem_desc(sa + MF_A_SUB + kk * 2048, 8192, 1024), db, idesc,
+            mma_bf16(tmem + 256u, smem_desc(aa + MF_A_SUB + kk * 2048, 8192, 1024), db, idesc,
                      (i > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&ctl->empty[s]);
+        mma_commit(&ctl->in_empty[si]);
+        mma_commit(&ctl->a_empty[sa]);
       }
       mma_commit(&ctl->accum);
       int no_abort = 0;
       mbar_wait(&ctl->accum, 0, limit_ns, (volatile int*)&no_abort);
     }
   } else {
-    // ---- transform: thread = (box b, sample row sr of the 64-sample step) ----
+    // ---- transform: thread = (sample row sr of the 64-sample step, column quarter qt) ----
     const int ht = threadIdx.x - 64;
-    const int b = ht >> 6, sr = ht & 63;
-    const bool vb = cid[b] >= 0;
-    float mu_acc[64];
+    const int sr = ht & 63, qt = ht >> 6;
+    const uint32_t u0 = (uint32_t)(((2 * qt) ^ (sr & 7)) << 4), u1 = (uint32_t)(((2 * qt + 1) ^ (sr & 7)) << 4);
+    float mu_acc[64];  // [chunk b][16 columns]
 #pragma unroll
     for (int k = 0; k < 64; ++k) mu_acc[k] = 0.f;
     bool ok_loop = true;
     for (int i = 0; i < nk; ++i) {
-      const int s = i % stages, u = i / stages;
-      if (!warp_wait(&ctl->loaded[s], u & 1, limit_ns, &ctl->abort)) {
+      const int si = i % VJP_NI, sa = i % VJP_NA;
+      if ((i >= VJP_NA && !warp_wait(&ctl->a_empty[sa], ((i / VJP_NA) - 1) & 1, limit_ns, &ctl->abort)) ||
+          !warp_wait(&ctl->in_full[si], (i / VJP_NI) & 1, limit_ns, &ctl->abort)) {
         if (lane == 0) mf_timeout(ctl, status);
         ok_loop = false;
         break;
       }
-      uint8_t* st = base + (size_t)s * stage_bytes;
-      if (vb) {
-        const float sc = __bfloat162float(reinterpret_cast<const bf16*>(st + off_t + b * 128)[sr]);
-        const uint8_t* sp = st + off_s + sr * 128;
-        uint8_t* ap = st + b * 8192 + sr * 128;
+      const uint8_t* st = base + (size_t)si * in_bytes;
+      const uint8_t* sp = st + off_s + sr * 128;
+      const uint4 v0 = *reinterpret_cast<const uint4*>(sp + u0), v1 = *reinterpret_cast<const uint4*>(sp + u1);
+      const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+      float x[16];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const uint32_t off = (uint32_t)((k ^ (sr & 7)) << 4);
-          const uint4 v = *reinterpret_cast<const uint4*>(sp + off);
-          uint4 o;
-          o.x = scale2(v.x, sc);
-          o.y = scale2(v.y, sc);
-          o.z = scale2(v.z, sc);
-          o.w = scale2(v.w, sc);
-          if (WITH_MU) {
-            const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+      for (int e = 0; e < 8; ++e) {
+        x[2 * e] = __uint_as_float(w[e] << 16);
+        x[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+      }
+      uint8_t* ap = a_base + (size_t)sa * 4 * 8192 + sr * 128;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              mu_acc[8 * k + 2 * e] += __uint_as_float(w4[e] << 16);
-              mu_acc[8 * k + 2 * e + 1] += __uint_as_float(w4[e] & 0xFFFF0000u);
-            }
+      for (int b = 0; b < 4; ++b) {
+        if (b < nvalid) {
+          const float sc = __bfloat162float(reinterpret_cast<const bf16*>(st + off_t + b * 128)[sr]);
+          float y[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            y[e] = x[e] * sc;
+            if (WITH_MU) mu_acc[16 * b + e] += y[e];
           }
-          *reinterpret_cast<uint4*>(ap + off) = o;
+          uint4 o0, o1;
+          o0.x = pack_bf16x2(y[0], y[1]), o0.y = pack_bf16x2(y[2], y[3]);
+          o0.z = pack_bf16x2(y[4], y[5]), o0.w = pack_bf16x2(y[6], y[7]);
+          o1.x = pack_bf16x2(y[8], y[9]), o1.y = pack_bf16x2(y[10], y[11]);
+          o1.z = pack_bf16x2(y[12], y[13]), o1.w = pack_bf16x2(y[14], y[15]);
+          *reinterpret_cast<uint4*>(ap + b * 8192 + u0) = o0;
+          *reinterpret_cast<uint4*>(ap + b * 8192 + u1) = o1;
         }
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->full[s]);
+      if (lane == 0) mbar_arrive(&ctl->a_full[sa]);
     }
     bool ok = ok_loop && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
     if (!ok && ok_loop) mf_timeout(ctl, status);
     ok = help_bar_and(ok);
     tc_fence_after();
-    // after the accumulator is complete every stage is idle: stage 0 holds
-    // the reduction scratch, mu and the column sums of Yhat
-    float* red = reinterpret_cast<float*>(base);          // [4 boxes][2 warps][64]
+    // after the accumulator is complete every slot is idle: the first input
+    // slot holds the reduction scratch, mu and the column sums of Yhat
+    float* red = reinterpret_cast<float*>(base);          // [2 warps][4 boxes][64 columns]
     float* mu_s = reinterpret_cast<float*>(base + 2048);  // [256]
     float* ys = reinterpret_cast<float*>(base + 3072);    // [256]
     if (ok) {
       if (WITH_MU) {
-        // reduce-scatter over the warp's 32 sample rows: lane L ends with
-        // the sums of parameters 2L and 2L + 1 of box b
+        // reduce-scatter over the warp's 32 sample rows: lane L ends with the
+        // sums of entries 2L, 2L + 1 of its 64 (= box (2L) / 16, column 16 qt + (2L) % 16)
 #pragma unroll
         for (int h = 32, bit = 16; h >= 2; h >>= 1, bit >>= 1) {
           const bool up = (lane & bit) != 0;
@@ -408,8 +438,12 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
             mu_acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
           }
         }
-        red[(b * 2 + ((ht >> 5) & 1)) * 64 + 2 * lane] = mu_acc[0];
-        red[(b * 2 + ((ht >> 5) & 1)) * 64 + 2 * lane + 1] = mu_acc[1];
+        const int w2 = (ht >> 5) & 1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int idx = 2 * lane + e, b = idx >> 4, col = 16 * qt + (idx & 15);
+          red[(w2 * 4 + b) * 64 + col] = mu_acc[e];
+        }
       }
       for (int j = ht; j < r; j += 256) ys[j] = (float)ysum[j];
       help_bar();
@@ -419,7 +453,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         if (cid[pb] >= 0) {
           const int64_t m = (int64_t)cid[pb] * 64 + pj;
           if (WITH_MU) {
-            mu = (red[(pb * 2) * 64 + pj] + red[(pb * 2 + 1) * 64 + pj]) / (float)N;
+            mu = (red[pb * 64 + pj] + red[(4 + pb) * 64 + pj]) / (float)N;
             mu_io[m] = mu;
           } else {
             mu = mu_io[m];
@@ -466,12 +500,12 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 }
 
 int mf_nmma(int r) { return (r + 15) / 16 * 16; }
-uint32_t jvp_stage_bytes(int nmma) { return (2 * MF_A_SUB + (uint32_t)nmma * 128 + 512 + 1023) & ~1023u; }
-uint32_t vjp_stage_bytes(int nmma) { return (4 * 8192 + (uint32_t)nmma * 128 + 8192 + 512 + 1023) & ~1023u; }
-int mf_stages(uint32_t stage_bytes) {
-  size_t s = (227 * 1024 - 1024 - sizeof(MfCtl)) / stage_bytes;
-  if (s > MF_MAX_STAGES) s = MF_MAX_STAGES;
-  return (int)s;
+size_t jvp_smem(int nmma) {
+  return 1024 + (size_t)JVP_NX * round1k((uint32_t)nmma * 128 + 512) + (size_t)JVP_NA * 2 * MF_A_SUB + sizeof(MfCtl);
+}
+size_t vjp_smem(int nmma) {
+  return 1024 + (size_t)VJP_NI * round1k((uint32_t)nmma * 128 + 8192 + 512) + (size_t)VJP_NA * 4 * 8192 +
+         sizeof(MfCtl);
 }
 
 }  // namespace
@@ -497,9 +531,8 @@ int tc_mf_jvp_splits(int64_t N, int64_t nchunks, int r, int num_sms) {
 int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, int splits, float* Yp,
                      int64_t wait_us, int* status, cudaStream_t st, int* splits_used) {
   const int nmma = mf_nmma(r);
-  const uint32_t sb = jvp_stage_bytes(nmma);
-  const int stages = mf_stages(sb);
-  if (stages < 2) return -1;
+  const size_t smem = jvp_smem(nmma);
+  if (smem > 227 * 1024) return -1;
   CUtensorMap tmX, tmT;
   if (!encode_blocked(&tmX, Xblk, src.Mp, r, (uint32_t)nmma)) return -1;
   if (!encode_2d(&tmT, src.ST, (uint64_t)N, (uint64_t)src.nscale, (uint64_t)src.ldst * 2, 256, 1, false)) return -1;
@@ -507,7 +540,6 @@ int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, i
   const int per_split = (int)ceil_div(nchunks, splits);
   const int s_eff = (int)ceil_div(nchunks, per_split);
   const int n_tiles = (int)ceil_div(N, 256);
-  const size_t smem = 1024 + (size_t)stages * sb + sizeof(MfCtl);
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_mf_jvp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
@@ -515,8 +547,8 @@ int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, i
     attr = true;
   }
   k_mf_jvp<<<(unsigned)(n_tiles * s_eff), MF_THREADS, smem, st>>>(
-      tmX, tmT, reinterpret_cast<const bf16*>(src.S), src.Cs, src.sched, N, r, nmma, stages, n_tiles, s_eff, nchunks,
-      per_split, Yp, (uint64_t)wait_us * 1000ull, status);
+      tmX, tmT, reinterpret_cast<const bf16*>(src.S), src.Cs, src.sched, N, r, nmma, n_tiles, nchunks, per_split, Yp,
+      (uint64_t)wait_us * 1000ull, status);
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
@@ -525,14 +557,12 @@ int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t
                      const double* ysum, float* Z, void* ZT, float* mu_io, int compute_mu, int64_t wait_us,
                      int* status, cudaStream_t st) {
   const int nmma = mf_nmma(r);
-  const uint32_t sb = vjp_stage_bytes(nmma);
-  const int stages = mf_stages(sb);
-  if (stages < 2) return -1;
+  const size_t smem = vjp_smem(nmma);
+  if (smem > 227 * 1024) return -1;
   CUtensorMap tmS, tmT, tmY;
   if (!encode_2d(&tmS, src.S, (uint64_t)src.Cs, (uint64_t)N, (uint64_t)src.Cs * 2, 64, 64, true)) return -1;
   if (!encode_2d(&tmT, src.ST, (uint64_t)N, (uint64_t)src.nscale, (uint64_t)src.ldst * 2, 64, 1, false)) return -1;
   if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, 64, (uint32_t)nmma, true)) return -1;
-  const size_t smem = 1024 + (size_t)stages * sb + sizeof(MfCtl);
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_mf_vjp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
@@ -543,11 +573,11 @@ int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t
   const unsigned grid = (unsigned)src.ngroups;
   const uint64_t lim = (uint64_t)wait_us * 1000ull;
   if (compute_mu)
-    k_mf_vjp<true><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, stages, ysum, Z,
+    k_mf_vjp<true><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, ysum, Z,
                                                    (bf16*)ZT, mu_io, lim, status);
   else
-    k_mf_vjp<false><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, stages, ysum,
-                                                    Z, (bf16*)ZT, mu_io, lim, status);
+    k_mf_vjp<false><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, ysum, Z,
+                                                    (bf16*)ZT, mu_io, lim, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -302,7 +302,7 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, N, r, h->gram_part, h->G, 1.0 / (double)N, st);
   launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
-  launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->W, st);
+  launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->opt.jacobi_sweeps, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
   if (h->use_tc) {
@@ -432,7 +432,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   h->ldy = (N + 7) / 8 * 8;
   // pass A partials: one N x r block per split
   h->yp_elems = (int64_t)std::max(h->use_tc ? h->splits_tc : h->splits_simt, h->splits_mf) * N * r;
-  const int64_t blocks64 = ceil_div(std::max(N, M), 64);
+  // column-sum partials: split reduction (16-row blocks of Y), casts and applies (64-row blocks)
+  const int64_t blocks64 = std::max(ceil_div(N, 16), ceil_div(std::max(N, M), 64));
   const int64_t gpart = std::max(gram_part_elems(N, r), gram_part_elems(M, r));
   cudaError_t e = cudaSuccess;
 #define ALLOC(p, bytes) \
@@ -607,8 +608,23 @@ wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n) {
   if (cudaMemcpy(&dev_vals[0], h->nsweeps, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(&dev_vals[1], h->status + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return WSSR_ERR_CUDA;
-  const int64_t vals[3] = {dev_vals[0], dev_vals[1], h->launches};
-  for (int i = 0; i < n && i < 3; ++i) out[i] = vals[i];
+  const int r = h->r, ms = h->opt.jacobi_sweeps;
+  std::vector<int> rounds((size_t)ms * (r - 1), 0);
+  if (n > 3) {
+    // per-round rotation counts stored after the rotation log
+    const float* cnt = h->rot_log + (size_t)ms * (r - 1) * (r / 2) * 2;
+    if (cudaMemcpy(rounds.data(), cnt, rounds.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return WSSR_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    int64_t v = 0;
+    if (i == 0) v = dev_vals[0];
+    else if (i == 1) v = dev_vals[1];
+    else if (i == 2) v = h->launches;
+    else if (i - 3 < ms && i - 3 < dev_vals[0])
+      for (int k = 0; k < r - 1; ++k) v += rounds[(size_t)(i - 3) * (r - 1) + k];
+    out[i] = v;
+  }
   return WSSR_OK;
 }
 

@@ -272,11 +272,15 @@ def wssr_profile_end(h: int):
     return {KCAT_NAMES[i]: (ms[i], la[i]) for i in range(n)}
 
 
-def wssr_get_stats(h: int) -> dict:
-    """{'jacobi_sweeps', 'cholesky_shifts', 'launches'} of the last step (synchronises)."""
-    out = (ctypes.c_int64 * 3)()
-    _check(load().wssr_get_stats(h, out, 3), "wssr_get_stats")
-    return {"jacobi_sweeps": out[0], "cholesky_shifts": out[1], "launches": out[2]}
+def wssr_get_stats(h: int, max_sweeps: int = 12) -> dict:
+    """{'jacobi_sweeps', 'cholesky_shifts', 'launches', 'rotations_per_sweep'} of the
+    last step (synchronises)."""
+    n = 3 + max_sweeps
+    out = (ctypes.c_int64 * n)()
+    _check(load().wssr_get_stats(h, out, n), "wssr_get_stats")
+    sweeps = int(out[0])
+    return {"jacobi_sweeps": sweeps, "cholesky_shifts": out[1], "launches": out[2],
+            "rotations_per_sweep": [int(out[3 + i]) for i in range(min(sweeps, max_sweeps))]}
 
 
 def wssr_mlp_param_count(desc: wssr_mlp_desc) -> int:
@@ -344,6 +348,7 @@ class WSSR:
         opt.engine = {"auto": WSSR_ENGINE_AUTO, "simt": WSSR_ENGINE_SIMT,
                       "tcgen05": WSSR_ENGINE_TCGEN05}[engine]
         self.N, self.M, self.r, self.lam, self.dtype = N, M, r, lam, dtype
+        self.jacobi_sweeps = jacobi_sweeps
         self.handle = wssr_create(N, M, r, lam, opt)
 
     def close(self):
@@ -420,7 +425,7 @@ class WSSR:
         return wssr_last_launch_count(self.handle)
 
     def stats(self) -> dict:
-        return wssr_get_stats(self.handle)
+        return wssr_get_stats(self.handle, self.jacobi_sweeps)
 
     def profile_begin(self):
         wssr_profile_begin(self.handle)

@@ -120,6 +120,11 @@ WORKLOADS = {
     "mlp-75-1024x3-1": MLPWorkload(
         "mlp-75-1024x3-1", widths=(75, 1024, 1024, 1024, 1), N=8192, r=256, lam=1e-4, m=2,
         steps=50, matrix_free=True),
+    # The same network on 2048 samples (operand basis 1.1 GB, above L2; about
+    # 5 GB on the device): the case ncu captures of the matrix-free kernels run on.
+    "mlp-75-1024x3-1-n2048": MLPWorkload(
+        "mlp-75-1024x3-1-n2048", widths=(75, 1024, 1024, 1024, 1), N=2048, r=256, lam=1e-4, m=2,
+        steps=50, matrix_free=True),
 }
 
 
