@@ -522,7 +522,8 @@ def mlp_cpu_sample(w, cols: int):
 def run_mlp_mf(args, w):
     """Matrix-free workload: each step recomputes the activations and adjoints
     of fresh electron samples and runs one WSSR step with O applied on the
-    tensor cores from them (O never formed)."""
+    tensor cores from them (O never formed), then updates theta by the SR
+    direction. The timed region covers the step and the parameter update."""
     import torch
     import torch.distributed as dist
 
@@ -546,8 +547,15 @@ def run_mlp_mf(args, w):
     delta = torch.empty(ans.Mp, device=dev)
     sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
     Vb = torch.empty_like(V)
+    def sr_update():
+        # parameter update of an SR step, theta <- theta - eta delta with
+        # eta = 1e-3 |theta| / |delta| (the step-to-step change of the workload)
+        d_user = ans.unpad(delta)
+        theta.sub_(d_user * (1e-3 * theta.norm() / d_user.norm()))
+
     for t in range(args.warmup):
         s.step(ans.operator(theta, xs[1 + t]), g, V, out=(delta, sigma, Vb))
+        sr_update()
         V, Vb = Vb, V
     s.check("warmup")
     clocks = ClockSampler(local)
@@ -564,6 +572,7 @@ def run_mlp_mf(args, w):
     for t in range(args.steps):
         s.step(ans.operator(theta, xs[1 + args.warmup + t]), g, V, out=(delta, sigma, Vb))
         launches += s.last_launch_count()
+        sr_update()
         V, Vb = Vb, V
     e1.record(stream)
     torch.cuda.synchronize()

@@ -236,9 +236,6 @@ void launch_sum_partials(const float* Gp, int S, int r, double scale, double* G,
 // upper storage, in-place inverse, T = D R'^-1.
 // ---------------------------------------------------------------------------
 namespace {
-__device__ __forceinline__ int pidx(int i, int j, int r) {  // i <= j
-  return i * r - (i * (i - 1)) / 2 + (j - i);
-}
 
 // Blocked algorithm with 32 x 32 blocks (nb = ceil(r / 32) <= 8):
 //   factor:   for each K, one warp factors the diagonal block A_KK = R_KK^T R_KK
@@ -694,23 +691,44 @@ __device__ __forceinline__ void rr_pair(int k, int i, int r, int& p, int& q) {
   q = ((r - 2 - i + k) % n1) + 1;
 }
 
+// Rotation zeroing a_pq of [[app, apq], [apq, aqq]]: rotate when the pair is
+// not yet orthogonal relative to its diagonal (tol) and a_pq is above the
+// FP32 rounding noise that rotations of the larger element leave behind (a
+// few ulp of max |a_pp|, |a_qq|).
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float& c, float& s, float& t) {
+  const float tol = 3e-7f;
+  const float noise = 4.f * 5.96e-8f * fmaxf(fabsf(app), fabsf(aqq));
+  c = 1.f, s = 0.f, t = 0.f;
+  if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > noise) {
+    const float tau = (aqq - app) / (2.f * apq);
+    t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    c = rsqrtf(1.f + t * t);
+    s = t * c;
+  }
+}
+
+// One CTA of 1024 threads; A = packed upper triangle in shared memory
+// (A[rb[i] + j], j >= i, rb[i] = i r - i (i + 1) / 2). Per round: the r/2
+// rotations go into a table {c, s, p, q} + {rb[p], rb[q]} (+ t for the
+// diagonal blocks); then every warp updates the 2 x 2 blocks (i1, i2 >= i1)
+// of its (at most 4) block rows i1, enumerated as one flat index range so
+// that lanes stay busy across row ends; blocks whose two pairs are both idle
+// are skipped.
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
                                                  float2* __restrict__ rot_log, int* nsweeps_out,
                                                  float* __restrict__ evals, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);
-  // per-round rotation counts, stored after the rotation log
+  __shared__ float4 tab[128];  // {c, s, p, q} (p, q as int bits)
+  __shared__ int2 tabrb[128];  // {rb[p], rb[q]}
+  __shared__ float tabt[128];  // t = tan(theta)
+  __shared__ int rb[256];
+  __shared__ int warp_act[4], rot_sweep, bad;
   int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * (r - 1) * (r / 2));
-  __shared__ float cs_c[128], cs_s[128], cs_t[128];
-  __shared__ int pp[128], qq[128];
-  __shared__ int act[128];  // indices of the pairs that rotate in this round
-  __shared__ int rb[256];   // packed row base: A[i][j] = A[rb[i] + j] for j >= i
-  __shared__ int rot_round, rot_sweep, bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int h = r / 2;
-  const float tol = 3e-7f;
+  const int h = r / 2, n1 = r - 1;
   if (tid == 0) bad = 0;
-  if (tid < r) rb[tid] = pidx(tid, 0, r);
+  if (tid < r) rb[tid] = tid * r - tid * (tid + 1) / 2;
   __syncthreads();
   for (int e = tid; e < r * r; e += 1024) {
     const int i = e / r, j = e % r;
@@ -728,107 +746,127 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     }
     return;
   }
-#define AIX(a, b) ((a) <= (b) ? rb[a] + (b) : rb[b] + (a))
+  // this warp's block rows (balanced when h % 64 == 0: w, 63-w, 64+w, 127-w)
+  // and the start of each in the warp's flat block index
+  int row_i1[4], row_start[4], n_blocks = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
+    row_start[t] = n_blocks;
+    row_i1[t] = i1;
+    if (i1 < h) n_blocks += h - i1;
+    else row_start[t] = 1 << 30;
+  }
+
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) rot_sweep = 0;
-    __syncthreads();
-    for (int k = 0; k < r - 1; ++k) {
-      if (tid == 0) rot_round = 0;
-      __syncthreads();  // also orders the previous round's reads of rot_round
+    for (int k = 0; k < n1; ++k) {
       if (tid < h) {
         int p, q;
         rr_pair(k, tid, r, p, q);
-        pp[tid] = p;
-        qq[tid] = q;
-        const float app = A[rb[p] + p], aqq = A[rb[q] + q];
-        const float apq = A[AIX(p, q)];
-        float c = 1.f, s = 0.f, t = 0.f;
-        // rotate when the pair is not yet orthogonal relative to its diagonal
-        // (tol) and a_pq is above the FP32 rounding noise that rotations of
-        // the larger element leave behind (a few ulp of max |a_pp|, |a_qq|)
-        const float noise = 4.f * 5.96e-8f * fmaxf(fabsf(app), fabsf(aqq));
-        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > noise) {
-          const float tau = (aqq - app) / (2.f * apq);
-          t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = rsqrtf(1.f + t * t);
-          s = t * c;
-        }
-        cs_c[tid] = c;
-        cs_s[tid] = s;
-        cs_t[tid] = t;
-        if (s != 0.f) act[atomicAdd(&rot_round, 1)] = tid;
-        rot_log[((int64_t)sweep * (r - 1) + k) * h + tid] = make_float2(c, s);
+        const int rbp = rb[p], rbq = rb[q];
+        const float app = A[rbp + p], aqq = A[rbq + q];
+        const float apq = A[p < q ? rbp + q : rbq + p];
+        float c, s, t;
+        jacobi_rotation(app, aqq, apq, c, s, t);
+        tab[tid] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
+        tabrb[tid] = make_int2(rbp, rbq);
+        tabt[tid] = t;
+        rot_log[((int64_t)sweep * n1 + k) * h + tid] = make_float2(c, s);
+        const unsigned act = __ballot_sync(__activemask(), s != 0.f);
+        if ((tid & 31) == 0) warp_act[tid >> 5] = __popc(act);
       }
       __syncthreads();
-      const int nact = rot_round;
-      if (tid == 0) round_nact[sweep * (r - 1) + k] = nact;
+      const int nact = (h > 0 ? warp_act[0] : 0) + (h > 32 ? warp_act[1] : 0) + (h > 64 ? warp_act[2] : 0) +
+                       (h > 96 ? warp_act[3] : 0);
+      if (tid == 0) {
+        round_nact[sweep * n1 + k] = nact;
+        if (nact) rot_sweep = 1;
+      }
       if (nact) {
-        // Blocks (i1, i2), i1 <= i2, change only when pair i1 or pair i2
-        // rotates: a rotating i1 updates its whole block row; an idle i1 only
-        // the blocks of rotating pairs i2 > i1.
-        // warp rows in a balanced order (w, 63-w, 64+w, 127-w, ... when h % 64 == 0)
-        for (int t = 0; 32 * t + warp < h; ++t) {
-          const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
-          const int p1 = pp[i1], q1 = qq[i1];
-          const float c1 = cs_c[i1], s1 = cs_s[i1];
-          const bool full_row = s1 != 0.f;
-          const int n_inner = full_row ? h - i1 : nact;
-          for (int e = lane; e < n_inner; e += 32) {
-            const int i2 = full_row ? i1 + e : act[e];
-            if (!full_row && i2 <= i1) continue;
-            if (i2 == i1) {
-              const float t1 = cs_t[i1];
-              const int ipq = AIX(p1, q1);
-              const float apq = A[ipq];
-              A[rb[p1] + p1] -= t1 * apq;
-              A[rb[q1] + q1] += t1 * apq;
-              A[ipq] = 0.f;
-            } else {
-              const int p2 = pp[i2], q2 = qq[i2];
-              const float c2 = cs_c[i2], s2 = cs_s[i2];
-              const int i_pp = AIX(p1, p2), i_pq = AIX(p1, q2), i_qp = AIX(q1, p2), i_qq = AIX(q1, q2);
-              const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
-              // B J2 (columns p2, q2), then J1^T (rows p1, q1)
-              const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
-              const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
-              A[i_pp] = c1 * xpp - s1 * xqp;
-              A[i_qp] = s1 * xpp + c1 * xqp;
-              A[i_pq] = c1 * xpq - s1 * xqq;
-              A[i_qq] = s1 * xpq + c1 * xqq;
-            }
+        for (int e = lane; e < n_blocks; e += 32) {
+          const int j = (e >= row_start[1]) + (e >= row_start[2]) + (e >= row_start[3]);
+          const int i1 = j == 0 ? row_i1[0] : (j == 1 ? row_i1[1] : (j == 2 ? row_i1[2] : row_i1[3]));
+          const int st_j = j == 0 ? row_start[0] : (j == 1 ? row_start[1] : (j == 2 ? row_start[2] : row_start[3]));
+          const int i2 = i1 + (e - st_j);
+          const float4 t1 = tab[i1], t2 = tab[i2];
+          if (t1.y == 0.f && t2.y == 0.f) continue;
+          const int p1 = __float_as_int(t1.z), q1 = __float_as_int(t1.w);
+          const int2 rb1 = tabrb[i1];
+          if (i2 == i1) {
+            const float tt = tabt[i1];
+            const int ipq = p1 < q1 ? rb1.x + q1 : rb1.y + p1;
+            const float apq = A[ipq];
+            A[rb1.x + p1] -= tt * apq;
+            A[rb1.y + q1] += tt * apq;
+            A[ipq] = 0.f;
+          } else {
+            const int p2 = __float_as_int(t2.z), q2 = __float_as_int(t2.w);
+            const int2 rb2 = tabrb[i2];
+            const int i_pp = p1 <= p2 ? rb1.x + p2 : rb2.x + p1;
+            const int i_pq = p1 <= q2 ? rb1.x + q2 : rb2.y + p1;
+            const int i_qp = q1 <= p2 ? rb1.y + p2 : rb2.x + q1;
+            const int i_qq = q1 <= q2 ? rb1.y + q2 : rb2.y + q1;
+            const float c1 = t1.x, s1 = t1.y, c2 = t2.x, s2 = t2.y;
+            const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
+            // B J2 (columns p2, q2), then J1^T (rows p1, q1)
+            const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
+            const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
+            A[i_pp] = c1 * xpp - s1 * xqp;
+            A[i_qp] = s1 * xpp + c1 * xqp;
+            A[i_pq] = c1 * xpq - s1 * xqq;
+            A[i_qq] = s1 * xpq + c1 * xqq;
           }
         }
-        if (tid == 0) rot_sweep = 1;
       }
       __syncthreads();
     }
     __syncthreads();
     if (!rot_sweep) {
-      ++sweep;  // this sweep did no rotation; keep its (identity) log
+      ++sweep;  // this sweep did no rotation
       break;
     }
   }
-#undef AIX
+
   if (tid == 0) *nsweeps_out = sweep;
   for (int i = tid; i < r; i += 1024) evals[i] = A[rb[i] + i];
 }
 
-// Replays the logged rotations on rows of the identity (4 rows per CTA),
-// then writes W with columns sorted by descending eigenvalue.
-__global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* __restrict__ nsweeps,
-                                 const float* __restrict__ evals, int r, int max_sweeps, float* __restrict__ W) {
-  __shared__ float Wr[4][256];
+// Replays the logged rotations on rows of the identity: one warp per row of
+// W (JV_WARPS rows per CTA), each row in shared memory, rounds separated by
+// __syncwarp only (the r/2 rotations of a round touch disjoint columns).
+// The CTA stages the log through shared memory in chunks of JV_CHUNK rounds
+// with double-buffered cp.async, so the L2 latency of the next chunk overlaps
+// the rotations of the current one. A lane follows its pairs' indices from
+// round to round incrementally (each advances by one on the ring of r - 1).
+// Idle rounds and idle pairs are skipped. Then writes W with columns sorted
+// by descending eigenvalue.
+constexpr int JV_CHUNK = 16;
+constexpr int JV_WARPS = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* __restrict__ rot_log,
+                                                                  const int* __restrict__ nsweeps,
+                                                                  const float* __restrict__ evals, int r,
+                                                                  int max_sweeps, float* __restrict__ W) {
+  __shared__ __align__(16) float2 stage[2][JV_CHUNK * 128];
+  __shared__ int stage_cnt[2][JV_CHUNK];
+  __shared__ float wr_all[JV_WARPS][256];
   __shared__ int rank_of[256];
-  const int tid = threadIdx.x;
-  const int h = r / 2;
-  const int row_l = tid / h, pi = tid % h;  // blockDim = 4 * h
-  const int row = blockIdx.x * 4 + row_l;
-  for (int e = tid; e < 4 * r; e += blockDim.x) {
-    const int rl = e / r, c = e % r;
-    Wr[rl][c] = (blockIdx.x * 4 + rl == c) ? 1.f : 0.f;
-  }
-  for (int i = tid; i < r; i += blockDim.x) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = blockIdx.x * JV_WARPS + warp;
+  const int h = r / 2, n1 = r - 1;
+  float* wr = wr_all[warp];
+  for (int i = tid; i < r; i += 32 * JV_WARPS) {
     const float li = evals[i];
     int rk = 0;
     for (int j = 0; j < r; ++j) {
@@ -837,25 +875,67 @@ __global__ void k_jacobi_vectors(const float2* __restrict__ rot_log, const int* 
     }
     rank_of[i] = rk;
   }
-  __syncthreads();
-  const int total = nsweeps[0] * (r - 1);
-  const int* round_nact = reinterpret_cast<const int*>(rot_log + (int64_t)max_sweeps * (r - 1) * h);
-  for (int t = 0; t < total; ++t) {
-    if (round_nact[t] == 0) continue;  // uniform over the CTA
-    const int k = t % (r - 1);
-    int p, q;
-    rr_pair(k, pi, r, p, q);
-    const float2 cs = rot_log[(int64_t)t * h + pi];
-    if (cs.y != 0.f) {
-      const float wp = Wr[row_l][p], wq = Wr[row_l][q];
-      Wr[row_l][p] = cs.x * wp - cs.y * wq;
-      Wr[row_l][q] = cs.y * wp + cs.x * wq;
+  for (int c = lane; c < r; c += 32) wr[c] = (c == row) ? 1.f : 0.f;
+  const int total = nsweeps[0] * n1;
+  const int* round_nact = reinterpret_cast<const int*>(rot_log + (int64_t)max_sweeps * n1 * h);
+  const int nchunks = (total + JV_CHUNK - 1) / JV_CHUNK;
+  auto issue = [&](int c) {
+    const int t0 = c * JV_CHUNK, nt = min(JV_CHUNK, total - t0);
+    const float2* src = rot_log + (int64_t)t0 * h;
+    float2* dst = stage[c & 1];
+    for (int e = 2 * tid; e < nt * h; e += 64 * JV_WARPS) cp_async16(dst + e, src + e);
+    cp_async_commit();
+    if (tid < JV_CHUNK) stage_cnt[c & 1][tid] = (tid < nt) ? round_nact[t0 + tid] : 0;
+  };
+  // ring positions (index - 1) of this lane's pairs i = lane + 32 m in round 0;
+  // pair 0's first index is the fixed index 0
+  int pu[4], qu[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = lane + 32 * m;
+    pu[m] = (i + n1 - 1) % n1;
+    qu[m] = (r - 2 - i + n1) % n1;
+  }
+  if (nchunks > 0) issue(0);
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      issue(c + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const int t0 = c * JV_CHUNK, nt = min(JV_CHUNK, total - t0);
+    const float2* cs_chunk = stage[c & 1];
+    if (row < r) {
+      for (int j = 0; j < nt; ++j) {
+        if (stage_cnt[c & 1][j] != 0) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int i = lane + 32 * m;
+            if (i < h) {
+              const float2 cs = cs_chunk[j * h + i];
+              if (cs.y != 0.f) {
+                const int p = (i == 0) ? 0 : pu[m] + 1, q = qu[m] + 1;
+                const float wp = wr[p], wq = wr[q];
+                wr[p] = cs.x * wp - cs.y * wq;
+                wr[q] = cs.y * wp + cs.x * wq;
+              }
+            }
+          }
+          __syncwarp();
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          pu[m] = pu[m] + 1 == n1 ? 0 : pu[m] + 1;
+          qu[m] = qu[m] + 1 == n1 ? 0 : qu[m] + 1;
+        }
+      }
+    }
+    __syncthreads();  // the stage just read is refilled by the next issue
   }
-  if (row < r) {
-    for (int c = pi; c < r; c += h) W[(int64_t)row * r + rank_of[c]] = Wr[row_l][c];
-  }
+  if (row < r)
+    for (int c = lane; c < r; c += 32) W[(int64_t)row * r + rank_of[c]] = wr[c];
 }
 }  // namespace
 
@@ -878,8 +958,8 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
 
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
                            int max_sweeps, float* W, cudaStream_t st) {
-  k_jacobi_vectors<<<(unsigned)ceil_div(r, 4), 4 * (r / 2), 0, st>>>((const float2*)rot_log, nsweeps,
-                                                                     evals, r, max_sweeps, W);
+  k_jacobi_vectors<<<(unsigned)ceil_div(r, JV_WARPS), 32 * JV_WARPS, 0, st>>>((const float2*)rot_log, nsweeps,
+                                                                               evals, r, max_sweeps, W);
 }
 
 // ---------------------------------------------------------------------------

@@ -317,10 +317,12 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
   } else {
     launch_apply_any(Xop, operand_layout(h), r, M, r, h->TW, V_out, nullptr, 0, nullptr, 0, nullptr,
                      nullptr, st);
+    h->launches += 1;
   }
   launch_apply(h->Y, N, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   launch_gram(h->Y2, N, r, h->gram_part, h->Hp, 1.0 / (double)N, st);
-  h->launches += 2 + 1 + 1 + 1 + 1 + 1 + 2;
+  // Gram (2), Jacobi and its eigenvector replay (2), T W (1), Y W (1), Gram (2)
+  h->launches += 2 + 2 + 1 + 1 + 2;
   double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
   launch_finalize_sigma(h->Hp, r, sig, st);
   h->launches++;
