@@ -19,6 +19,10 @@ function following the passage it cites:
   (Hestenes' method) gives sigma and the rotation of V (this replaces the
   |diag R| sort at the end of Algorithm 1, whose output is left
   unnormalised by the paper);
+* history averaging (Section 4.1, Eq. (Ohat), (Lhat), (Obar), (Lbar), (barg),
+  (barS)): the SVD runs on O^ = [sqrt(w) Obar_prev, sqrt(1-w) O_N] with
+  Obar_prev = V_prev diag(sigma_prev) and O_N = O_c^T / sqrt(N), the
+  gradient on gbar = O^ L^ = w Obar_prev Lbar_prev + (1 - w) g;
 * the low-rank-plus-damping apply of Eq. (updated_sr_1) (Section 4.1):
   damped reading delta = [V diag(1/(sigma^2+lam)) V^T + lam^-1 (I - V V^T)] g,
   and the paper's own cutoff reading (S^dagger + sigma_floor^-1 S^perp) g.
@@ -37,6 +41,7 @@ __all__ = [
     "column_mean", "centre", "householder_qr", "jacobi_svd", "orth",
     "subspace_iteration", "rayleigh_ritz", "fix_signs", "woodbury_apply",
     "wssr_step", "init_subspace", "projector_distance", "S_matvec",
+    "history_operator", "averaged_gradient", "wssr_step_averaged",
 ]
 
 
@@ -223,6 +228,56 @@ def wssr_step(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: i
     V = fix_signs(V)
     delta = woodbury_apply(V, sigma, g, lam, mode, sigma_floor)
     return delta, sigma, V
+
+
+def history_operator(O: np.ndarray, V_prev: np.ndarray, sigma_prev: np.ndarray, weight: float) -> np.ndarray:
+    """O^ of Eq. (Ohat) in the paper's orientation (parameters x columns):
+    [sqrt(w) Obar_prev, sqrt(1 - w) O_N], M x (r + N), with Obar_prev =
+    V_prev diag(sigma_prev) (Eq. (Obar): U Sigma of the previous step) and
+    O_N = O_c^T / sqrt(N) the current samples (Eq. (Osrn))."""
+    Oc = centre(O)
+    N = Oc.shape[0]
+    V_prev = np.asarray(V_prev, dtype=np.float64)
+    sigma_prev = np.asarray(sigma_prev, dtype=np.float64)
+    return np.concatenate([np.sqrt(weight) * V_prev * sigma_prev[None, :],
+                           np.sqrt(1.0 - weight) * Oc.T / np.sqrt(N)], axis=1)
+
+
+def averaged_gradient(g: np.ndarray, V_prev: np.ndarray, sigma_prev: np.ndarray, Lbar_prev: np.ndarray,
+                      weight: float) -> np.ndarray:
+    """gbar = O^ L^ (Eq. (barg) with Eq. (Lhat)): the history block gives
+    w Obar_prev Lbar_prev, the current block (1 - w) O_N Lbar_N = (1 - w) g,
+    since the current gradient estimate is g = O_N Lbar_N (Eq. (gradient:vmc))."""
+    V_prev = np.asarray(V_prev, dtype=np.float64)
+    hist = V_prev @ (np.asarray(sigma_prev, dtype=np.float64) * np.asarray(Lbar_prev, dtype=np.float64))
+    return weight * hist + (1.0 - weight) * np.asarray(g, dtype=np.float64)
+
+
+def wssr_step_averaged(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, sigma_prev: np.ndarray,
+                       Lbar_prev: np.ndarray, lam: float, m: int, weight: float,
+                       mode: str = "damped", sigma_floor: float | None = None):
+    """One WSSR step with history averaging (Section 4.1 and Algorithm 2's
+    update of Obar and Lbar), the truncated SVD of O^ by warm-started subspace
+    iteration on O^ O^^T (Section 4.2) plus Rayleigh-Ritz.
+
+    Returns (delta, sigma, V, Lbar, gbar): sigma the r largest singular values
+    of O^ (s_i; the S-bar eigenvalues are s_i^2), V its left singular vectors
+    (Obar = V diag(sigma), Eq. (Obar)), Lbar = V^(k) L^ = diag(1/sigma) V^T gbar
+    (Eq. (Lbar), with V^(k) = diag(1/sigma) V^T O^ the right singular vectors),
+    and delta the apply of Eq. (updated_sr_1) to gbar with S-bar = V diag(sigma^2) V^T
+    (Eq. (barS))."""
+    Oh = history_operator(O, V_prev, sigma_prev, weight)
+    V = np.asarray(V_prev, dtype=np.float64)
+    for _ in range(m):
+        Q = orth(V)
+        V = Oh @ (Oh.T @ Q)
+    V = orth(V)
+    _, sigma, W = jacobi_svd(Oh.T @ V)
+    V = fix_signs(V @ W)
+    gbar = averaged_gradient(g, V_prev, sigma_prev, Lbar_prev, weight)
+    Lbar = (V.T @ gbar) / sigma
+    delta = woodbury_apply(V, sigma, gbar, lam, mode, sigma_floor)
+    return delta, sigma, V, Lbar, gbar
 
 
 def init_subspace(O: np.ndarray, V_rand: np.ndarray, m_init: int = 20) -> np.ndarray:

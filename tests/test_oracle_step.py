@@ -194,3 +194,61 @@ def test_removing_centring_is_detected():
     # uncentred S would have a leading value of order |offset|
     Sraw = np.linalg.svd(O / np.sqrt(N), compute_uv=False)
     assert Sraw[0] > 3.0
+
+
+# ---------------------------------------------------------------------------
+# History averaging (Section 4.1, Eq. (Ohat)-(barS), Remark 3)
+# ---------------------------------------------------------------------------
+
+def test_averaged_step_weight_zero_is_the_plain_step():
+    w = wl.small_planted(60, 90, 6, K=60, sigma_power=1.0, noise=1e-3)
+    O = wl.planted_O_np(w)
+    g = wl.gradient_np(w.M, 0, "avg0")
+    V0 = orc.init_subspace(O, wl.start_subspace_np(w.M, w.r, "avg0"), m_init=30)
+    sp = np.linspace(2.0, 0.5, w.r)
+    Lp = wl.gaussian_np((w.r,), "avg0L")
+    d, s, V, _, gbar = orc.wssr_step_averaged(O, g, V0, sp, Lp, 1e-3, 2, 0.0)
+    d0, s0, V0b = orc.wssr_step(O, g, V0, 1e-3, 2)
+    assert np.allclose(gbar, g, rtol=0, atol=0)
+    assert np.abs(s - s0).max() <= 1e-12 * s0[0]
+    assert np.linalg.norm(d - d0) <= 1e-11 * np.linalg.norm(d0)
+    assert orc.projector_distance(V, V0b) <= 1e-10
+
+
+def test_remark3_exact_averaging_at_full_rank():
+    """With r = M and full row rank of O^ (no truncation), S-bar = Obar Obar^T
+    and gbar = Obar Lbar follow the averaging recursions exactly:
+    S-bar_k = w S-bar_{k-1} + (1 - w) S_k, gbar_k = w gbar_{k-1} + (1 - w) g_k
+    (Remark 3), starting from Obar_0 = 0, Lbar_0 = 0."""
+    N, M, wgt = 9, 5, 0.7
+    V = np.eye(M)
+    sigma = np.zeros(M)
+    Lbar = np.zeros(M)
+    S_avg = np.zeros((M, M))
+    g_avg = np.zeros(M)
+    for k in range(3):
+        O = wl.gaussian_np((N, M), "rem3", k) + 0.3 * k
+        g = wl.gaussian_np((M,), "rem3g", k)
+        _, sigma, V, Lbar, gbar = orc.wssr_step_averaged(O, g, V, sigma, Lbar, 1e-3, 30, wgt)
+        Oc = orc.centre(O)
+        S_avg = wgt * S_avg + (1 - wgt) * Oc.T @ Oc / N
+        g_avg = wgt * g_avg + (1 - wgt) * g
+        Sbar = (V * sigma ** 2) @ V.T
+        assert np.abs(Sbar - S_avg).max() <= 1e-12 * np.abs(S_avg).max()
+        assert np.abs(gbar - g_avg).max() <= 1e-12 * np.abs(g_avg).max()
+        # gbar lies in span(Obar): Obar Lbar reproduces it
+        assert np.abs((V * sigma) @ Lbar - g_avg).max() <= 1e-11 * np.abs(g_avg).max()
+
+
+def test_averaged_step_truncated_matches_numpy_svd():
+    """With truncation, many subspace iterations converge to the top-r SVD of
+    O^ (numpy's SVD as an external check of sigma and the subspace)."""
+    w = wl.small_planted(40, 70, 5, K=40, sigma_power=1.0, noise=1e-3)
+    O = wl.planted_O_np(w)
+    Vp = np.linalg.qr(wl.gaussian_np((w.M, w.r), "avgt"))[0]
+    sp = np.array([3.0, 2.0, 1.5, 1.0, 0.7])
+    _, s, V, _, _ = orc.wssr_step_averaged(O, np.zeros(w.M), Vp, sp, np.zeros(w.r), 1e-3, 200, 0.4)
+    Oh = orc.history_operator(O, Vp, sp, 0.4)
+    U, S, _ = np.linalg.svd(Oh, full_matrices=False)
+    assert np.abs(s - S[:w.r]).max() <= 1e-10 * S[0]
+    assert orc.projector_distance(V, U[:, :w.r]) <= 1e-8
