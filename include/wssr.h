@@ -80,6 +80,8 @@ typedef struct {
                            on expiry the kernel records WSSR_ERR_DEVICE_TIMEOUT and returns */
   int32_t engine;       /* WSSR_ENGINE_* (default AUTO) */
   int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
+  int32_t history;      /* 1: allocate the workspace of wssr_step_averaged (tcgen05 engine) (default 0) */
+  int32_t reserved;     /* 0 */
 } wssr_options;
 
 struct wssr_mlp_ctx;
@@ -131,6 +133,27 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda,
 wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g,
                       const float* V_prev, float* delta, double* sigma, float* V_out,
                       wssr_stream_t stream);
+
+/* One WSSR step with history averaging (Section 4.1: Eq. (Ohat), (Lhat),
+ * (Obar), (Lbar), (barg), (barS); Algorithm 2's update of Obar and Lbar).
+ * The truncated SVD runs on the averaged operator whose S-matrix is
+ *   S-bar = (1 - w) O_c^T O_c / N + w V_prev diag(sigma_prev^2) V_prev^T,
+ * and the apply uses the averaged gradient
+ *   gbar = (1 - w) g + w V_prev (sigma_prev * Lbar_prev).
+ *   weight      w in [0, 1); w = 0 is wssr_step up to rounding
+ *   sigma_prev  r doubles (device), sigma of the previous averaged step (zeros at the first step)
+ *   Lbar_prev   r doubles (device), Lbar of the previous step (zeros at the first step)
+ *   Lbar_out    r doubles (device): diag(1/sigma) V_out^T gbar (Eq. (Lbar))
+ *   gbar_out    M floats (device) or NULL: the averaged gradient that was applied
+ * Other arguments as in wssr_step (delta, sigma, V_out describe the averaged
+ * S-bar). Needs a context created with options.history = 1 on the tcgen05
+ * engine (else WSSR_ERR_UNSUPPORTED). Lbar_out may alias Lbar_prev and V_out
+ * V_prev only if the caller double-buffers sigma (sigma_prev is read until the
+ * end of the step). */
+wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const float* g, const float* V_prev,
+                               const double* sigma_prev, const double* Lbar_prev, double weight, float* delta,
+                               double* sigma, float* V_out, double* Lbar_out, float* gbar_out,
+                               wssr_stream_t stream);
 
 /* Cold start of the first step (the paper uses LMSVD there, Algorithm 2):
  * orthonormalise the caller's seeded block V_rand (M x r), run m_init

@@ -34,7 +34,7 @@ int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, i
 // computed in the pass (compute_mu) or read from mu_io.
 int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t ldy, int r,
                      const double* ysum, float* Z, void* ZT, float* mu_io, int compute_mu, int64_t wait_us,
-                     int* status, cudaStream_t st);
+                     int* status, cudaStream_t st, const float* Zadd = nullptr);
 
 
 // ---- O passes, SIMT engine (simt_passes.cu) ----
@@ -59,8 +59,22 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 // Z (M x r floats) when ZT == nullptr, else the K-blocked bf16 block ZT.
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
                     int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
-                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st);
+                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st,
+                    const float* Zadd = nullptr);
 // FP32 partial Grams Gp[split] (r x r) of the K-blocked bf16 block XT (L rows).
+// History averaging helpers (small_ops.cu): out[j][k] = gamma sigma_prev[j] in[j][k]
+// (r x r, in with row pitch ld_in); e = weight * sigma_prev * Lbar_prev; Lbar = c / sigma.
+void launch_scale_rows_r(const double* in, int64_t ld_in, const double* sigma_prev, double gamma, int r, float* out,
+                         cudaStream_t st);
+void launch_scale_rows_r(const float* in, int64_t ld_in, const double* sigma_prev, double gamma, int r, float* out,
+                         cudaStream_t st);
+void launch_hist_coeffs(const double* sigma_prev, const double* Lbar_prev, double weight, int r, double* e,
+                        cudaStream_t st);
+void launch_lbar(const double* c, const double* sigma, int r, double* Lbar, cudaStream_t st);
+// Cross Gram Gp[split] (r x r, FP32) = XA^T XB over the split's parameter
+// chunks, XA and XB K-blocked bf16 operands of L rows (tc_passes.cu).
+int tc_xgram_launch(const void* XA, const void* XB, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                    int* status, cudaStream_t st, int* splits_used);
 int tc_gram_splits(int64_t L, int num_sms);
 int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
                    int* status, cudaStream_t st, int* splits_used);
@@ -93,12 +107,12 @@ size_t chol_inv_smem(int r);
 // and FP64 column-sum partials of the bf16/f32 operand values written.
 void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
                   int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
-                  int64_t* nblocks_out, cudaStream_t st);
+                  int64_t* nblocks_out, cudaStream_t st, int64_t csum_rows = -1);
 // Same with the tall block given as layout 0 = float row-major, 1 = bf16
 // row-major, 2 = bf16 K-blocked (blk_index).
 void launch_apply_any(const void* X, int layout, int64_t ldx, int64_t L, int r, const float* T,
                       float* Xo, void* out_lp_rowmajor, int lp_is_bf16, void* out_bf16_T, int64_t ldT,
-                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st);
+                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st, int64_t csum_rows = -1);
 void launch_colsum_finalize(const double* part, int64_t nblocks, int r, double* out,
                             cudaStream_t st);
 // Gram of a float or bf16 row-major L x r block (FP64 result).

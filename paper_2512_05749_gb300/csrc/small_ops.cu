@@ -464,7 +464,7 @@ template <int LAYOUT>
 __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int64_t ldx, int64_t L, int r,
                                                const float* __restrict__ T, float* __restrict__ Xo,
                                                void* lp_row, int lp_bf16, bf16* __restrict__ outT,
-                                               int64_t ldT, double* __restrict__ colsum_part) {
+                                               int64_t ldT, double* __restrict__ colsum_part, int64_t csum_rows) {
   __shared__ __align__(16) float As[AK][AM + 4];
   __shared__ __align__(16) float Bs[AK][AN];
   __shared__ float Cs[AN][AM + 1];
@@ -542,10 +542,13 @@ __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int6
     }
   }
   if (colsum_part && tid < AN) {
+    // column sums over the rows below csum_rows (the sample rows of a block
+    // that may carry extra rows after them)
     const int j = j0 + tid;
     if (j < r) {
       double s = 0.0;
-      for (int rr = 0; rr < AM; ++rr) s += (double)Cs[tid][rr];
+      const int64_t lim = csum_rows - m0;
+      for (int rr = 0; rr < AM && rr < lim; ++rr) s += (double)Cs[tid][rr];
       colsum_part[(int64_t)blockIdx.x * r + j] = s;
     }
   }
@@ -554,25 +557,67 @@ __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int6
 
 void launch_apply_any(const void* X, int layout, int64_t ldx, int64_t L, int r, const float* T,
                       float* Xo, void* out_lp_rowmajor, int lp_is_bf16, void* out_bf16_T, int64_t ldT,
-                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st) {
+                      double* colsum_part, int64_t* nblocks_out, cudaStream_t st, int64_t csum_rows) {
+  if (csum_rows < 0) csum_rows = L;
   dim3 grid((unsigned)ceil_div(L, AM), (unsigned)ceil_div(r, AN));
   if (layout == 2)
     k_apply<2><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
-                                     ldT, colsum_part);
+                                     ldT, colsum_part, csum_rows);
   else if (layout == 1)
     k_apply<1><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
-                                     ldT, colsum_part);
+                                     ldT, colsum_part, csum_rows);
   else
     k_apply<0><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
-                                     ldT, colsum_part);
+                                     ldT, colsum_part, csum_rows);
   if (nblocks_out) *nblocks_out = ceil_div(L, AM);
 }
 
 void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
                   int lp_is_bf16, void* out_bf16_T, int64_t ldT, double* colsum_part,
-                  int64_t* nblocks_out, cudaStream_t st) {
+                  int64_t* nblocks_out, cudaStream_t st, int64_t csum_rows) {
   launch_apply_any(X, 0, r, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, out_bf16_T, ldT, colsum_part,
-                   nblocks_out, st);
+                   nblocks_out, st, csum_rows);
+}
+
+// ---------------------------------------------------------------------------
+// History averaging helpers (Section 4.1, Eq. (Ohat)): rows scaled by
+// gamma * sigma_prev[j], and the update of Lbar (Eq. (Lbar)).
+// ---------------------------------------------------------------------------
+namespace {
+template <typename TIn>
+__global__ void k_scale_rows_r(const TIn* __restrict__ in, int64_t ld_in, const double* __restrict__ sigma_prev,
+                               double gamma, int r, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * r) return;
+  const int j = e / r, k = e % r;
+  out[(int64_t)j * r + k] = (float)(gamma * sigma_prev[j] * (double)in[(int64_t)j * ld_in + k]);
+}
+__global__ void k_hist_coeffs(const double* __restrict__ sigma_prev, const double* __restrict__ Lbar_prev,
+                              double weight, int r, double* __restrict__ e) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < r) e[j] = weight * sigma_prev[j] * Lbar_prev[j];
+}
+__global__ void k_lbar(const double* __restrict__ c, const double* __restrict__ sigma, int r,
+                       double* __restrict__ Lbar) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < r) Lbar[j] = sigma[j] > 0.0 ? c[j] / sigma[j] : 0.0;
+}
+}  // namespace
+
+void launch_scale_rows_r(const double* in, int64_t ld_in, const double* sigma_prev, double gamma, int r, float* out,
+                         cudaStream_t st) {
+  k_scale_rows_r<double><<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(in, ld_in, sigma_prev, gamma, r, out);
+}
+void launch_scale_rows_r(const float* in, int64_t ld_in, const double* sigma_prev, double gamma, int r, float* out,
+                         cudaStream_t st) {
+  k_scale_rows_r<float><<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(in, ld_in, sigma_prev, gamma, r, out);
+}
+void launch_hist_coeffs(const double* sigma_prev, const double* Lbar_prev, double weight, int r, double* e,
+                        cudaStream_t st) {
+  k_hist_coeffs<<<1, 256, 0, st>>>(sigma_prev, Lbar_prev, weight, r, e);
+}
+void launch_lbar(const double* c, const double* sigma, int r, double* Lbar, cudaStream_t st) {
+  k_lbar<<<1, 256, 0, st>>>(c, sigma, r, Lbar);
 }
 
 // ---------------------------------------------------------------------------

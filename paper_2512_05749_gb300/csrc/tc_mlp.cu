@@ -290,8 +290,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     k_mf_vjp(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmT,
              const __grid_constant__ CUtensorMap tmY, const int2* __restrict__ chunks,
              const int4* __restrict__ groups, int64_t N, int r, int nmma, const double* __restrict__ ysum,
-             float* __restrict__ Z, bf16* __restrict__ ZT, float* __restrict__ mu_io, uint64_t limit_ns,
-             int* status) {
+             float* __restrict__ Z, bf16* __restrict__ ZT, float* __restrict__ mu_io,
+             const float* __restrict__ Zadd, uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t ybytes = (uint32_t)nmma * 128;
@@ -477,6 +477,11 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         if (ok && c >= 0) {
 #pragma unroll
           for (int k = 0; k < 16; ++k) v[k] -= mu * ys[cc + k < 256 ? cc + k : 255];
+          if (Zadd) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (cc + k < r) v[k] += Zadd[m * r + cc + k];
+          }
           if (ZT) {
 #pragma unroll
             for (int k = 0; k < 16; ++k)
@@ -555,7 +560,7 @@ int tc_mf_jvp_launch(const MlpSource& src, int64_t N, const void* Xblk, int r, i
 
 int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t ldy, int r,
                      const double* ysum, float* Z, void* ZT, float* mu_io, int compute_mu, int64_t wait_us,
-                     int* status, cudaStream_t st) {
+                     int* status, cudaStream_t st, const float* Zadd) {
   const int nmma = mf_nmma(r);
   const size_t smem = vjp_smem(nmma);
   if (smem > 227 * 1024) return -1;
@@ -574,10 +579,10 @@ int tc_mf_vjp_launch(const MlpSource& src, int64_t N, const void* YhatT, int64_t
   const uint64_t lim = (uint64_t)wait_us * 1000ull;
   if (compute_mu)
     k_mf_vjp<true><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, ysum, Z,
-                                                   (bf16*)ZT, mu_io, lim, status);
+                                                   (bf16*)ZT, mu_io, Zadd, lim, status);
   else
     k_mf_vjp<false><<<grid, MF_THREADS, smem, st>>>(tmS, tmT, tmY, src.chunks, src.groups, N, r, nmma, ysum, Z,
-                                                    (bf16*)ZT, mu_io, lim, status);
+                                                    (bf16*)ZT, mu_io, Zadd, lim, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

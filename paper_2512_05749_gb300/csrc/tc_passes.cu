@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
                int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
                const double* __restrict__ ysum, float* __restrict__ Z, bf16* __restrict__ ZT,
-               int64_t ldz, float* __restrict__ mu_io, uint64_t limit_ns, int* status) {
+               int64_t ldz, float* __restrict__ mu_io, const float* __restrict__ Zadd, uint64_t limit_ns,
+               int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t a_bytes = A_BYTES * MT;
@@ -344,6 +345,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (ok && m < M) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 256 ? c + i : 255];
+          if (Zadd) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c + i < r) v[i] += Zadd[m * r + c + i];
+          }
           if (ZT) {
             // K-blocked bf16 operand: for each column the warp writes 32
             // consecutive parameters (64 contiguous bytes)
@@ -375,13 +381,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 // operands; rows = 128 (one accumulator) or 256 (two, TMEM columns 0 and 256).
 // Products of bf16 values are exact; accumulation is FP32 in TMEM.
 // ---------------------------------------------------------------------------
+// CROSS: Gp = XA^T XB with the A tile from tmX and the B tile (nmma rows)
+// from tmB, both loaded per stage; otherwise one tile serves both operands.
+template <bool CROSS>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_gram(const __grid_constant__ CUtensorMap tmX, int r, int nmma, int rows, int tmem_cols,
-              int stages, int k_chunks, int kc_per_split, float* __restrict__ Gp, uint64_t limit_ns,
-              int* status) {
+    k_tc_gram(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, int r, int nmma,
+              int rows, int tmem_cols, int stages, int k_chunks, int kc_per_split, float* __restrict__ Gp,
+              uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  const uint32_t stage_bytes = (uint32_t)rows * BK * 2;
+  const uint32_t a_bytes = (uint32_t)rows * BK * 2;
+  const uint32_t stage_bytes = a_bytes + (CROSS ? (uint32_t)nmma * BK * 2 : 0u);
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int split = blockIdx.x;
@@ -405,15 +415,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = ctl->tmem;
   if (warp == 0) {
     if (lane == 0 && nk > 0)
-      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status,
-               [&](int i, uint8_t* st, uint64_t* bar) { tma_load_3d(st, &tmX, bar, 0, 0, kc0 + i); });
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](int i, uint8_t* st, uint64_t* bar) {
+        tma_load_3d(st, &tmX, bar, 0, 0, kc0 + i);
+        if (CROSS) tma_load_3d(st + a_bytes, &tmB, bar, 0, 0, kc0 + i);
+      });
   } else if (warp == 1) {
     if (lane == 0 && nk > 0) {
       const uint32_t idesc = make_idesc(BM, nmma, 0, 0);
       mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk) {
-          const uint64_t db = smem_desc(sa + kk * 32, 16, 1024);
+          const uint64_t db = smem_desc(sa + (CROSS ? a_bytes : 0u) + kk * 32, 16, 1024);
           for (int a = 0; a < MT; ++a)
             mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + a * 16384 + kk * 32, 16, 1024), db, idesc,
                      (!first || kk > 0) ? 1u : 0u);
@@ -691,7 +703,7 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
                     int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
-                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st) {
+                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st, const float* Zadd) {
   constexpr int MT = 2;
   const int nmma = nmma_for(r);
   const size_t stage = (size_t)A_BYTES * MT + (size_t)nmma * BK * 2;
@@ -710,12 +722,12 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   dim3 grid((unsigned)ceil_div(M, (int64_t)BM * MT));
   if (compute_mu)
     k_tc_passB<true, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                      (bf16*)ZT, ldz, mu_io, (uint64_t)wait_us * 1000ull,
-                                                      status);
+                                                      (bf16*)ZT, ldz, mu_io, Zadd,
+                                                      (uint64_t)wait_us * 1000ull, status);
   else
     k_tc_passB<false, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                       (bf16*)ZT, ldz, mu_io, (uint64_t)wait_us * 1000ull,
-                                                       status);
+                                                       (bf16*)ZT, ldz, mu_io, Zadd,
+                                                       (uint64_t)wait_us * 1000ull, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -726,29 +738,49 @@ int tc_gram_splits(int64_t L, int num_sms) {
   return (int)S;
 }
 
-int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
-                   int* status, cudaStream_t st, int* splits_used) {
+namespace {
+int gram_launch_impl(const void* XA, const void* XB, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                     int* status, cudaStream_t st, int* splits_used) {
+  const bool cross = XB != nullptr;
   const int nmma = nmma_for(r);
   const int rows = r <= 128 ? 128 : 256;
   const int tmem_cols = rows == 256 ? 512 : tmem_cols_for(nmma);
-  const size_t stage = (size_t)rows * BK * 2;
+  const size_t stage = (size_t)rows * BK * 2 + (cross ? (size_t)nmma * BK * 2 : 0);
   size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
   if (stages > MAX_STAGES) stages = MAX_STAGES;
-  CUtensorMap tm;
-  if (!encode_blocked(&tm, XT, L, r, (uint32_t)rows)) return -1;
+  CUtensorMap tm, tmb;
+  if (!encode_blocked(&tm, XA, L, r, (uint32_t)rows)) return -1;
+  if (!encode_blocked(&tmb, cross ? XB : XA, L, r, (uint32_t)nmma)) return -1;
   const int k_chunks = (int)ceil_div(L, BK);
   const int kc_per_split = (int)ceil_div(k_chunks, splits);
   const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
   const size_t smem = 1024 + stages * stage + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  k_tc_gram<<<s_eff, THREADS, smem, st>>>(tm, r, nmma, rows, tmem_cols, (int)stages, k_chunks, kc_per_split,
-                                          Gp, (uint64_t)wait_us * 1000ull, status);
+  if (cross)
+    k_tc_gram<true><<<s_eff, THREADS, smem, st>>>(tm, tmb, r, nmma, rows, tmem_cols, (int)stages, k_chunks,
+                                                  kc_per_split, Gp, (uint64_t)wait_us * 1000ull, status);
+  else
+    k_tc_gram<false><<<s_eff, THREADS, smem, st>>>(tm, tmb, r, nmma, rows, tmem_cols, (int)stages, k_chunks,
+                                                   kc_per_split, Gp, (uint64_t)wait_us * 1000ull, status);
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+}
+}  // namespace
+
+int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                   int* status, cudaStream_t st, int* splits_used) {
+  (void)ld;
+  return gram_launch_impl(XT, nullptr, L, r, splits, Gp, wait_us, status, st, splits_used);
+}
+
+int tc_xgram_launch(const void* XA, const void* XB, int64_t L, int r, int splits, float* Gp, int64_t wait_us,
+                    int* status, cudaStream_t st, int* splits_used) {
+  return gram_launch_impl(XA, XB, L, r, splits, Gp, wait_us, status, st, splits_used);
 }
 
 int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, const float* g,

@@ -74,6 +74,8 @@ struct wssr_ctx {
   void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
   double* cpart = nullptr;        // per-tile partials of V^T g fused into the rotation
   bool c_ready = false;           // h->c already holds V_out^T g
+  void* Vhp = nullptr;            // history averaging: bf16 K-blocked copy of V_prev
+  float* gbar = nullptr;          // history averaging: the averaged gradient (M)
   int gram_splits_tc = 1;
 
   // profiling: event pairs around kernel groups
@@ -101,7 +103,7 @@ void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart};
+                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -191,7 +193,7 @@ wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const void* Xop, float*
 // (bf16 transposed for tcgen05; for SIMT + bf16 the float result in h->Z is
 // cast to bf16 row-major). Returns the operand pointer in *Xop_out. ----
 wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float* Zf,
-                   const void** Xop_out, cudaStream_t st) {
+                   const void** Xop_out, cudaStream_t st, const float* Zadd = nullptr) {
   const int64_t N = h->N, M = h->M;
   const int r = h->r;
   {
@@ -200,13 +202,13 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
       void* ZT = Zf ? nullptr : h->Xhat;
       const MlpSource src = mlp_source(op->mlp);
       int rc = tc_mf_vjp_launch(src, N, Yop, h->ldy, r, h->ysum, Zf, ZT, h->mu, h->mu_valid ? 0 : 1,
-                                h->opt.wait_cap, h->status, st);
+                                h->opt.wait_cap, h->status, st, Zadd);
       if (rc != 0) return WSSR_ERR_UNSUPPORTED;
       h->mu_valid = true;
     } else if (h->use_tc) {
       void* ZT = Zf ? nullptr : h->Xhat;
       int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Zf, ZT, h->ldx, h->mu,
-                               h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st);
+                               h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st, Zadd);
       if (rc != 0) return WSSR_ERR_UNSUPPORTED;
       h->mu_valid = true;
     } else if (is_bf16(h)) {
@@ -247,60 +249,110 @@ void factor_operand(wssr_ctx* h, const void* Xop, float* T_out, cudaStream_t st)
   h->launches += 3;
 }
 
-// One Cholesky QR pass on a float block: Xo = X R^-1 (optional operand copies / column sums).
+// History averaging (Section 4.1, Eq. (Ohat)): the sample-side block gets r
+// extra rows gamma diag(sigma_prev) V_prev^T X after the N sample rows, with
+// gamma = sqrt(w N / (1 - w)), so that (1 - w)/N (Y^T Y) = X^T S-bar X with
+// S-bar = (1 - w) O_c^T O_c / N + w V_prev diag(sigma_prev^2) V_prev^T.
+struct Hist {
+  double weight, gamma, hscale;  // hscale = (1 - w) / N replaces 1 / N in the Rayleigh-Ritz Grams
+  const double* sigma_prev;
+};
+
+int64_t rows_of(const wssr_ctx* h, const Hist* hist) { return h->N + (hist ? h->r : 0); }
+
+// One Cholesky QR pass on a float block: Xo = X R^-1 (optional operand copies /
+// column sums over the first csum_rows rows).
 void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row, void* lpT,
-                 int64_t ldT, double* colsum_part, int64_t* nb_out, cudaStream_t st) {
+                 int64_t ldT, double* colsum_part, int64_t* nb_out, cudaStream_t st, int64_t csum_rows = -1) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_ORTH, st);
   launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
   launch_chol_inv(h->G, r, h->TY, h->status, h->status + 1, st);
-  launch_apply(X, L, r, h->TY, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st);
+  launch_apply(X, L, r, h->TY, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st, csum_rows);
   h->launches += 4;
 }
 
-// Orthonormalise Y (one Cholesky QR pass) into h->Y2 and produce the pass B operand.
-const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, cudaStream_t st) {
+// The r history rows of Y: Y[N + j, :] = gamma sigma_prev[j] (V_prev^T Xop)[j, :].
+void history_rows(wssr_ctx* h, const Hist* hist, const void* Xop, float* Y, cudaStream_t st) {
+  Timed tm(h, WSSR_KCAT_PASS_A, st);
+  const int r = h->r;
+  int used = 0;
+  tc_xgram_launch(h->Vhp, Xop, h->M, r, h->gram_splits_tc, h->tc_gram_part, h->opt.wait_cap, h->status, st,
+                  &used);
+  launch_sum_partials(h->tc_gram_part, used, r, 1.0, h->G, st);
+  launch_scale_rows_r(h->G, r, hist->sigma_prev, hist->gamma, r, Y + h->N * r, st);
+  h->launches += 3;
+}
+
+// History term of pass B, gamma V_prev diag(sigma_prev) Q_bot (M x r, FP32,
+// into h->Z), with Q_bot the history rows of the orthonormalised block.
+void history_pass_B_term(wssr_ctx* h, const Hist* hist, const float* Q, cudaStream_t st) {
+  Timed tm(h, WSSR_KCAT_PASS_B, st);
+  const int r = h->r;
+  launch_scale_rows_r(Q + h->N * r, r, hist->sigma_prev, hist->gamma, r, h->TW, st);
+  launch_split3_T(h->TW, r, h->TWT3, st);
+  tc_rotate_launch(h->Vhp, h->M, r, h->TWT3, h->Z, nullptr, nullptr, h->opt.wait_cap, h->status, st);
+  h->launches += 3;
+}
+
+// Orthonormalise Y (one Cholesky QR pass over L rows) into h->Y2 and produce
+// the pass B operand (column sums over the N sample rows).
+const void* orth_Y_and_operand(wssr_ctx* h, const float* Y, int64_t L, cudaStream_t st) {
   const int64_t N = h->N;
   int64_t nb = 0;
   void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
   void* lpT = h->use_tc ? h->Yhat : nullptr;
-  cholqr_pass(h, Y, N, h->Y2, lp_row, lpT, h->ldy, h->csum_part, &nb, st);
+  cholqr_pass(h, Y, L, h->Y2, lp_row, lpT, h->ldy, h->csum_part, &nb, st, N);
   launch_colsum_finalize(h->csum_part, nb, h->r, h->ysum, st);
   h->launches++;
   if (h->use_tc || is_bf16(h)) return h->Yhat;
   return h->Y2;
 }
 
-// Y <- Y T (N x r times r x r) through h->Y2.
-void right_multiply_Y(wssr_ctx* h, float* Y, const float* T, cudaStream_t st) {
+// Y <- Y T (L x r times r x r) through h->Y2.
+void right_multiply_Y(wssr_ctx* h, float* Y, const float* T, int64_t L, cudaStream_t st) {
   Timed tm(h, WSSR_KCAT_ORTH, st);
-  launch_apply(Y, h->N, h->r, T, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
-  cudaMemcpyAsync(Y, h->Y2, (size_t)h->N * h->r * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  launch_apply(Y, L, h->r, T, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  cudaMemcpyAsync(Y, h->Y2, (size_t)L * h->r * sizeof(float), cudaMemcpyDeviceToDevice, st);
   h->launches++;
 }
 
-// Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
+// Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma
+// written. With hist, the operator is the history-averaged one (r extra rows).
 wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, int m, float* V_out,
-                   double* sigma, const float* g, cudaStream_t st) {
+                   double* sigma, const float* g, cudaStream_t st, const Hist* hist = nullptr) {
   const int64_t N = h->N, M = h->M;
   const int r = h->r;
+  const int64_t L = rows_of(h, hist);
+  const double gscale = hist ? hist->hscale : 1.0 / (double)N;
   wssr_status s;
   h->mu_valid = false;
-  const void* Xop = cast_X_operand(h, V_start, st);
+  const void* Xop;
+  if (hist) {
+    // V_prev's operand copy is kept for the history rows; pass B writes the next basis into Xhat
+    launch_cast(V_start, M, r, nullptr, 1, h->Vhp, 0, nullptr, st);
+    h->launches++;
+    Xop = h->Vhp;
+  } else {
+    Xop = cast_X_operand(h, V_start, st);
+  }
   bool have_T = false;
   for (int it = 0; it < m; ++it) {
     if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
-    if (have_T) right_multiply_Y(h, h->Y, h->TX, st);
-    const void* Yop = orth_Y_and_operand(h, h->Y, st);
-    if ((s = pass_B(h, op, Yop, nullptr, &Xop, st)) != WSSR_OK) return s;
+    if (hist) history_rows(h, hist, Xop, h->Y, st);
+    if (have_T) right_multiply_Y(h, h->Y, h->TX, L, st);
+    const void* Yop = orth_Y_and_operand(h, h->Y, L, st);
+    if (hist) history_pass_B_term(h, hist, h->Y2, st);
+    if ((s = pass_B(h, op, Yop, nullptr, &Xop, st, hist ? h->Z : nullptr)) != WSSR_OK) return s;
     factor_operand(h, Xop, h->TX, st);
     have_T = true;
   }
   // Rayleigh-Ritz on span(Xh) = span(Xh TX)
   if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
-  right_multiply_Y(h, h->Y, h->TX, st);
+  if (hist) history_rows(h, hist, Xop, h->Y, st);
+  right_multiply_Y(h, h->Y, h->TX, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
-  launch_gram(h->Y, N, r, h->gram_part, h->G, 1.0 / (double)N, st);
+  launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
   launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
   launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->opt.jacobi_sweeps, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
@@ -319,8 +371,8 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
                      nullptr, st);
     h->launches += 1;
   }
-  launch_apply(h->Y, N, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
-  launch_gram(h->Y2, N, r, h->gram_part, h->Hp, 1.0 / (double)N, st);
+  launch_apply(h->Y, L, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  launch_gram(h->Y2, L, r, h->gram_part, h->Hp, gscale, st);
   // Gram (2), Jacobi and its eigenvector replay (2), T W (1), Y W (1), Gram (2)
   h->launches += 2 + 2 + 1 + 1 + 2;
   double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
@@ -385,6 +437,7 @@ void wssr_default_options(wssr_options* opt) {
   opt->wait_cap = 2000000;
   opt->engine = WSSR_ENGINE_AUTO;
   opt->jacobi_sweeps = 12;
+  opt->history = 0;
 }
 
 wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const wssr_options* opt_in,
@@ -402,6 +455,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (opt.apply_mode == WSSR_APPLY_CUTOFF && !(opt.sigma_floor > 0.0)) return WSSR_ERR_INVALID_ARG;
   if (opt.engine < WSSR_ENGINE_AUTO || opt.engine > WSSR_ENGINE_TCGEN05) return WSSR_ERR_INVALID_ARG;
   if (opt.wait_cap < 1) return WSSR_ERR_INVALID_ARG;
+  if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;
 
   wssr_ctx* h = new (std::nothrow) wssr_ctx();
   if (!h) return WSSR_ERR_OOM;
@@ -431,19 +485,20 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   h->splits_tc = h->use_tc ? tc_passA_splits(N, M, r, h->num_sms) : 1;
   h->splits_mf = (h->use_tc && M % 64 == 0) ? tc_mf_jvp_splits(N, M / 64, r, h->num_sms) : 1;
   h->ldx = (M + 7) / 8 * 8;
-  h->ldy = (N + 7) / 8 * 8;
+  h->ldy = (N + r + 7) / 8 * 8;  // the operand copy of Y also holds the history rows
   // pass A partials: one N x r block per split
   h->yp_elems = (int64_t)std::max(h->use_tc ? h->splits_tc : h->splits_simt, h->splits_mf) * N * r;
   // column-sum partials: split reduction (16-row blocks of Y), casts and applies (64-row blocks)
-  const int64_t blocks64 = std::max(ceil_div(N, 16), ceil_div(std::max(N, M), 64));
-  const int64_t gpart = std::max(gram_part_elems(N, r), gram_part_elems(M, r));
+  const int64_t blocks64 = std::max(ceil_div(N, 16), ceil_div(std::max(N + r, M), 64));
+  const int64_t gpart = std::max(gram_part_elems(N + r, r), gram_part_elems(M, r));
   cudaError_t e = cudaSuccess;
 #define ALLOC(p, bytes) \
   if (e == cudaSuccess) e = dalloc(&h->p, (bytes))
   ALLOC(status, 2 * sizeof(int));
   ALLOC(Yp, h->yp_elems * f);
-  ALLOC(Y, (size_t)N * r * f);
-  ALLOC(Y2, (size_t)N * r * f);
+  // sample-side blocks carry r extra rows (history averaging)
+  ALLOC(Y, (size_t)(N + r) * r * f);
+  ALLOC(Y2, (size_t)(N + r) * r * f);
   ALLOC(csum_part, (size_t)blocks64 * r * d);
   ALLOC(mean_r, (size_t)r * d);
   ALLOC(ysum, (size_t)r * d);
@@ -474,6 +529,10 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
     ALLOC(tc_gram_part, (size_t)h->gram_splits_tc * r * r * f);
     ALLOC(TWT3, (size_t)3 * r * r * 2);
     ALLOC(cpart, (size_t)tc_rotate_cpart_rows(M) * r * d);
+    if (opt.history) {
+      ALLOC(Vhp, (size_t)blk_elems(M, r) * 2);
+      ALLOC(gbar, (size_t)M * f);
+    }
   }
 #undef ALLOC
   if (e != cudaSuccess) {
@@ -504,6 +563,41 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g, st)) != WSSR_OK) return s;
   return woodbury(h, V_out, sigma, g, delta, st);
+}
+
+wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const float* g, const float* V_prev,
+                               const double* sigma_prev, const double* Lbar_prev, double weight, float* delta,
+                               double* sigma, float* V_out, double* Lbar_out, float* gbar_out,
+                               wssr_stream_t stream) {
+  if (!h || !g || !V_prev || !sigma_prev || !Lbar_prev || !delta || !sigma || !V_out || !Lbar_out)
+    return WSSR_ERR_INVALID_ARG;
+  if (!(weight >= 0.0 && weight < 1.0)) return WSSR_ERR_INVALID_ARG;
+  if (!h->opt.history || !h->use_tc) return WSSR_ERR_UNSUPPORTED;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  h->mu_valid = false;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
+  const int r = h->r;
+  {
+    // gbar = (1 - w) g + w V_prev (sigma_prev * Lbar_prev)  (Eq. (barg), (Lhat))
+    Timed tm(h, WSSR_KCAT_APPLY, st);
+    launch_hist_coeffs(sigma_prev, Lbar_prev, weight, r, h->e, st);
+    launch_woodbury(V_prev, g, h->e, h->M, r, 1.0 / (1.0 - weight), h->gbar, st);
+    h->launches += 2;
+  }
+  Hist hist{weight, sqrt(weight * (double)h->N / (1.0 - weight)), (1.0 - weight) / (double)h->N, sigma_prev};
+  if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, h->gbar, st, &hist)) != WSSR_OK) return s;
+  if ((s = woodbury(h, V_out, sigma, h->gbar, delta, st)) != WSSR_OK) return s;
+  // Lbar = diag(1/sigma) V_out^T gbar (Eq. (Lbar)); h->c holds V_out^T gbar
+  launch_lbar(h->c, sigma, r, Lbar_out, st);
+  h->launches++;
+  if (gbar_out &&
+      cudaMemcpyAsync(gbar_out, h->gbar, (size_t)h->M * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return WSSR_ERR_CUDA;
+  return check_launch(h);
 }
 
 wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const float* V_rand,

@@ -40,7 +40,7 @@ EXPORTED = [
     "wssr_last_launch_count", "wssr_destroy", "wssr_status_string", "wssr_profile_begin",
     "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
-    "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad",
+    "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -58,6 +58,8 @@ class wssr_options(ctypes.Structure):
         ("wait_cap", ctypes.c_int64),
         ("engine", ctypes.c_int32),
         ("jacobi_sweeps", ctypes.c_int32),
+        ("history", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -122,6 +124,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_create": (i32, [i64, i64, i32, f64, P(wssr_options), P(vp)]),
         "wssr_step": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp]),
         "wssr_init_subspace": (i32, [vp, P(wssr_operator), vp, vp, vp, vp]),
+        "wssr_step_averaged": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, vp]),
         "wssr_apply_O": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_apply_Ot": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_orthonormalize": (i32, [vp, vp, i64, i32, vp]),
@@ -210,6 +213,13 @@ def wssr_create(N: int, M: int, r: int, lam: float, opt: Optional[wssr_options] 
 def wssr_step(h: int, op: wssr_operator, g, V_prev, delta, sigma, V_out, stream=None):
     _check(load().wssr_step(h, ctypes.byref(op), _ptr(g), _ptr(V_prev), _ptr(delta), _ptr(sigma),
                             _ptr(V_out), _stream(stream)), "wssr_step")
+
+
+def wssr_step_averaged(h: int, op: wssr_operator, g, V_prev, sigma_prev, Lbar_prev, weight: float, delta, sigma,
+                       V_out, Lbar_out, gbar_out=None, stream=None):
+    _check(load().wssr_step_averaged(h, ctypes.byref(op), _ptr(g), _ptr(V_prev), _ptr(sigma_prev), _ptr(Lbar_prev),
+                                     float(weight), _ptr(delta), _ptr(sigma), _ptr(V_out), _ptr(Lbar_out),
+                                     _ptr(gbar_out), _stream(stream)), "wssr_step_averaged")
 
 
 def wssr_init_subspace(h: int, op: wssr_operator, V_rand, V_out, sigma=None, stream=None):
@@ -339,9 +349,10 @@ class WSSR:
 
     def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
                  dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
-                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000):
+                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000, history: bool = False):
         opt = wssr_default_options()
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
+        opt.history = 1 if history else 0
         opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]
         opt.apply_mode = {"damped": WSSR_APPLY_DAMPED, "cutoff": WSSR_APPLY_CUTOFF}[apply_mode]
         opt.sigma_floor = sigma_floor
@@ -383,6 +394,22 @@ class WSSR:
             delta, sigma, V = out
         wssr_step(self.handle, self._op(O), g, V_prev, delta, sigma, V, stream)
         return delta, sigma, V
+
+    def step_averaged(self, O, g, V_prev, sigma_prev, Lbar_prev, weight: float, out=None, stream=None):
+        """History-averaged step (Section 4.1): returns (delta, sigma, V, Lbar, gbar)."""
+        import torch
+        dev = g.device
+        if out is None:
+            delta = torch.empty(self.M, device=dev, dtype=torch.float32)
+            sigma = torch.empty(self.r, device=dev, dtype=torch.float64)
+            V = torch.empty(self.M, self.r, device=dev, dtype=torch.float32)
+            Lbar = torch.empty(self.r, device=dev, dtype=torch.float64)
+            gbar = torch.empty(self.M, device=dev, dtype=torch.float32)
+        else:
+            delta, sigma, V, Lbar, gbar = out
+        wssr_step_averaged(self.handle, self._op(O), g, V_prev, sigma_prev, Lbar_prev, weight, delta, sigma, V,
+                           Lbar, gbar, stream)
+        return delta, sigma, V, Lbar, gbar
 
     def init_subspace(self, O, V_rand, stream=None):
         import torch
