@@ -183,6 +183,7 @@ def run_reference(args, w):
 
 def workload_config(w, args, engine):
     return {"workload": w.name, "N": w.N, "M": w.M, "r": w.r, "lambda": w.lam, "m": w.m,
+            "history_weight": args.history,
             "o_dtype": args.dtype, "engine": engine, "parallelism": f"replicas{args.gpus}",
             "l2": f"inputs larger than L2 (O = {w.N * w.M * (2 if args.dtype == 'bf16' else 4) / 1e9:.1f} GB)"}
 
@@ -248,6 +249,32 @@ def step_roofline_ms(w, args, peaks):
     return passes * max(t_bytes, t_flop) * 1e3
 
 
+class Stepper:
+    """One WSSR step per call: the plain step, or the history-averaged step with
+    sigma and Lbar carried from call to call (double-buffered)."""
+
+    def __init__(self, s, r, dev, weight):
+        import torch
+        self.s, self.w = s, weight
+        self.sig = [torch.zeros(r, device=dev, dtype=torch.float64) for _ in range(2)]
+        self.lb = [torch.zeros(r, device=dev, dtype=torch.float64) for _ in range(2)]
+        self.gbar = None
+        self.k = 0
+
+    def __call__(self, O, g, V, delta, sigma, V_out):
+        if self.w <= 0.0:
+            self.s.step(O, g, V, out=(delta, sigma, V_out))
+            return
+        import torch
+        if self.gbar is None:
+            self.gbar = torch.empty_like(g)
+        i, j = self.k & 1, (self.k & 1) ^ 1
+        self.s.step_averaged(O, g, V, self.sig[i], self.lb[i], self.w,
+                             out=(delta, self.sig[j], V_out, self.lb[j], self.gbar))
+        sigma.copy_(self.sig[j])
+        self.k += 1
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -273,7 +300,9 @@ def run_ours(args, w):
     V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
     torch.cuda.synchronize()
 
-    s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine)
+    s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine,
+             history=args.history > 0)
+    step = Stepper(s, w.r, dev, args.history)
     engine_name = "tcgen05" if (args.dtype == "bf16" and s.handle and args.engine != "simt"
                                 and _uses_tc(s)) else "simt"
     V, _ = s.init_subspace(O, V0)
@@ -282,7 +311,7 @@ def run_ours(args, w):
     sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
     Vb = torch.empty_like(V)
     for t in range(args.warmup):
-        s.step(O, gs[t % len(gs)], V, out=(delta, sigma, Vb))
+        step(O, gs[t % len(gs)], V, delta, sigma, Vb)
         V, Vb = Vb, V
     s.check("warmup")
 
@@ -298,7 +327,7 @@ def run_ours(args, w):
     launches = 0
     e0.record(stream)
     for t in range(args.steps):
-        s.step(O, gs[t], V, out=(delta, sigma, Vb))
+        step(O, gs[t], V, delta, sigma, Vb)
         launches += s.last_launch_count()
         V, Vb = Vb, V
     e1.record(stream)
@@ -333,7 +362,7 @@ def run_ours(args, w):
         for t in range(args.e2e_steps):
             O.copy_(O_host, non_blocking=True)
             gs[t].copy_(g_host[t], non_blocking=True)
-            s.step(O, gs[t], V, out=(delta, sigma, Vb))
+            step(O, gs[t], V, delta, sigma, Vb)
             V, Vb = Vb, V
             d_host.copy_(delta, non_blocking=True)
             s_host.copy_(sigma, non_blocking=True)
@@ -541,7 +570,9 @@ def run_mlp_mf(args, w):
     xs = [wl.electrons_torch(w.N, dev, w.n_electrons, w.coord_std, "bench", t) for t in range(nsteps + 1)]
     g_user = wl.gradient_torch(w.M, 0, dev, "bench")
     g = ans.pad(g_user)
-    s = WSSR(w.N, ans.Mp, w.r, w.lam, m=w.m, m_init=args.m_init, dtype="bf16", engine="tcgen05")
+    s = WSSR(w.N, ans.Mp, w.r, w.lam, m=w.m, m_init=args.m_init, dtype="bf16", engine="tcgen05",
+             history=args.history > 0)
+    step = Stepper(s, w.r, dev, args.history)
     V, _ = s.init_subspace(ans.operator(theta, xs[0]), ans.pad(wl.start_subspace_torch(w.M, w.r, dev, "bench")))
     s.check("init_subspace")
     delta = torch.empty(ans.Mp, device=dev)
@@ -554,7 +585,7 @@ def run_mlp_mf(args, w):
         theta.sub_(d_user * (1e-3 * theta.norm() / d_user.norm()))
 
     for t in range(args.warmup):
-        s.step(ans.operator(theta, xs[1 + t]), g, V, out=(delta, sigma, Vb))
+        step(ans.operator(theta, xs[1 + t]), g, V, delta, sigma, Vb)
         sr_update()
         V, Vb = Vb, V
     s.check("warmup")
@@ -570,7 +601,7 @@ def run_mlp_mf(args, w):
     launches = 0
     e0.record(stream)
     for t in range(args.steps):
-        s.step(ans.operator(theta, xs[1 + args.warmup + t]), g, V, out=(delta, sigma, Vb))
+        step(ans.operator(theta, xs[1 + args.warmup + t]), g, V, delta, sigma, Vb)
         launches += s.last_launch_count()
         sr_update()
         V, Vb = Vb, V
@@ -602,7 +633,7 @@ def run_mlp_mf(args, w):
         for t in range(args.e2e_steps):
             th_dev.copy_(th_host, non_blocking=True)
             x_dev.copy_(x_host[t], non_blocking=True)
-            s.step(ans.operator(th_dev, x_dev), g, V, out=(delta, sigma, Vb))
+            step(ans.operator(th_dev, x_dev), g, V, delta, sigma, Vb)
             V, Vb = Vb, V
             d_host.copy_(ans.unpad(delta), non_blocking=True)
             s_host.copy_(sigma, non_blocking=True)
@@ -681,6 +712,7 @@ def run_mlp_mf(args, w):
             "dtype": "bf16", "data": "synthetic",
             "config": {"workload": w.name, "widths": list(w.widths), "N": w.N, "M": w.M, "M_padded": ans.Mp,
                        "r": w.r, "lambda": w.lam, "m": w.m, "engine": "tcgen05 matrix-free",
+                       "history_weight": args.history,
                        "parallelism": f"replicas{world}",
                        "l2": "operand source (activations+adjoints, ~104 MB bf16) is L2-resident by design; "
                              "the basis blocks (1.1 GB) exceed L2"},
@@ -721,6 +753,9 @@ def main():
     ap.add_argument("--compare-f32", type=int, default=0,
                     help="also time this many steps of the plain FP32 (SIMT) path on the FP32 master "
                          "of the same planted matrix and report the speedup and the delta difference")
+    ap.add_argument("--history", type=float, default=0.0,
+                    help="history-averaging weight w in [0, 1) (Section 4.1): run wssr_step_averaged "
+                         "with sigma and Lbar carried from step to step")
     ap.add_argument("--materialise", action="store_true",
                     help="MLP workloads: form O with the per-sample Jacobian kernel instead of the "
                          "matrix-free operator")

@@ -63,7 +63,12 @@ typedef enum {
 } wssr_status;
 
 enum { WSSR_DTYPE_F32 = 0, WSSR_DTYPE_BF16 = 1 };
-enum { WSSR_APPLY_DAMPED = 0, WSSR_APPLY_CUTOFF = 1 };
+/* DAMPED: [V diag(1/(sigma^2+lambda)) V^T + lambda^-1 (I - V V^T)] g.
+ * CUTOFF: the paper's (S^dagger + sigma_floor^-1 S^perp) g (Eq. (updated_sr_1)).
+ * PINV:   the truncated pseudo-inverse V diag(sigma_i^dagger)^2 V^T g of Eq. (svd0),
+ *         Eq. (sigmaplus): S-eigenvalues sigma_i^2 below eps_tol sigma_1^2 are dropped;
+ *         options.sigma_floor holds eps_tol (0 < eps_tol <= 1); no complement term. */
+enum { WSSR_APPLY_DAMPED = 0, WSSR_APPLY_CUTOFF = 1, WSSR_APPLY_PINV = 2 };
 enum { WSSR_OP_DENSE = 0, WSSR_OP_MLP = 1 };
 /* Product engines for the two O passes. AUTO = tcgen05 tensor cores for
  * BF16 when the shape allows it, SIMT FMA otherwise. */
@@ -75,7 +80,8 @@ typedef struct {
   int32_t dtype;        /* WSSR_DTYPE_*: element type of O in memory (default F32) */
   int32_t apply_mode;   /* WSSR_APPLY_* (default DAMPED) */
   double sigma_floor;   /* CUTOFF mode: the paper's sigma_floor, in S-eigenvalue
-                           units (> 0); ignored for DAMPED */
+                           units (> 0); PINV mode: eps_tol (0 < eps_tol <= 1);
+                           ignored for DAMPED */
   int64_t wait_cap;     /* bound of every device wait, microseconds of GPU time (default 2000000);
                            on expiry the kernel records WSSR_ERR_DEVICE_TIMEOUT and returns */
   int32_t engine;       /* WSSR_ENGINE_* (default AUTO) */

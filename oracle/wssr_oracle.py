@@ -41,7 +41,7 @@ __all__ = [
     "column_mean", "centre", "householder_qr", "jacobi_svd", "orth",
     "subspace_iteration", "rayleigh_ritz", "fix_signs", "woodbury_apply",
     "wssr_step", "init_subspace", "projector_distance", "S_matvec",
-    "history_operator", "averaged_gradient", "wssr_step_averaged",
+    "history_operator", "averaged_gradient", "wssr_step_averaged", "local_energy_gradient",
 ]
 
 
@@ -197,6 +197,10 @@ def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
     ``cutoff``: the paper's form (S^dagger + sigma_floor^-1 S^perp) g with
     S^dagger = V diag(sigma^-2) V^T and S^perp = I - V V^T, i.e.
     d_i = 1/sigma_i^2 - 1/sigma_floor (sigma_floor in S-eigenvalue units).
+
+    ``pinv``: the truncated pseudo-inverse S^dagger g of Eq. (svd0) with the
+    cutoff of Eq. (sigmaplus) on the S-eigenvalues sigma_i^2: 1/sigma_i^2 when
+    sigma_i^2 >= eps_tol max_j sigma_j^2, else 0 (eps_tol passed as sigma_floor).
     """
     V = np.asarray(V, dtype=np.float64)
     sigma = np.asarray(sigma, dtype=np.float64)
@@ -211,6 +215,10 @@ def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
             sigma_floor = lam
         d = 1.0 / s2 - 1.0 / sigma_floor
         return g / sigma_floor + V @ (d * c)
+    if mode == "pinv":
+        keep = (s2 > 0) & (s2 >= sigma_floor * s2.max())
+        d = np.where(keep, 1.0 / np.where(keep, s2, 1.0), 0.0)
+        return V @ (d * c)
     raise ValueError(mode)
 
 
@@ -228,6 +236,15 @@ def wssr_step(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: i
     V = fix_signs(V)
     delta = woodbury_apply(V, sigma, g, lam, mode, sigma_floor)
     return delta, sigma, V
+
+
+def local_energy_gradient(O: np.ndarray, E_loc: np.ndarray) -> np.ndarray:
+    """The VMC gradient estimate of Eq. (gradient:vmc): g = (2/N) sum_n O_c[n, :]
+    (E_L(x_n) - L_N) with L_N the sample mean of the local energies, i.e.
+    g = 2 O_N Lbar_N with Lbar_N = (E_L - L_N) / sqrt(N) (Eq. (Lbarn))."""
+    Oc = centre(O)
+    E = np.asarray(E_loc, dtype=np.float64)
+    return 2.0 * Oc.T @ (E - E.mean()) / Oc.shape[0]
 
 
 def history_operator(O: np.ndarray, V_prev: np.ndarray, sigma_prev: np.ndarray, weight: float) -> np.ndarray:

@@ -20,6 +20,7 @@
 // later reads, so nothing has to start at zero; but two calls whose kernels
 // overlap on the GPU (different streams, or different host threads without
 // ordering) race on the array and give wrong results.
+#include <math.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -67,8 +68,10 @@ extern "C" wssr_status wssr_woodbury_noalloc(const float* V, const double* sigma
   if (!V || !sigma || !g || !delta) return WSSR_ERR_INVALID_ARG;
   if (M < 1 || r < 1 || r > kMaxR) return WSSR_ERR_INVALID_ARG;
   if (!(lambda > 0.0)) return WSSR_ERR_INVALID_ARG;
-  if (apply_mode != WSSR_APPLY_DAMPED && apply_mode != WSSR_APPLY_CUTOFF) return WSSR_ERR_INVALID_ARG;
+  if (apply_mode != WSSR_APPLY_DAMPED && apply_mode != WSSR_APPLY_CUTOFF && apply_mode != WSSR_APPLY_PINV)
+    return WSSR_ERR_INVALID_ARG;
   if (apply_mode == WSSR_APPLY_CUTOFF && !(sigma_floor > 0.0)) return WSSR_ERR_INVALID_ARG;
+  if (apply_mode == WSSR_APPLY_PINV && !(sigma_floor > 0.0 && sigma_floor <= 1.0)) return WSSR_ERR_INVALID_ARG;
   if (wssr::dot_part_elems(M, r) > (int64_t)kPartDoubles) return WSSR_ERR_INVALID_ARG;
   int dev = -1;
   double* base = scratch_for_current_device(&dev);
@@ -79,7 +82,9 @@ extern "C" wssr_status wssr_woodbury_noalloc(const float* V, const double* sigma
   cudaStream_t st = (cudaStream_t)stream;
   wssr::launch_dot(V, g, M, r, part, c, st);
   wssr::launch_woodbury_coeffs(sigma, c, r, lambda, apply_mode, sigma_floor, e, nullptr, st);
-  const double lam_eff = (apply_mode == WSSR_APPLY_CUTOFF) ? sigma_floor : lambda;
+  const double lam_eff = apply_mode == WSSR_APPLY_CUTOFF ? sigma_floor
+                         : apply_mode == WSSR_APPLY_PINV ? INFINITY
+                                                         : lambda;
   wssr::launch_woodbury(V, g, e, M, r, lam_eff, delta, st);
   return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }

@@ -1080,6 +1080,10 @@ __global__ void k_woodbury_coeffs(const double* __restrict__ sigma, const double
   double d;
   if (mode == WSSR_APPLY_CUTOFF) {
     d = (s2 > 0.0) ? 1.0 / s2 - 1.0 / floor_ : 0.0;
+  } else if (mode == WSSR_APPLY_PINV) {
+    // pseudo-inverse of Eq. (sigmaplus): 1/s2 when s2 >= eps_tol s2_max (sigma descending), else 0
+    const double s2max = sigma[0] * sigma[0];
+    d = (s2 > 0.0 && s2 >= floor_ * s2max) ? 1.0 / s2 : 0.0;
   } else {
     d = -s2 / (lam * (s2 + lam));
   }

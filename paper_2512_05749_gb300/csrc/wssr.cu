@@ -14,6 +14,7 @@
 //   Rayleigh-Ritz: Y = (O_c Xh) T_X, H = Y^T Y / N (FP64), Jacobi H = W L W^T,
 //     V_out = Xh (T_X W), sigma_i^2 = FP64 Rayleigh quotients of Y W
 //   apply:  c = V_out^T g, delta = g / lam + V_out (d * c)
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -387,7 +388,10 @@ wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const flo
   Timed tm(h, WSSR_KCAT_APPLY, st);
   if (!h->c_ready) launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
   h->c_ready = false;
-  const double lam_eff = (h->opt.apply_mode == WSSR_APPLY_CUTOFF) ? h->opt.sigma_floor : h->lam;
+  // complement weight 1/lam_eff: 1/lambda (damped), 1/sigma_floor (cutoff), none (pseudo-inverse)
+  const double lam_eff = h->opt.apply_mode == WSSR_APPLY_CUTOFF ? h->opt.sigma_floor
+                         : h->opt.apply_mode == WSSR_APPLY_PINV ? INFINITY
+                                                                : h->lam;
   launch_woodbury_coeffs(sigma, h->c, r, h->lam, h->opt.apply_mode, h->opt.sigma_floor, h->e,
                          h->status, st);
   launch_woodbury(V, g, h->e, h->M, r, lam_eff, delta, st);
@@ -451,8 +455,12 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (!(lambda > 0.0)) return WSSR_ERR_INVALID_ARG;
   if (opt.m < 1 || opt.m_init < 1 || opt.jacobi_sweeps < 1 || opt.jacobi_sweeps > 64) return WSSR_ERR_INVALID_ARG;
   if (opt.dtype != WSSR_DTYPE_F32 && opt.dtype != WSSR_DTYPE_BF16) return WSSR_ERR_INVALID_ARG;
-  if (opt.apply_mode != WSSR_APPLY_DAMPED && opt.apply_mode != WSSR_APPLY_CUTOFF) return WSSR_ERR_INVALID_ARG;
+  if (opt.apply_mode != WSSR_APPLY_DAMPED && opt.apply_mode != WSSR_APPLY_CUTOFF &&
+      opt.apply_mode != WSSR_APPLY_PINV)
+    return WSSR_ERR_INVALID_ARG;
   if (opt.apply_mode == WSSR_APPLY_CUTOFF && !(opt.sigma_floor > 0.0)) return WSSR_ERR_INVALID_ARG;
+  if (opt.apply_mode == WSSR_APPLY_PINV && !(opt.sigma_floor > 0.0 && opt.sigma_floor <= 1.0))
+    return WSSR_ERR_INVALID_ARG;
   if (opt.engine < WSSR_ENGINE_AUTO || opt.engine > WSSR_ENGINE_TCGEN05) return WSSR_ERR_INVALID_ARG;
   if (opt.wait_cap < 1) return WSSR_ERR_INVALID_ARG;
   if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;

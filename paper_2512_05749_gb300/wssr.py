@@ -27,6 +27,7 @@ WSSR_DTYPE_F32 = 0
 WSSR_DTYPE_BF16 = 1
 WSSR_APPLY_DAMPED = 0
 WSSR_APPLY_CUTOFF = 1
+WSSR_APPLY_PINV = 2
 WSSR_OP_DENSE = 0
 WSSR_OP_MLP = 1
 WSSR_ENGINE_AUTO = 0
@@ -354,7 +355,8 @@ class WSSR:
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
         opt.history = 1 if history else 0
         opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]
-        opt.apply_mode = {"damped": WSSR_APPLY_DAMPED, "cutoff": WSSR_APPLY_CUTOFF}[apply_mode]
+        opt.apply_mode = {"damped": WSSR_APPLY_DAMPED, "cutoff": WSSR_APPLY_CUTOFF,
+                          "pinv": WSSR_APPLY_PINV}[apply_mode]
         opt.sigma_floor = sigma_floor
         opt.engine = {"auto": WSSR_ENGINE_AUTO, "simt": WSSR_ENGINE_SIMT,
                       "tcgen05": WSSR_ENGINE_TCGEN05}[engine]

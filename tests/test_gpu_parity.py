@@ -180,7 +180,7 @@ def run_step(W, w, dtype, engine="auto", m=2, mode="damped", floor=0.0, ld_pad=0
     s.check("step")
     out = delta.double().cpu().numpy(), sigma.cpu().numpy(), V.double().cpu().numpy()
     ref = orc.wssr_step(Oex, g.astype(np.float64), Vprev.astype(np.float64), w.lam, m, mode,
-                        floor if mode == "cutoff" else None)
+                        floor if mode in ("cutoff", "pinv") else None)
     s.close()
     return out, ref, Vprev
 
@@ -223,6 +223,15 @@ def test_step_f32_offset_columns_and_low_rank_part(W):
     assert err < 1e-4
     assert np.max(np.abs(sg.cpu().numpy() - sr) / sr) < 1e-4
     s.close()
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-6])
+def test_step_pinv_mode(W, eps):
+    """Truncated pseudo-inverse apply (Eq. (svd0), Eq. (sigmaplus)): eps = 1e-2
+    drops the small Ritz values, eps = 1e-6 keeps them all."""
+    w = wl.small_planted(800, 1500, 16, K=800, sigma_power=1.0, noise=1e-4, lam=1e-3)
+    out, ref, _ = run_step(W, w, "f32", mode="pinv", floor=eps)
+    compare_step(out, ref, 1e-5, 1e-4, 1e-3)
 
 
 def test_step_cutoff_mode(W):

@@ -107,3 +107,32 @@ def test_adjoints_are_bias_derivatives():
         fd = _fd_jacobian(theta, widths, x, h=1e-4, idx=idx)
         assert np.abs(fd - dl[l]).max() <= 1e-7 * max(1.0, np.abs(dl[l]).max())
         off += widths[l + 1]
+
+
+def test_energy_gradient_of_the_network_against_autograd():
+    """For the network ansatz, g = (2/N) O_c^T (E - mean E) equals the gradient of
+    the surrogate (2/N) sum_n f_theta(x_n) (E_n - mean E) with E held fixed,
+    computed by torch's reverse-mode autograd in float64 (external check)."""
+    torch = pytest.importorskip("torch")
+    from oracle import wssr_oracle as orc
+    widths = (25, 9, 7, 1)
+    theta = wl.mlp_theta_np(widths, "eg") + 0.1 * wl.gaussian_np((mo.param_count(widths),), "egb")
+    x = wl.electrons_np(11, 5, 1.5, "eg")
+    E = wl.gaussian_np((11,), "egE")
+    J = mo.per_sample_jacobian(theta, widths, x)
+    g = orc.local_energy_gradient(J, E)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    h = torch.tensor(mo.features(x), dtype=torch.float64)
+    off = 0
+    for l in range(len(widths) - 1):
+        fi, fo = widths[l], widths[l + 1]
+        Wl = th[off:off + fo * fi].reshape(fo, fi)
+        off += fo * fi
+        bl = th[off:off + fo]
+        off += fo
+        h = h @ Wl.T + bl
+        if l < len(widths) - 2:
+            h = torch.tanh(h)
+    Et = torch.tensor(E - E.mean(), dtype=torch.float64)
+    (2.0 * (h[:, 0] * Et).sum() / len(E)).backward()
+    assert np.abs(th.grad.numpy() - g).max() <= 1e-12 * np.abs(g).max()

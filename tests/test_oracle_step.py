@@ -252,3 +252,34 @@ def test_averaged_step_truncated_matches_numpy_svd():
     U, S, _ = np.linalg.svd(Oh, full_matrices=False)
     assert np.abs(s - S[:w.r]).max() <= 1e-10 * S[0]
     assert orc.projector_distance(V, U[:, :w.r]) <= 1e-8
+
+
+def test_pinv_apply_matches_truncated_pseudo_inverse():
+    """The pseudo-inverse mode (Eq. (svd0), Eq. (sigmaplus)) at full rank equals
+    numpy's Hermitian pinv of S with the same relative cutoff on its
+    eigenvalues, for a cutoff that drops some and one that keeps all."""
+    N, M = 30, 12
+    O = wl.gaussian_np((N, M), "pinv") * np.logspace(0, -3, M)[None, :]
+    Oc = orc.centre(O)
+    S = Oc.T @ Oc / N
+    g = wl.gaussian_np((M,), "pinvg")
+    ev, U = np.linalg.eigh(S)
+    order = np.argsort(ev)[::-1]
+    V, sigma = U[:, order], np.sqrt(np.maximum(ev[order], 0))
+    for eps in (1e-3, 1e-12):
+        d = orc.woodbury_apply(V, sigma, g, 1e-3, "pinv", eps)
+        ref = np.linalg.pinv(S, rcond=eps, hermitian=True) @ g
+        assert np.linalg.norm(d - ref) <= 1e-10 * np.linalg.norm(ref), eps
+    # the cutoff really removes directions: the result differs from the full inverse
+    assert np.linalg.norm(orc.woodbury_apply(V, sigma, g, 1e-3, "pinv", 1e-3) - np.linalg.solve(S, g)) > 1e-3
+
+
+def test_local_energy_gradient_is_twice_the_sample_covariance():
+    """Eq. (gradient:vmc): g = 2 Cov(O, E_L) with divisor N; numpy's cov is the
+    external check."""
+    N, M = 50, 7
+    O = wl.gaussian_np((N, M), "leg") + 3.0
+    E = wl.gaussian_np((N,), "legE") - 1.5
+    g = orc.local_energy_gradient(O, E)
+    C = np.cov(np.c_[O, E].T, bias=True)
+    assert np.abs(g - 2.0 * C[:-1, -1]).max() <= 1e-13 * np.abs(g).max()
