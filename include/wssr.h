@@ -140,6 +140,18 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g,
                       const float* V_prev, float* delta, double* sigma, float* V_out,
                       wssr_stream_t stream);
 
+/* One WSSR step whose gradient is formed in the step from the per-sample
+ * local energies E_loc (N floats, device): the VMC estimate of Eq.
+ * (gradient:vmc), g = (2/N) O_c^T (E_L - mean E_L) = 2 O_N Lbar_N (Eq.
+ * (Lbarn)), written to g_out (M floats, device) and applied as in wssr_step.
+ * Dense O on the tensor-core engine: g is accumulated by the first O^T pass
+ * of the step next to the column means (no extra read of O); plain engine:
+ * one extra transposed pass; network operator: the weighted backward pass
+ * of the network. */
+wssr_status wssr_step_local_energy(wssr_handle h, const wssr_operator* op, const float* E_loc,
+                                   const float* V_prev, float* delta, double* sigma, float* V_out, float* g_out,
+                                   wssr_stream_t stream);
+
 /* One WSSR step with history averaging (Section 4.1: Eq. (Ohat), (Lhat),
  * (Obar), (Lbar), (barg), (barS); Algorithm 2's update of Obar and Lbar).
  * The truncated SVD runs on the averaged operator whose S-matrix is

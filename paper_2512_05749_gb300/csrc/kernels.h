@@ -21,6 +21,7 @@ struct MlpSource {
   int64_t Mp;           // padded parameter count (= 64 nchunks)
 };
 int64_t mlp_M(const wssr_mlp_ctx* h);
+int mlp_layers(const wssr_mlp_ctx* h);
 int64_t mlp_Mp(const wssr_mlp_ctx* h);
 int64_t mlp_Nmax(const wssr_mlp_ctx* h);
 MlpSource mlp_source(const wssr_mlp_ctx* h);
@@ -60,7 +61,8 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
                     int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
                     int compute_mu, int64_t wait_us, int* status, cudaStream_t st,
-                    const float* Zadd = nullptr);
+                    const float* Zadd = nullptr, const float* wgt = nullptr, float* g_out = nullptr,
+                    const double* wsum = nullptr);
 // FP32 partial Grams Gp[split] (r x r) of the K-blocked bf16 block XT (L rows).
 // History averaging helpers (small_ops.cu): out[j][k] = gamma sigma_prev[j] in[j][k]
 // (r x r, in with row pitch ld_in); e = weight * sigma_prev * Lbar_prev; Lbar = c / sigma.
@@ -71,6 +73,14 @@ void launch_scale_rows_r(const float* in, int64_t ld_in, const double* sigma_pre
 void launch_hist_coeffs(const double* sigma_prev, const double* Lbar_prev, double weight, int r, double* e,
                         cudaStream_t st);
 void launch_lbar(const double* c, const double* sigma, int r, double* Lbar, cudaStream_t st);
+// VMC gradient weights w = 2 (E - mean E) / N (Eq. (gradient:vmc)), and the
+// plain transposed product g = O^T w (O N x ld, float or bf16) for the SIMT engine.
+void launch_energy_weights(const float* E, int64_t N, float* w, double* wsum, cudaStream_t st);
+void launch_gemv_t(const void* O, int o_bf16, int64_t ld, int64_t N, int64_t M, const float* w,
+                   const double* wsum, float* g, cudaStream_t st);
+// Network operator: g (padded space) = sum_n w[n] d f(x_n) / d theta from the
+// activations and adjoints of the last mlp_prepare_source (mlp.cu).
+wssr_status mlp_weighted_grad_padded(wssr_mlp_ctx* h, const float* w, int64_t N, float* g_padded, cudaStream_t st);
 // Cross Gram Gp[split] (r x r, FP32) = XA^T XB over the split's parameter
 // chunks, XA and XB K-blocked bf16 operands of L rows (tc_passes.cu).
 int tc_xgram_launch(const void* XA, const void* XB, int64_t L, int r, int splits, float* Gp, int64_t wait_us,

@@ -60,6 +60,7 @@ struct wssr_mlp_ctx {
   int* pmap = nullptr;      // padded parameter -> user parameter index (or -1)
   int* umap = nullptr;      // user parameter -> padded parameter index
   int* segs = nullptr;      // packing segments of S (5 ints each)
+  float* gtmp = nullptr;    // M floats: a user-order gradient before padding
   int nseg = 0;
 };
 
@@ -351,8 +352,24 @@ wssr_status run_forward_backward(wssr_mlp_ctx* h, const float* theta, const floa
 }
 
 
+// grad (user order) = sum_n w[n] d f(x_n) / d theta from the activations and
+// adjoints in h (the backward pass of f for the output cotangent w):
+// grad W_l = (w * delta_l)^T a_{l-1}, grad b_l = column sums of w * delta_l (delta_L = 1).
+wssr_status weighted_grad(wssr_mlp_ctx* h, const float* w, int64_t N, float* grad, cudaStream_t st) {
+  const int* wd = h->desc.widths;
+  for (int l = 1; l <= h->L; ++l) {
+    const int dout = wd[l], dp = wd[l - 1];
+    const float* del = l < h->L ? h->dels + h->del_off[l] : nullptr;
+    k_scale_rows<<<(unsigned)ceil_div(N * dout, 256), 256, 0, st>>>(del, h->del_cols, w, N, dout, h->wtmp, dout);
+    gemm<true, false, 0>(h->wtmp, dout, h->acts + h->act_off[l - 1], h->act_cols, grad + h->off_w[l - 1], dp,
+                         dout, dp, (int)N, nullptr, nullptr, 0, st);
+    k_colsum_rows<<<(unsigned)ceil_div(dout, 256), 256, 0, st>>>(h->wtmp, dout, N, dout, grad + h->off_b[l - 1]);
+  }
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
 void mlp_free_mf(wssr_mlp_ctx* h) {
-  void* ptrs[] = {h->S, h->ST, h->chunks, h->sched, h->groups, h->pmap, h->umap, h->segs};
+  void* ptrs[] = {h->S, h->ST, h->chunks, h->sched, h->groups, h->pmap, h->umap, h->segs, h->gtmp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -500,6 +517,7 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
   if (e == cudaSuccess) e = cudaMalloc(&h->pmap, (size_t)h->Mp * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->umap, (size_t)h->M * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->segs, (size_t)(2 * WSSR_MLP_MAX_LAYERS + 1) * 5 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)h->M * sizeof(float));
   if (e == cudaSuccess) e = mlp_tables(h);
   if (e == cudaSuccess) {
     int meta[WSSR_MLP_MAX_LAYERS * 8] = {0};
@@ -592,17 +610,7 @@ wssr_status wssr_mlp_vjp(wssr_mlp_handle h, const float* theta, const float* x, 
   cudaStream_t st = (cudaStream_t)stream;
   wssr_status s = run_forward_backward(h, theta, x, N, true, st);
   if (s != WSSR_OK) return s;
-  const int* wd = h->desc.widths;
-  for (int l = 1; l <= h->L; ++l) {
-    const int dout = wd[l], dp = wd[l - 1];
-    // S = w * delta_l (delta_L = 1), grad W_l = S^T a_{l-1}, grad b_l = column sums of S
-    const float* del = l < h->L ? h->dels + h->del_off[l] : nullptr;
-    k_scale_rows<<<(unsigned)ceil_div(N * dout, 256), 256, 0, st>>>(del, h->del_cols, w, N, dout, h->wtmp, dout);
-    gemm<true, false, 0>(h->wtmp, dout, h->acts + h->act_off[l - 1], h->act_cols, grad + h->off_w[l - 1], dp,
-                         dout, dp, (int)N, nullptr, nullptr, 0, st);
-    k_colsum_rows<<<(unsigned)ceil_div(dout, 256), 256, 0, st>>>(h->wtmp, dout, N, dout, grad + h->off_b[l - 1]);
-  }
-  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+  return weighted_grad(h, w, N, grad, st);
 }
 
 }  // extern "C"
@@ -611,6 +619,7 @@ wssr_status wssr_mlp_vjp(wssr_mlp_handle h, const float* theta, const float* x, 
 namespace wssr {
 
 int64_t mlp_M(const wssr_mlp_ctx* h) { return h->M; }
+int mlp_layers(const wssr_mlp_ctx* h) { return h->L; }
 int64_t mlp_Mp(const wssr_mlp_ctx* h) { return h->Mp; }
 int64_t mlp_Nmax(const wssr_mlp_ctx* h) { return h->N_max; }
 
@@ -646,6 +655,14 @@ wssr_status mlp_prepare_source(wssr_mlp_ctx* h, const float* theta, const float*
     k_pack_scales<<<grid, dim3(32, 8), 0, st>>>(h->dels, h->del_cols, N, h->ST, h->ldst);
   }
   k_fill_bf16<<<(unsigned)ceil_div(h->ldst, 256), 256, 0, st>>>(h->ST + h->t_ones * h->ldst, h->ldst, 1.f);
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
+wssr_status mlp_weighted_grad_padded(wssr_mlp_ctx* h, const float* w, int64_t N, float* g_padded, cudaStream_t st) {
+  if (N < 1 || N > h->N_max) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = weighted_grad(h, w, N, h->gtmp, st);
+  if (s != WSSR_OK) return s;
+  k_pad_rows<<<(unsigned)ceil_div(h->Mp, 256), 256, 0, st>>>(h->gtmp, 1, h->pmap, h->Mp, g_padded);
   return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
 

@@ -621,6 +621,80 @@ void launch_lbar(const double* c, const double* sigma, int r, double* Lbar, cuda
 }
 
 // ---------------------------------------------------------------------------
+// VMC gradient (Section 2.2, Eq. (gradient:vmc); Eq. (Lbarn)):
+// g = (2/N) O_c^T (E - mean E) = O^T w with w = 2 (E - mean E) / N
+// (the weights sum to zero, so the centring term drops out).
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(1024) k_energy_weights(const float* __restrict__ E, int64_t N,
+                                                         float* __restrict__ w, double* __restrict__ wsum) {
+  __shared__ double part[32];
+  double s = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += 1024) s += (double)E[n];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = part[threadIdx.x];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[0] = t;
+  }
+  __syncthreads();
+  const double mean = part[0] / (double)N;
+  double ws = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += 1024) {
+    const float wn = (float)(2.0 * ((double)E[n] - mean) / (double)N);
+    w[n] = wn;
+    ws += (double)wn;
+  }
+  // sum of the rounded weights (zero up to rounding), for the centring correction
+  __syncthreads();
+  ws = warp_sum(ws);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = part[threadIdx.x];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) *wsum = t;
+  }
+}
+
+// g[m] = sum_n O[n, m] w[n]: thread = one column (coalesced rows), FP32 runs of
+// 64 rows flushed into FP64, accumulated relative to the first sample row
+// (sum_n (O[n, m] - O[0, m]) w[n] + O[0, m] sum_n w[n]) so that a large column
+// mean does not cancel in FP32.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_t(const T* __restrict__ O, int64_t ld, int64_t N, int64_t M,
+                                                const float* __restrict__ w, const double* __restrict__ wsum,
+                                                float* __restrict__ g) {
+  const int64_t m = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (m >= M) return;
+  const float o0 = to_f32(O[m]);
+  double acc = 0.0;
+  for (int64_t n0 = 0; n0 < N; n0 += 64) {
+    float a = 0.f;
+    const int64_t n1 = n0 + 64 < N ? n0 + 64 : N;
+    for (int64_t n = n0; n < n1; ++n) a = fmaf(to_f32(O[n * ld + m]) - o0, __ldg(w + n), a);
+    acc += (double)a;
+  }
+  g[m] = (float)(acc + (double)o0 * wsum[0]);
+}
+}  // namespace
+
+void launch_energy_weights(const float* E, int64_t N, float* w, double* wsum, cudaStream_t st) {
+  k_energy_weights<<<1, 1024, 0, st>>>(E, N, w, wsum);
+}
+
+void launch_gemv_t(const void* O, int o_bf16, int64_t ld, int64_t N, int64_t M, const float* w,
+                   const double* wsum, float* g, cudaStream_t st) {
+  const unsigned grid = (unsigned)ceil_div(M, 256);
+  if (o_bf16)
+    k_gemv_t<bf16><<<grid, 256, 0, st>>>(reinterpret_cast<const bf16*>(O), ld, N, M, w, wsum, g);
+  else
+    k_gemv_t<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(O), ld, N, M, w, wsum, g);
+}
+
+// ---------------------------------------------------------------------------
 // Cast an L x r float block to bf16 (row-major and/or transposed r x ldT)
 // ---------------------------------------------------------------------------
 namespace {

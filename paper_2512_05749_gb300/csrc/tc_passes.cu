@@ -221,8 +221,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
                int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
                const double* __restrict__ ysum, float* __restrict__ Z, bf16* __restrict__ ZT,
-               int64_t ldz, float* __restrict__ mu_io, const float* __restrict__ Zadd, uint64_t limit_ns,
-               int* status) {
+               int64_t ldz, float* __restrict__ mu_io, const float* __restrict__ Zadd,
+               const float* __restrict__ wgt, float* __restrict__ g_out, const double* __restrict__ wsum,
+               uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t a_bytes = A_BYTES * MT;
@@ -285,10 +286,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr int RPS = 64 / NSG;        // rows per sample group and stage
       const int pg = et % PG, sg = et / PG;
       const int box = pg >> 3, c = pg & 7;
-      float acc[8];
-      double acc64[8];
+      // with wgt: also the weighted sums sum_n O[n, p] wgt[n] (the fused gradient)
+      float acc[8], accw[8];
+      double acc64[8], accw64[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) acc[e] = 0.f, acc64[e] = 0.0;
+      for (int e = 0; e < 8; ++e) acc[e] = 0.f, acc64[e] = 0.0, accw[e] = 0.f, accw64[e] = 0.0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % stages, u = i / stages;
         const bool got = mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort);
@@ -299,10 +301,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = sg * RPS + j;
             const uint4 v = *reinterpret_cast<const uint4*>(sa + row * 128 + ((c ^ (row & 7)) << 4));
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            const int64_t n = (int64_t)i * BK + row;
+            const float wn = (wgt && n < N) ? __ldg(wgt + n) : 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              acc[2 * e] += __uint_as_float(w[e] << 16);
-              acc[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
+              const float lo = __uint_as_float(w[e] << 16), hi = __uint_as_float(w[e] & 0xFFFF0000u);
+              acc[2 * e] += lo;
+              acc[2 * e + 1] += hi;
+              accw[2 * e] = fmaf(lo, wn, accw[2 * e]);
+              accw[2 * e + 1] = fmaf(hi, wn, accw[2 * e + 1]);
             }
           }
         }
@@ -314,7 +321,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (et == 0) mbar_arrive(&ctl->empty[s]);
         if ((i & 15) == 15) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) acc64[e] += (double)acc[e], acc[e] = 0.f;
+          for (int e = 0; e < 8; ++e)
+            acc64[e] += (double)acc[e], acc[e] = 0.f, accw64[e] += (double)accw[e], accw[e] = 0.f;
         }
       }
       double* red = &ctl->red[0][0];  // [NSG][PG * 8]
@@ -327,6 +335,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         const float mu = (float)(sum / (double)N);
         ctl->mu[p] = mu;
         if (m0 + p < M) mu_io[m0 + p] = mu;
+      }
+      if (g_out) {
+        // (O_c^T w)[p] = sum_n O[n, p] w[n] - mu_p sum_n w[n]; the weights sum to zero
+        // up to their rounding, which the second term removes
+        epi_bar();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) red[sg * (PG * 8) + pg * 8 + e] = accw64[e] + (double)accw[e];
+        epi_bar();
+        for (int p = et; p < PG * 8; p += 128) {
+          double sum = 0.0;
+          for (int gq = 0; gq < NSG; ++gq) sum += red[gq * (PG * 8) + p];
+          if (m0 + p < M) g_out[m0 + p] = (float)(sum - (double)ctl->mu[p] * wsum[0]);
+        }
       }
     }
     epi_bar();
@@ -703,7 +724,9 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 
 int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void* YhatT, int64_t ldy,
                     int r, const double* ysum, float* Z, void* ZT, int64_t ldz, float* mu_io,
-                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st, const float* Zadd) {
+                    int compute_mu, int64_t wait_us, int* status, cudaStream_t st, const float* Zadd,
+                    const float* wgt, float* g_out, const double* wsum) {
+  if (!compute_mu) wgt = nullptr, g_out = nullptr;  // the weighted sums ride on the column-mean pass
   constexpr int MT = 2;
   const int nmma = nmma_for(r);
   const size_t stage = (size_t)A_BYTES * MT + (size_t)nmma * BK * 2;
@@ -722,11 +745,11 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   dim3 grid((unsigned)ceil_div(M, (int64_t)BM * MT));
   if (compute_mu)
     k_tc_passB<true, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                      (bf16*)ZT, ldz, mu_io, Zadd,
+                                                      (bf16*)ZT, ldz, mu_io, Zadd, wgt, g_out, wsum,
                                                       (uint64_t)wait_us * 1000ull, status);
   else
     k_tc_passB<false, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                       (bf16*)ZT, ldz, mu_io, Zadd,
+                                                       (bf16*)ZT, ldz, mu_io, Zadd, nullptr, nullptr, nullptr,
                                                        (uint64_t)wait_us * 1000ull, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }

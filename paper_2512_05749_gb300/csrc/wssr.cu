@@ -76,6 +76,10 @@ struct wssr_ctx {
   double* cpart = nullptr;        // per-tile partials of V^T g fused into the rotation
   bool c_ready = false;           // h->c already holds V_out^T g
   void* Vhp = nullptr;            // history averaging: bf16 K-blocked copy of V_prev
+  float* wE = nullptr;            // VMC gradient weights 2 (E - mean E) / N (N floats)
+  double* wE_sum = nullptr;       // their sum (zero up to rounding)
+  const float* fuse_w = nullptr;  // set for one step: the first pass B also forms g = O^T fuse_w
+  float* fuse_g = nullptr;
   float* gbar = nullptr;          // history averaging: the averaged gradient (M)
   int gram_splits_tc = 1;
 
@@ -104,7 +108,7 @@ void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar};
+                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar, h->wE, h->wE_sum};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -209,7 +213,9 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
     } else if (h->use_tc) {
       void* ZT = Zf ? nullptr : h->Xhat;
       int rc = tc_passB_launch(op->O, op->ld, N, M, Yop, h->ldy, r, h->ysum, Zf, ZT, h->ldx, h->mu,
-                               h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st, Zadd);
+                               h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st, Zadd, h->fuse_w, h->fuse_g,
+                               h->wE_sum);
+      h->fuse_w = nullptr, h->fuse_g = nullptr;  // formed with this step's column means
       if (rc != 0) return WSSR_ERR_UNSUPPORTED;
       h->mu_valid = true;
     } else if (is_bf16(h)) {
@@ -509,6 +515,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(Y2, (size_t)(N + r) * r * f);
   ALLOC(csum_part, (size_t)blocks64 * r * d);
   ALLOC(mean_r, (size_t)r * d);
+  ALLOC(wE, (size_t)N * f);
+  ALLOC(wE_sum, d);
   ALLOC(ysum, (size_t)r * d);
   ALLOC(Z, (size_t)M * r * f);
   ALLOC(V, (size_t)M * r * f);
@@ -606,6 +614,41 @@ wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const flo
       cudaMemcpyAsync(gbar_out, h->gbar, (size_t)h->M * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return WSSR_ERR_CUDA;
   return check_launch(h);
+}
+
+wssr_status wssr_step_local_energy(wssr_handle h, const wssr_operator* op, const float* E_loc,
+                                   const float* V_prev, float* delta, double* sigma, float* V_out, float* g_out,
+                                   wssr_stream_t stream) {
+  if (!h || !E_loc || !V_prev || !delta || !sigma || !V_out || !g_out) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  h->mu_valid = false;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
+  {
+    Timed tm(h, WSSR_KCAT_APPLY, st);
+    launch_energy_weights(E_loc, h->N, h->wE, h->wE_sum, st);
+    h->launches++;
+    if (op->kind == WSSR_OP_MLP) {
+      // the weighted backward pass of the network from the activations and adjoints just recomputed
+      if ((s = mlp_weighted_grad_padded(op->mlp, h->wE, h->N, g_out, st)) != WSSR_OK) return s;
+      h->launches += 3 * mlp_layers(op->mlp) + 1;  // per layer: scale, GEMM, column sums; then the padding
+    } else if (!h->use_tc) {
+      launch_gemv_t(op->O, is_bf16(h) ? 1 : 0, op->ld, h->N, h->M, h->wE, h->wE_sum, g_out, st);
+      h->launches++;
+    }
+  }
+  if (op->kind == WSSR_OP_DENSE && h->use_tc) {
+    // formed by the epilogue warps of the first pass B, next to the column means
+    h->fuse_w = h->wE;
+    h->fuse_g = g_out;
+  }
+  s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g_out, st);
+  h->fuse_w = nullptr, h->fuse_g = nullptr;
+  if (s != WSSR_OK) return s;
+  return woodbury(h, V_out, sigma, g_out, delta, st);
 }
 
 wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const float* V_rand,

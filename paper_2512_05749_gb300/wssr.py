@@ -42,6 +42,7 @@ EXPORTED = [
     "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
+    "wssr_step_local_energy",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_step": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp]),
         "wssr_init_subspace": (i32, [vp, P(wssr_operator), vp, vp, vp, vp]),
         "wssr_step_averaged": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, vp]),
+        "wssr_step_local_energy": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp, vp]),
         "wssr_apply_O": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_apply_Ot": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_orthonormalize": (i32, [vp, vp, i64, i32, vp]),
@@ -221,6 +223,11 @@ def wssr_step_averaged(h: int, op: wssr_operator, g, V_prev, sigma_prev, Lbar_pr
     _check(load().wssr_step_averaged(h, ctypes.byref(op), _ptr(g), _ptr(V_prev), _ptr(sigma_prev), _ptr(Lbar_prev),
                                      float(weight), _ptr(delta), _ptr(sigma), _ptr(V_out), _ptr(Lbar_out),
                                      _ptr(gbar_out), _stream(stream)), "wssr_step_averaged")
+
+
+def wssr_step_local_energy(h: int, op: wssr_operator, E_loc, V_prev, delta, sigma, V_out, g_out, stream=None):
+    _check(load().wssr_step_local_energy(h, ctypes.byref(op), _ptr(E_loc), _ptr(V_prev), _ptr(delta), _ptr(sigma),
+                                         _ptr(V_out), _ptr(g_out), _stream(stream)), "wssr_step_local_energy")
 
 
 def wssr_init_subspace(h: int, op: wssr_operator, V_rand, V_out, sigma=None, stream=None):
@@ -396,6 +403,21 @@ class WSSR:
             delta, sigma, V = out
         wssr_step(self.handle, self._op(O), g, V_prev, delta, sigma, V, stream)
         return delta, sigma, V
+
+    def step_local_energy(self, O, E_loc, V_prev, out=None, stream=None):
+        """Step with the VMC gradient formed from the local energies (Eq. (gradient:vmc)):
+        returns (delta, sigma, V, g)."""
+        import torch
+        dev = E_loc.device
+        if out is None:
+            delta = torch.empty(self.M, device=dev, dtype=torch.float32)
+            sigma = torch.empty(self.r, device=dev, dtype=torch.float64)
+            V = torch.empty(self.M, self.r, device=dev, dtype=torch.float32)
+            g = torch.empty(self.M, device=dev, dtype=torch.float32)
+        else:
+            delta, sigma, V, g = out
+        wssr_step_local_energy(self.handle, self._op(O), E_loc, V_prev, delta, sigma, V, g, stream)
+        return delta, sigma, V, g
 
     def step_averaged(self, O, g, V_prev, sigma_prev, Lbar_prev, weight: float, out=None, stream=None):
         """History-averaged step (Section 4.1): returns (delta, sigma, V, Lbar, gbar)."""
