@@ -42,6 +42,7 @@ __all__ = [
     "subspace_iteration", "rayleigh_ritz", "fix_signs", "woodbury_apply",
     "wssr_step", "init_subspace", "projector_distance", "S_matvec",
     "history_operator", "averaged_gradient", "wssr_step_averaged", "local_energy_gradient",
+    "randomized_svd",
 ]
 
 
@@ -295,6 +296,23 @@ def wssr_step_averaged(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, sigma_p
     Lbar = (V.T @ gbar) / sigma
     delta = woodbury_apply(V, sigma, gbar, lam, mode, sigma_floor)
     return delta, sigma, V, Lbar, gbar
+
+
+def randomized_svd(O: np.ndarray, Omega: np.ndarray, q: int = 0):
+    """Randomized sketching SVD (Appendix A, Eq. (randsvd), after Halko et al.):
+    Y = O^ Omega for a Gaussian block Omega with one row per column of O^ (the
+    samples; O^ = O_c^T / sqrt(N), Eq. (Osrn)), Q = orth(Y), q optional power
+    iterations Q = orth(O^ O^^T Q), then the SVD of B = Q^T O^ (here as
+    Rayleigh-Ritz on span(Q)). Returns (sigma, V) for all k = Omega.shape[1]
+    columns, sigma descending; the caller keeps the leading r of the r + p."""
+    Oc = centre(O)
+    N = Oc.shape[0]
+    Y = Oc.T @ np.asarray(Omega, dtype=np.float64) / np.sqrt(N)
+    Q = orth(Y)
+    for _ in range(q):
+        Q = orth(S_matvec(Oc, Q))
+    V, sigma = rayleigh_ritz(Oc, Q)
+    return sigma, fix_signs(V)
 
 
 def init_subspace(O: np.ndarray, V_rand: np.ndarray, m_init: int = 20) -> np.ndarray:

@@ -283,3 +283,33 @@ def test_local_energy_gradient_is_twice_the_sample_covariance():
     g = orc.local_energy_gradient(O, E)
     C = np.cov(np.c_[O, E].T, bias=True)
     assert np.abs(g - 2.0 * C[:-1, -1]).max() <= 1e-13 * np.abs(g).max()
+
+
+# ---------------------------------------------------------------------------
+# Randomized sketching SVD (Appendix A, Eq. (randsvd))
+# ---------------------------------------------------------------------------
+
+def test_randomized_svd_is_exact_on_low_rank():
+    """An exactly rank-K centred O (planted, no noise, U orthogonal to 1) is
+    recovered exactly from one sketch of width k >= K: sigma_1..K are the
+    planted values, the rest vanish, and span(V[:, :K]) is the planted span."""
+    N, M, K, k = 80, 120, 6, 10
+    U = orc.orth(wl.gaussian_np((N, K), "rsU") - wl.gaussian_np((N, K), "rsU").mean(axis=0))
+    Wp = orc.orth(wl.gaussian_np((M, K), "rsW"))
+    sv = np.array([5.0, 3.0, 2.0, 1.0, 0.5, 0.25])
+    O = np.sqrt(N) * (U * sv) @ Wp.T
+    Omega = wl.gaussian_np((N, k), "rsO")
+    sigma, V = orc.randomized_svd(O, Omega)
+    assert np.abs(sigma[:K] - sv).max() <= 1e-12 * sv[0]
+    assert np.abs(sigma[K:]).max() <= 1e-12 * sv[0]
+    assert orc.projector_distance(V[:, :K], Wp) <= 1e-11
+
+
+def test_randomized_svd_power_iterations_converge_to_numpy_svd():
+    w = wl.small_planted(60, 90, 8, K=60, sigma_power=1.0, noise=1e-3)
+    O = wl.planted_O_np(w)
+    Omega = wl.gaussian_np((w.N, 12), "rsq")
+    sigma, V = orc.randomized_svd(O, Omega, q=60)
+    _, S, Vt = np.linalg.svd(orc.centre(O) / np.sqrt(w.N), full_matrices=False)
+    assert np.abs(sigma[:8] - S[:8]).max() <= 1e-9 * S[0]
+    assert orc.projector_distance(V[:, :8], Vt[:8].T) <= 1e-6
