@@ -140,6 +140,16 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g,
                       const float* V_prev, float* delta, double* sigma, float* V_out,
                       wssr_stream_t stream);
 
+/* Randomized sketching SVD (Appendix A, Eq. (randsvd); the paper's RSSR and
+ * a cold start in place of wssr_init_subspace): the sketch Y = O_c^T Omega
+ * of a caller-supplied block Omega over the samples (N x r floats, device,
+ * e.g. Gaussian; r = the context's width = target rank + oversampling p),
+ * Q = orth(Y), q >= 0 power iterations (subspace iterations), then the
+ * Rayleigh-Ritz finish. Writes all r columns of V_out (M x r) and sigma (r,
+ * descending); callers keep the leading target-rank ones. */
+wssr_status wssr_randomized_svd(wssr_handle h, const wssr_operator* op, const float* Omega, int32_t q,
+                                float* V_out, double* sigma, wssr_stream_t stream);
+
 /* One WSSR step whose gradient is formed in the step from the per-sample
  * local energies E_loc (N floats, device): the VMC estimate of Eq.
  * (gradient:vmc), g = (2/N) O_c^T (E_L - mean E_L) = 2 O_N Lbar_N (Eq.

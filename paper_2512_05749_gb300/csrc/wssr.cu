@@ -324,37 +324,35 @@ void right_multiply_Y(wssr_ctx* h, float* Y, const float* T, int64_t L, cudaStre
   h->launches++;
 }
 
-// Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma
-// written. With hist, the operator is the history-averaged one (r extra rows).
-wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, int m, float* V_out,
-                   double* sigma, const float* g, cudaStream_t st, const Hist* hist = nullptr) {
+// m rounds of subspace iteration on the operand basis Xop (with its factor
+// TX when have_T): Y = O_c Xh (TX), Cholesky QR, Xh = O_c^T Qh_Y, TX = R^-1.
+// With hist, the operator is the history-averaged one (r extra rows).
+wssr_status iterate(wssr_ctx* h, const wssr_operator* op, const void** Xop, bool have_T, int m,
+                    const Hist* hist, cudaStream_t st) {
+  const int64_t L = rows_of(h, hist);
+  wssr_status s;
+  for (int it = 0; it < m; ++it) {
+    if ((s = pass_A(h, op, *Xop, h->Y, st)) != WSSR_OK) return s;
+    if (hist) history_rows(h, hist, *Xop, h->Y, st);
+    if (have_T) right_multiply_Y(h, h->Y, h->TX, L, st);
+    const void* Yop = orth_Y_and_operand(h, h->Y, L, st);
+    if (hist) history_pass_B_term(h, hist, h->Y2, st);
+    if ((s = pass_B(h, op, Yop, nullptr, Xop, st, hist ? h->Z : nullptr)) != WSSR_OK) return s;
+    factor_operand(h, *Xop, h->TX, st);
+    have_T = true;
+  }
+  return WSSR_OK;
+}
+
+// Rayleigh-Ritz on span(Xh) = span(Xh TX): Y = (O_c Xh) TX, H = Y^T Y scaled,
+// H = W L W^T (Jacobi), V_out = Xh (TX W), sigma from FP64 Rayleigh quotients.
+wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, float* V_out, double* sigma,
+                      const Hist* hist, cudaStream_t st) {
   const int64_t N = h->N, M = h->M;
   const int r = h->r;
   const int64_t L = rows_of(h, hist);
   const double gscale = hist ? hist->hscale : 1.0 / (double)N;
   wssr_status s;
-  h->mu_valid = false;
-  const void* Xop;
-  if (hist) {
-    // V_prev's operand copy is kept for the history rows; pass B writes the next basis into Xhat
-    launch_cast(V_start, M, r, nullptr, 1, h->Vhp, 0, nullptr, st);
-    h->launches++;
-    Xop = h->Vhp;
-  } else {
-    Xop = cast_X_operand(h, V_start, st);
-  }
-  bool have_T = false;
-  for (int it = 0; it < m; ++it) {
-    if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
-    if (hist) history_rows(h, hist, Xop, h->Y, st);
-    if (have_T) right_multiply_Y(h, h->Y, h->TX, L, st);
-    const void* Yop = orth_Y_and_operand(h, h->Y, L, st);
-    if (hist) history_pass_B_term(h, hist, h->Y2, st);
-    if ((s = pass_B(h, op, Yop, nullptr, &Xop, st, hist ? h->Z : nullptr)) != WSSR_OK) return s;
-    factor_operand(h, Xop, h->TX, st);
-    have_T = true;
-  }
-  // Rayleigh-Ritz on span(Xh) = span(Xh TX)
   if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
   if (hist) history_rows(h, hist, Xop, h->Y, st);
   right_multiply_Y(h, h->Y, h->TX, L, st);
@@ -368,7 +366,6 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
     // V_out = Xh (T W) on the tensor cores (c = V_out^T g is a separate,
     // bandwidth-bound pass: fusing its column sums into this epilogue costs
     // more warp shuffles than re-reading V_out)
-    (void)g;
     launch_split3_T(h->TW, r, h->TWT3, st);
     if (tc_rotate_launch(Xop, M, r, h->TWT3, V_out, nullptr, nullptr, h->opt.wait_cap, h->status, st) != 0)
       return WSSR_ERR_UNSUPPORTED;
@@ -386,6 +383,25 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
   launch_finalize_sigma(h->Hp, r, sig, st);
   h->launches++;
   return check_launch(h);
+}
+
+// Subspace iteration from V_start (m rounds) + Rayleigh-Ritz; V_out, sigma written.
+wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, int m, float* V_out,
+                   double* sigma, const float* g, cudaStream_t st, const Hist* hist = nullptr) {
+  (void)g;
+  h->mu_valid = false;
+  const void* Xop;
+  if (hist) {
+    // V_prev's operand copy is kept for the history rows; pass B writes the next basis into Xhat
+    launch_cast(V_start, h->M, h->r, nullptr, 1, h->Vhp, 0, nullptr, st);
+    h->launches++;
+    Xop = h->Vhp;
+  } else {
+    Xop = cast_X_operand(h, V_start, st);
+  }
+  wssr_status s = iterate(h, op, &Xop, false, m, hist, st);
+  if (s != WSSR_OK) return s;
+  return rr_finish(h, op, Xop, V_out, sigma, hist, st);
 }
 
 wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const float* g, float* delta,
@@ -664,6 +680,42 @@ wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const flo
   cholqr_pass(h, V_rand, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
   cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
   return ssi_rr(h, op, h->V, h->opt.m_init, V_out, sigma, nullptr, st);
+}
+
+wssr_status wssr_randomized_svd(wssr_handle h, const wssr_operator* op, const float* Omega, int32_t q,
+                                float* V_out, double* sigma, wssr_stream_t stream) {
+  if (!h || !Omega || !V_out || !sigma || q < 0) return WSSR_ERR_INVALID_ARG;
+  wssr_status s = check_op(h, op);
+  if (s != WSSR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->launches = 0;
+  h->mu_valid = false;
+  if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
+  const int64_t N = h->N;
+  const int r = h->r;
+  // the sketch Y = O_c^T Omega is a reverse pass with Omega as the sample-side operand
+  const void* Yop = Omega;
+  {
+    Timed tm(h, WSSR_KCAT_ORTH, st);
+    void* lp_row = (!h->use_tc && is_bf16(h)) ? h->Yhat : nullptr;
+    void* lpT = h->use_tc ? h->Yhat : nullptr;
+    launch_cast(Omega, N, r, lp_row, is_bf16(h) ? 1 : 0, lpT, h->ldy, h->csum_part, st);
+    launch_colsum_finalize(h->csum_part, ceil_div(N, 64), r, h->ysum, st);
+    h->launches += 2;
+    if (is_bf16(h)) Yop = h->Yhat;
+  }
+  // a cold sketch mixes the singular directions at random: orthonormalise it
+  // explicitly (Cholesky QR twice on the FP32 block) before iterating
+  if ((s = pass_B(h, op, Yop, h->Z, nullptr, st)) != WSSR_OK) return s;
+  cholqr_pass(h, h->Z, h->M, h->V2, nullptr, nullptr, 0, nullptr, nullptr, st);
+  cholqr_pass(h, h->V2, h->M, h->V, nullptr, nullptr, 0, nullptr, nullptr, st);
+  // the operand copy of V (bf16 rounds it) is refactored so that Rayleigh-Ritz
+  // sees an orthonormal basis of exactly the span the passes apply
+  const void* Xop = cast_X_operand(h, h->V, st);
+  factor_operand(h, Xop, h->TX, st);
+  if ((s = iterate(h, op, &Xop, true, q, nullptr, st)) != WSSR_OK) return s;
+  return rr_finish(h, op, Xop, V_out, sigma, nullptr, st);
 }
 
 wssr_status wssr_apply_O(wssr_handle h, const wssr_operator* op, const float* X, float* Y,

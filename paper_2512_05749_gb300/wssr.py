@@ -42,7 +42,7 @@ EXPORTED = [
     "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
-    "wssr_step_local_energy",
+    "wssr_step_local_energy", "wssr_randomized_svd",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_init_subspace": (i32, [vp, P(wssr_operator), vp, vp, vp, vp]),
         "wssr_step_averaged": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, vp]),
         "wssr_step_local_energy": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp, vp]),
+        "wssr_randomized_svd": (i32, [vp, P(wssr_operator), vp, i32, vp, vp, vp]),
         "wssr_apply_O": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_apply_Ot": (i32, [vp, P(wssr_operator), vp, vp, vp]),
         "wssr_orthonormalize": (i32, [vp, vp, i64, i32, vp]),
@@ -228,6 +229,11 @@ def wssr_step_averaged(h: int, op: wssr_operator, g, V_prev, sigma_prev, Lbar_pr
 def wssr_step_local_energy(h: int, op: wssr_operator, E_loc, V_prev, delta, sigma, V_out, g_out, stream=None):
     _check(load().wssr_step_local_energy(h, ctypes.byref(op), _ptr(E_loc), _ptr(V_prev), _ptr(delta), _ptr(sigma),
                                          _ptr(V_out), _ptr(g_out), _stream(stream)), "wssr_step_local_energy")
+
+
+def wssr_randomized_svd(h: int, op: wssr_operator, Omega, q: int, V_out, sigma, stream=None):
+    _check(load().wssr_randomized_svd(h, ctypes.byref(op), _ptr(Omega), int(q), _ptr(V_out), _ptr(sigma),
+                                      _stream(stream)), "wssr_randomized_svd")
 
 
 def wssr_init_subspace(h: int, op: wssr_operator, V_rand, V_out, sigma=None, stream=None):
@@ -434,6 +440,14 @@ class WSSR:
         wssr_step_averaged(self.handle, self._op(O), g, V_prev, sigma_prev, Lbar_prev, weight, delta, sigma, V,
                            Lbar, gbar, stream)
         return delta, sigma, V, Lbar, gbar
+
+    def randomized_svd(self, O, Omega, q: int = 0, stream=None):
+        """Randomized sketching SVD from a sample-side block Omega (N x r): returns (V, sigma)."""
+        import torch
+        V = torch.empty(self.M, self.r, device=Omega.device, dtype=torch.float32)
+        sigma = torch.empty(self.r, device=Omega.device, dtype=torch.float64)
+        wssr_randomized_svd(self.handle, self._op(O), Omega.contiguous(), q, V, sigma, stream)
+        return V, sigma
 
     def init_subspace(self, O, V_rand, stream=None):
         import torch
