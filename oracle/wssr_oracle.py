@@ -25,7 +25,11 @@ function following the passage it cites:
   gradient on gbar = O^ L^ = w Obar_prev Lbar_prev + (1 - w) g;
 * the low-rank-plus-damping apply of Eq. (updated_sr_1) (Section 4.1):
   damped reading delta = [V diag(1/(sigma^2+lam)) V^T + lam^-1 (I - V V^T)] g,
-  and the paper's own cutoff reading (S^dagger + sigma_floor^-1 S^perp) g.
+  and the paper's own cutoff reading (S^dagger + sigma_floor^-1 S^perp) g;
+* adaptive rank selection (Section 4.3, Eq. (ruler) and Algorithm 3): the
+  rank r of the apply is the size of the ratio set I_reg within the r_max
+  computed singular values, and r_max grows by (1 + eps) after a step whose
+  r_max-th singular value still passes the ratio test.
 
 Pins (tests/test_oracle_*.py): planted spectra with known singular values,
 orthonormality, warm start from the exact subspace being a fixed point, the
@@ -42,7 +46,7 @@ __all__ = [
     "subspace_iteration", "rayleigh_ritz", "fix_signs", "woodbury_apply",
     "wssr_step", "init_subspace", "projector_distance", "S_matvec",
     "history_operator", "averaged_gradient", "wssr_step_averaged", "local_energy_gradient",
-    "randomized_svd",
+    "randomized_svd", "rank_select", "rank_expand", "extend_basis", "wssr_step_adaptive",
 ]
 
 
@@ -188,7 +192,7 @@ def fix_signs(V: np.ndarray) -> np.ndarray:
 
 
 def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
-                   mode: str = "damped", sigma_floor: float | None = None) -> np.ndarray:
+                   mode: str = "damped", sigma_floor: float | None = None, r_sel: int | None = None) -> np.ndarray:
     """The low-rank-plus-regulariser apply of Eq. (updated_sr_1) (Section 4.1).
 
     ``damped``: delta = g/lam + V (d * (V^T g)), d_i = -sigma_i^2 / (lam (sigma_i^2 + lam)),
@@ -202,9 +206,14 @@ def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
     ``pinv``: the truncated pseudo-inverse S^dagger g of Eq. (svd0) with the
     cutoff of Eq. (sigmaplus) on the S-eigenvalues sigma_i^2: 1/sigma_i^2 when
     sigma_i^2 >= eps_tol max_j sigma_j^2, else 0 (eps_tol passed as sigma_floor).
+
+    ``r_sel``: keep only the leading r_sel singular triplets (the rank of
+    Eq. (ruler)); the rest of span(V) joins the complement S^perp.
     """
     V = np.asarray(V, dtype=np.float64)
     sigma = np.asarray(sigma, dtype=np.float64)
+    if r_sel is not None:
+        V, sigma = V[:, :r_sel], sigma[:r_sel]
     g = np.asarray(g, dtype=np.float64)
     c = V.T @ g
     s2 = sigma * sigma
@@ -217,6 +226,8 @@ def woodbury_apply(V: np.ndarray, sigma: np.ndarray, g: np.ndarray, lam: float,
         d = 1.0 / s2 - 1.0 / sigma_floor
         return g / sigma_floor + V @ (d * c)
     if mode == "pinv":
+        if s2.size == 0:
+            return np.zeros_like(g)
         keep = (s2 > 0) & (s2 >= sigma_floor * s2.max())
         d = np.where(keep, 1.0 / np.where(keep, s2, 1.0), 0.0)
         return V @ (d * c)
@@ -237,6 +248,57 @@ def wssr_step(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: i
     V = fix_signs(V)
     delta = woodbury_apply(V, sigma, g, lam, mode, sigma_floor)
     return delta, sigma, V
+
+
+def rank_select(sigma: np.ndarray, r_reg: float) -> int:
+    """Eq. (ruler): r = max{i in I_reg : i <= r_max}, I_reg = {i : r_reg <= s_i / s_max},
+    over the r_max = len(sigma) computed values. The s_i are singular values of
+    S, i.e. the S-eigenvalues sigma_i^2 of the Ritz values sigma here (s_max =
+    sigma_1^2). Returns 0 when no value passes (sigma all zero)."""
+    s = np.asarray(sigma, dtype=np.float64) ** 2
+    if s.size == 0 or not s[0] > 0:
+        return 0
+    r = 0
+    for i in range(1, s.size + 1):  # 1-based as in Eq. (ruler)
+        if r_reg <= s[i - 1] / s[0]:
+            r = i
+    return r
+
+
+def rank_expand(sigma: np.ndarray, r_max: int, r_reg: float, eps: float, r_cap: int, align: int = 8) -> int:
+    """Algorithm 3's expansion test after the SVD of a step at maximum rank
+    r_max: when s_{r_max} > r_reg s_max (S-eigenvalues s = sigma^2) the next
+    step uses (1 + eps) r_max. Readings: (1 + eps) r_max is rounded up to a
+    multiple of `align` (the rank granularity of the kernels) and capped at
+    r_cap; the strict '>' of the algorithm is kept (the prose's membership test
+    differs only at equality)."""
+    s = np.asarray(sigma, dtype=np.float64) ** 2
+    if not (s[0] > 0 and s[r_max - 1] > r_reg * s[0]):
+        return r_max
+    grown = int(np.ceil((1.0 + eps) * r_max))
+    grown = -(-grown // align) * align
+    return min(grown, r_cap)
+
+
+def extend_basis(V_prev: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Warm start of a step whose maximum rank grew (Algorithm 3 leaves this
+    open; reading): the previous basis followed by the columns of a seeded
+    Gaussian block G; the subspace iteration orthonormalises the whole block."""
+    return np.concatenate([np.asarray(V_prev, dtype=np.float64), np.asarray(G, dtype=np.float64)], axis=1)
+
+
+def wssr_step_adaptive(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: int, r_reg: float,
+                       eps: float, r_cap: int, mode: str = "damped", sigma_floor: float | None = None):
+    """One step of Algorithm 3 at maximum rank r_max = V_prev.shape[1]: the
+    SSI-SVD of rank r_max (Algorithm 1 + Rayleigh-Ritz), the rank r of
+    Eq. (ruler), the apply of Eq. (updated_sr_1) on the leading r singular
+    triplets, and the maximum rank of the next step.
+
+    Returns (delta, sigma, V, r, r_max_next)."""
+    delta_full, sigma, V = wssr_step(O, g, V_prev, lam, m, mode, sigma_floor)
+    r = rank_select(sigma, r_reg)
+    delta = woodbury_apply(V, sigma, g, lam, mode, sigma_floor, r_sel=r)
+    return delta, sigma, V, r, rank_expand(sigma, V.shape[1], r_reg, eps, r_cap)
 
 
 def local_energy_gradient(O: np.ndarray, E_loc: np.ndarray) -> np.ndarray:
