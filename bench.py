@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "WSSR step ms & % roofline at N=16k,M=1M,r=256 BF16 vs FP32; rel err vs FP64"
+METRIC_RSSR = "randomized sketching SVD ms & % roofline at N=16k,M=1M,r=256 BF16"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -183,7 +184,8 @@ def run_reference(args, w):
 
 def workload_config(w, args, engine):
     return {"workload": w.name, "N": w.N, "M": w.M, "r": w.r, "lambda": w.lam, "m": w.m,
-            "history_weight": args.history,
+            "path": args.path + (f"-q{args.rssr_q}" if args.path == "rssr" else ""),
+            "history_weight": args.history, "apply": args.apply, "sigma_floor": args.sigma_floor,
             "o_dtype": args.dtype, "engine": engine, "parallelism": f"replicas{args.gpus}",
             "l2": f"inputs larger than L2 (O = {w.N * w.M * (2 if args.dtype == 'bf16' else 4) / 1e9:.1f} GB)"}
 
@@ -243,36 +245,74 @@ def measured_traffic(w, kernel):
 
 def step_roofline_ms(w, args, peaks):
     esz = 2 if args.dtype == "bf16" else 4
-    passes = 2 * w.m + 1
+    passes = 2 * args.rssr_q + 2 if args.path == "rssr" else 2 * w.m + 1
     t_bytes = w.N * w.M * esz / (peaks["hbm_gbs"] * 1e9)
     t_flop = 2.0 * w.N * w.M * w.r / (peaks["bf16_tflops"] * 1e12)
     return passes * max(t_bytes, t_flop) * 1e3
 
 
-class Stepper:
-    """One WSSR step per call: the plain step, or the history-averaged step with
-    sigma and Lbar carried from call to call (double-buffered)."""
+def resolve_sigma_floor(args, w):
+    """The apply mode's threshold: cutoff sigma_floor (default lambda), pinv eps_tol (default 1e-5)."""
+    if args.sigma_floor is None:
+        args.sigma_floor = {"damped": 0.0, "cutoff": w.lam, "pinv": 1e-5}[args.apply]
+    return args.sigma_floor
 
-    def __init__(self, s, r, dev, weight):
+
+class Stepper:
+    """One call of the timed path per __call__, with its per-step inputs:
+    - "step": wssr_step on a fresh gradient g (M floats); with a history weight
+      w > 0 the averaged step (Section 4.1), sigma and Lbar carried from call to
+      call (double-buffered);
+    - "local-energy": the step with g = (2/N) O_c^T (E - mean E) formed inside
+      from per-sample local energies E (N floats, Eq. (gradient:vmc));
+    - "rssr": the randomized sketching SVD (Appendix A) from a fresh sample-side
+      Gaussian block Omega (N x r) with q power iterations."""
+
+    def __init__(self, s, w, dev, args, M=None):
         import torch
-        self.s, self.w = s, weight
-        self.sig = [torch.zeros(r, device=dev, dtype=torch.float64) for _ in range(2)]
-        self.lb = [torch.zeros(r, device=dev, dtype=torch.float64) for _ in range(2)]
-        self.gbar = None
+        self.s, self.w, self.dev = s, w, dev
+        M = w.M if M is None else M  # the network operator works in its padded parameter space
+        self.path, self.weight, self.q = args.path, args.history, args.rssr_q
+        if self.path != "step" and self.weight > 0:
+            raise SystemExit("--history applies to --path step only")
+        self.sig = [torch.zeros(w.r, device=dev, dtype=torch.float64) for _ in range(2)]
+        self.lb = [torch.zeros(w.r, device=dev, dtype=torch.float64) for _ in range(2)]
+        self.gbar = torch.empty(M, device=dev) if self.weight > 0 else None
+        self.g = torch.empty(M, device=dev) if self.path == "local-energy" else None
         self.k = 0
 
-    def __call__(self, O, g, V, delta, sigma, V_out):
-        if self.w <= 0.0:
-            self.s.step(O, g, V, out=(delta, sigma, V_out))
+    def inputs(self, n):
+        from synth import workloads as wl
+        w, dev = self.w, self.dev
+        if self.path == "local-energy":
+            return [wl.local_energies_torch(w.N, t, dev, "bench") for t in range(n)]
+        if self.path == "rssr":
+            return [wl.sketch_block_torch(w.N, w.r, dev, "bench", t) for t in range(n)]
+        return [wl.gradient_torch(w.M, t, dev, "bench") for t in range(n)]
+
+    def d2h_bytes(self):
+        w = self.w
+        return 4 * w.M * w.r + 8 * w.r if self.path == "rssr" else 4 * w.M + 8 * w.r
+
+    def __call__(self, O, inp, V, delta, sigma, V_out):
+        if self.path == "rssr":
+            self.s.randomized_svd(O, inp, q=self.q, out=(V_out, sigma))
             return
-        import torch
-        if self.gbar is None:
-            self.gbar = torch.empty_like(g)
+        if self.path == "local-energy":
+            self.s.step_local_energy(O, inp, V, out=(delta, sigma, V_out, self.g))
+            return
+        if self.weight <= 0.0:
+            self.s.step(O, inp, V, out=(delta, sigma, V_out))
+            return
         i, j = self.k & 1, (self.k & 1) ^ 1
-        self.s.step_averaged(O, g, V, self.sig[i], self.lb[i], self.w,
+        self.s.step_averaged(O, inp, V, self.sig[i], self.lb[i], self.weight,
                              out=(delta, self.sig[j], V_out, self.lb[j], self.gbar))
         sigma.copy_(self.sig[j])
         self.k += 1
+
+    def result(self, delta, V_out):
+        """The step's result read back to the host in the end-to-end run."""
+        return V_out if self.path == "rssr" else delta
 
 
 def run_ours(args, w):
@@ -293,16 +333,15 @@ def run_ours(args, w):
     dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
     ld = w.M + ((-w.M) % 8)
     master = None
-    if args.compare_f32 > 0 and args.dtype == "bf16":
+    if args.compare_f32 > 0 and args.dtype == "bf16" and args.path == "step":
         master = torch.zeros((w.N, ld), dtype=torch.float32, device=dev)
     O = wl.planted_O_torch(w, dev, out_dtype=dt, ld=ld, master=master)
-    gs = [wl.gradient_torch(w.M, t, dev, "bench") for t in range(max(1, args.steps))]
     V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
-    torch.cuda.synchronize()
-
     s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine,
-             history=args.history > 0)
-    step = Stepper(s, w.r, dev, args.history)
+             history=args.history > 0, apply_mode=args.apply, sigma_floor=resolve_sigma_floor(args, w))
+    step = Stepper(s, w, dev, args)
+    gs = step.inputs(max(1, args.steps))
+    torch.cuda.synchronize()
     engine_name = "tcgen05" if (args.dtype == "bf16" and s.handle and args.engine != "simt"
                                 and _uses_tc(s)) else "simt"
     V, _ = s.init_subspace(O, V0)
@@ -351,7 +390,7 @@ def run_ours(args, w):
         O_host = torch.empty(O.shape, dtype=O.dtype, pin_memory=True)
         O_host.copy_(O)
         g_host = [g.cpu().pin_memory() for g in gs[:args.e2e_steps]]
-        d_host = torch.empty(w.M, pin_memory=True)
+        d_host = torch.empty(step.result(delta, Vb).shape, pin_memory=True)
         s_host = torch.empty(w.r, dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
         if world > 1:
@@ -364,7 +403,7 @@ def run_ours(args, w):
             gs[t].copy_(g_host[t], non_blocking=True)
             step(O, gs[t], V, delta, sigma, Vb)
             V, Vb = Vb, V
-            d_host.copy_(delta, non_blocking=True)
+            d_host.copy_(step.result(delta, Vb), non_blocking=True)
             s_host.copy_(sigma, non_blocking=True)
         e3.record(stream)
         torch.cuda.synchronize()
@@ -375,12 +414,12 @@ def run_ours(args, w):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
         e2e = {"value": e2e_ms, "unit": "ms",
-               "h2d_bytes_per_step": int(O.numel() * O.element_size() + 4 * w.M),
-               "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
+               "h2d_bytes_per_step": int(O.numel() * O.element_size() + gs[0].numel() * gs[0].element_size()),
+               "d2h_bytes_per_step": int(step.d2h_bytes()), "steps": args.e2e_steps}
         del O_host
 
     compare = None
-    if master is not None:
+    if master is not None and args.path == "step":
         # the plain FP32 SIMT path on the FP32 master of the same matrix, same start
         d_bf = delta.clone()
         s32 = WSSR(w.N, w.M, w.r, w.lam, m=w.m, dtype="f32", engine="simt")
@@ -423,20 +462,21 @@ def run_ours(args, w):
     if rank != 0:
         return
     cpu = None
-    if world == 1 and args.cpu_cols > 0:
+    if world == 1 and args.cpu_cols > 0 and args.path == "step" and args.history <= 0 and args.apply == "damped":
         ms, info = time_oracle(w, max(w.r, args.cpu_cols // 4))
         info["value"] = ms
         info["unit"] = "ms"
         cpu = info
     line = {
-        "metric": METRIC, "value": ms_step / world, "unit": "ms", "n_gpus": world,
+        "metric": METRIC if args.path != "rssr" else METRIC_RSSR, "value": ms_step / world, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic", "config": workload_config(w, args, engine_name),
         "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         "roofline": roof,
         "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
-                          "model": f"{2 * w.m + 1} O passes x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
+                          "model": f"{2 * args.rssr_q + 2 if args.path == 'rssr' else 2 * w.m + 1} O passes "
+                                   "x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
         "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
@@ -571,8 +611,9 @@ def run_mlp_mf(args, w):
     g_user = wl.gradient_torch(w.M, 0, dev, "bench")
     g = ans.pad(g_user)
     s = WSSR(w.N, ans.Mp, w.r, w.lam, m=w.m, m_init=args.m_init, dtype="bf16", engine="tcgen05",
-             history=args.history > 0)
-    step = Stepper(s, w.r, dev, args.history)
+             history=args.history > 0, apply_mode=args.apply, sigma_floor=resolve_sigma_floor(args, w))
+    step = Stepper(s, w, dev, args, M=ans.Mp)
+    ins = step.inputs(nsteps + 1) if args.path == "local-energy" else [g] * (nsteps + 1)
     V, _ = s.init_subspace(ans.operator(theta, xs[0]), ans.pad(wl.start_subspace_torch(w.M, w.r, dev, "bench")))
     s.check("init_subspace")
     delta = torch.empty(ans.Mp, device=dev)
@@ -585,7 +626,7 @@ def run_mlp_mf(args, w):
         theta.sub_(d_user * (1e-3 * theta.norm() / d_user.norm()))
 
     for t in range(args.warmup):
-        step(ans.operator(theta, xs[1 + t]), g, V, delta, sigma, Vb)
+        step(ans.operator(theta, xs[1 + t]), ins[1 + t], V, delta, sigma, Vb)
         sr_update()
         V, Vb = Vb, V
     s.check("warmup")
@@ -601,7 +642,7 @@ def run_mlp_mf(args, w):
     launches = 0
     e0.record(stream)
     for t in range(args.steps):
-        step(ans.operator(theta, xs[1 + args.warmup + t]), g, V, delta, sigma, Vb)
+        step(ans.operator(theta, xs[1 + args.warmup + t]), ins[1 + args.warmup + t], V, delta, sigma, Vb)
         launches += s.last_launch_count()
         sr_update()
         V, Vb = Vb, V
@@ -624,6 +665,8 @@ def run_mlp_mf(args, w):
     if args.e2e_steps > 0:
         th_host = theta.cpu().pin_memory()
         x_host = [xs[t].cpu().pin_memory() for t in range(args.e2e_steps)]
+        in_host = [ins[t].cpu().pin_memory() for t in range(args.e2e_steps)]
+        in_dev = torch.empty_like(ins[0])
         d_host = torch.empty(w.M, pin_memory=True)
         s_host = torch.empty(w.r, dtype=torch.float64, pin_memory=True)
         th_dev, x_dev = torch.empty_like(theta), torch.empty_like(xs[0])
@@ -633,7 +676,8 @@ def run_mlp_mf(args, w):
         for t in range(args.e2e_steps):
             th_dev.copy_(th_host, non_blocking=True)
             x_dev.copy_(x_host[t], non_blocking=True)
-            step(ans.operator(th_dev, x_dev), g, V, delta, sigma, Vb)
+            in_dev.copy_(in_host[t], non_blocking=True)
+            step(ans.operator(th_dev, x_dev), in_dev, V, delta, sigma, Vb)
             V, Vb = Vb, V
             d_host.copy_(ans.unpad(delta), non_blocking=True)
             s_host.copy_(sigma, non_blocking=True)
@@ -641,7 +685,7 @@ def run_mlp_mf(args, w):
         torch.cuda.synchronize()
         s.check("e2e")
         e2e = {"value": e2.elapsed_time(e3) / args.e2e_steps, "unit": "ms",
-               "h2d_bytes_per_step": int(4 * w.M + xs[0].numel() * 4),
+               "h2d_bytes_per_step": int(4 * w.M + xs[0].numel() * 4 + ins[0].numel() * 4),
                "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
 
     compare = None
@@ -704,7 +748,7 @@ def run_mlp_mf(args, w):
     if rank != 0:
         return
     cpu = None
-    if world == 1 and args.cpu_cols > 0:
+    if world == 1 and args.cpu_cols > 0 and args.path == "step" and args.history <= 0 and args.apply == "damped":
         _, cpu = mlp_cpu_sample(w, max(w.r, args.cpu_cols // 4))
     line = {"metric": "WSSR step ms, matrix-free O (JVP/VJP on tcgen05) for a 2.2M-parameter tanh MLP",
             "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -712,8 +756,8 @@ def run_mlp_mf(args, w):
             "dtype": "bf16", "data": "synthetic",
             "config": {"workload": w.name, "widths": list(w.widths), "N": w.N, "M": w.M, "M_padded": ans.Mp,
                        "r": w.r, "lambda": w.lam, "m": w.m, "engine": "tcgen05 matrix-free",
-                       "history_weight": args.history,
-                       "parallelism": f"replicas{world}",
+                       "path": args.path, "history_weight": args.history, "apply": args.apply,
+                       "sigma_floor": args.sigma_floor, "parallelism": f"replicas{world}",
                        "l2": "operand source (activations+adjoints, ~104 MB bf16) is L2-resident by design; "
                              "the basis blocks (1.1 GB) exceed L2"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
@@ -756,6 +800,14 @@ def main():
     ap.add_argument("--history", type=float, default=0.0,
                     help="history-averaging weight w in [0, 1) (Section 4.1): run wssr_step_averaged "
                          "with sigma and Lbar carried from step to step")
+    ap.add_argument("--path", default="step", choices=["step", "local-energy", "rssr"],
+                    help="what one timed step runs: the WSSR step on a given gradient, the step with "
+                         "the gradient formed from local energies, or the randomized sketching SVD")
+    ap.add_argument("--rssr-q", type=int, default=2, help="power iterations of --path rssr")
+    ap.add_argument("--apply", default="damped", choices=["damped", "cutoff", "pinv"],
+                    help="regulariser of the apply (damped, the paper's cutoff, truncated pseudo-inverse)")
+    ap.add_argument("--sigma-floor", type=float, default=None,
+                    help="cutoff: sigma_floor (default lambda); pinv: eps_tol (default 1e-5)")
     ap.add_argument("--materialise", action="store_true",
                     help="MLP workloads: form O with the per-sample Jacobian kernel instead of the "
                          "matrix-free operator")
@@ -763,6 +815,8 @@ def main():
     from synth import workloads as wl
     w = wl.WORKLOADS[args.workload]
     if isinstance(w, wl.MLPWorkload):
+        if args.path == "rssr" or (args.materialise and (args.path != "step" or args.history > 0)):
+            raise SystemExit("the network workloads run --path step or local-energy (matrix-free)")
         if args.dtype is None:
             args.dtype = "f32"
         if args.impl == "reference":

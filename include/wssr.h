@@ -88,6 +88,10 @@ typedef struct {
   int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
   int32_t history;      /* 1: allocate the workspace of wssr_step_averaged (tcgen05 engine) (default 0) */
   int32_t reserved;     /* 0 */
+  double r_reg;         /* truncation ratio of Eq. (ruler) (Section 4.3), 0 <= r_reg <= 1 (default 0 = off):
+                           the apply keeps the leading Ritz triplets with r_reg <= sigma_i^2 / sigma_1^2
+                           (the paper's s_i are singular values of S = squares of sigma_i); the rest
+                           of span(V) joins the complement term */
 } wssr_options;
 
 struct wssr_mlp_ctx;
@@ -258,7 +262,9 @@ enum {
   WSSR_KCAT_RR = 3,     /* Rayleigh-Ritz Gram, Jacobi, rotations */
   WSSR_KCAT_APPLY = 4,  /* V^T g and the Woodbury apply */
   WSSR_KCAT_SOURCE = 5, /* matrix-free operator: forward/backward pass of the network, packing */
-  WSSR_KCAT_COUNT = 6
+  WSSR_KCAT_HISTORY = 6, /* history averaging: the r extra rows and the history term of pass B */
+  WSSR_KCAT_GRADIENT = 7, /* VMC gradient from local energies (when not fused into pass B) */
+  WSSR_KCAT_COUNT = 8
 };
 
 /* Start recording an event pair around every kernel group enqueued on `h`
@@ -319,6 +325,36 @@ wssr_status wssr_mlp_pad(wssr_mlp_handle h, const float* src, int64_t cols, floa
                          wssr_stream_t stream);
 wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst,
                            wssr_stream_t stream);
+
+/* ---- Adaptive rank (Section 4.3, Eq. (ruler) and Algorithm 3) ----
+ * wssr_create's r is the capacity r_cap; the working rank (Algorithm 3's
+ * r_max, the number of columns every following call reads and writes) starts
+ * at r_cap and is changed between calls. */
+
+/* Set the working rank: 8 <= r <= r_cap, r a multiple of 8. The next call's
+ * V_prev / V_out / sigma have r columns / entries. INVALID_ARG otherwise. */
+wssr_status wssr_set_rank(wssr_handle h, int32_t r);
+
+/* The working rank, or -1 for NULL. */
+int32_t wssr_get_rank(wssr_handle h);
+
+/* From the r = working-rank Ritz values `sigma` (device, descending, as written
+ * by the last step on `stream`): r_sel = max{i <= r : r_reg <= sigma_i^2 / sigma_1^2}
+ * (Eq. (ruler); 0 when sigma_1 = 0), and r_next = the next step's maximum rank by
+ * Algorithm 3's test: (1 + eps) r rounded up to a multiple of 8 and capped at
+ * r_cap when sigma_r^2 > r_reg sigma_1^2, else r. Synchronises `stream` (the
+ * decision shapes the next step's launches). r_sel may be NULL. r_reg in [0, 1],
+ * eps > 0, else INVALID_ARG. */
+wssr_status wssr_rank_next(wssr_handle h, const double* sigma, double r_reg, double eps, int32_t* r_sel,
+                           int32_t* r_next, wssr_stream_t stream);
+
+/* Warm start at a larger maximum rank (Algorithm 3 leaves it open; reading:
+ * the previous basis followed by fresh seeded Gaussian columns, which the next
+ * step's subspace iteration orthonormalises): V_out (M x r_new, row-major) =
+ * [V_prev (M x r_prev) | G (M x (r_new - r_prev))]. Device pointers; V_out may
+ * not overlap V_prev or G; G may be NULL when r_new == r_prev. Asynchronous. */
+wssr_status wssr_extend_basis(const float* V_prev, int64_t M, int32_t r_prev, const float* G, int32_t r_new,
+                              float* V_out, wssr_stream_t stream);
 
 /* Diagnostics of the last wssr_step / wssr_init_subspace (synchronises the
  * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz

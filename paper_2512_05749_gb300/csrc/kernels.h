@@ -150,7 +150,9 @@ void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, 
 // sigma_i = sqrt(Hp_ii) from the FP64 Gram of the rotated block; d_i; e_i = d_i c_i
 void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t st);
 void launch_woodbury_coeffs(const double* sigma, const double* c, int r, double lam, int mode,
-                            double sigma_floor, double* e, int* status, cudaStream_t st);
+                            double sigma_floor, double* e, int* status, cudaStream_t st, double r_reg = 0.0);
+void launch_extend_basis(const float* V_prev, int64_t M, int r_prev, const float* G, int r_new, float* V_out,
+                         cudaStream_t st);
 void launch_woodbury(const float* V, const float* g, const double* e, int64_t M, int r,
                      double lam_eff, float* delta, cudaStream_t st);
 // finite check of a float array: sets WSSR_ERR_NONFINITE

@@ -1147,10 +1147,19 @@ __global__ void k_finalize_sigma(const double* __restrict__ Hp, int r, double* _
 
 __global__ void k_woodbury_coeffs(const double* __restrict__ sigma, const double* __restrict__ c,
                                   int r, double lam, int mode, double floor_, double* __restrict__ e,
-                                  int* status) {
+                                  int* status, double r_reg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= r) return;
   const double s2 = sigma[i] * sigma[i];
+  if (r_reg > 0.0) {
+    // rank of Eq. (ruler): keep the leading triplets with r_reg <= s_i / s_max
+    // (S-eigenvalues s = sigma^2, sigma descending); the rest join the complement
+    const double s2max = sigma[0] * sigma[0];
+    if (!(s2max > 0.0 && r_reg <= s2 / s2max)) {
+      e[i] = 0.0;
+      return;
+    }
+  }
   double d;
   if (mode == WSSR_APPLY_CUTOFF) {
     d = (s2 > 0.0) ? 1.0 / s2 - 1.0 / floor_ : 0.0;
@@ -1206,8 +1215,24 @@ void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t 
 }
 
 void launch_woodbury_coeffs(const double* sigma, const double* c, int r, double lam, int mode,
-                            double sigma_floor, double* e, int* status, cudaStream_t st) {
-  k_woodbury_coeffs<<<1, 256, 0, st>>>(sigma, c, r, lam, mode, sigma_floor, e, status);
+                            double sigma_floor, double* e, int* status, cudaStream_t st, double r_reg) {
+  k_woodbury_coeffs<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(sigma, c, r, lam, mode, sigma_floor, e, status,
+                                                                r_reg);
+}
+
+// Warm start at a larger rank: V_out = [V_prev | G] (M x r_new, row-major).
+__global__ void k_extend_basis(const float* __restrict__ Vp, int64_t M, int rp, const float* __restrict__ G,
+                               int rn, float* __restrict__ Vo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * rn) return;
+  const int64_t m = e / rn;
+  const int j = (int)(e % rn);
+  Vo[e] = j < rp ? Vp[m * rp + j] : G[m * (rn - rp) + (j - rp)];
+}
+
+void launch_extend_basis(const float* V_prev, int64_t M, int r_prev, const float* G, int r_new, float* V_out,
+                         cudaStream_t st) {
+  k_extend_basis<<<(unsigned)ceil_div(M * r_new, 256), 256, 0, st>>>(V_prev, M, r_prev, G, r_new, V_out);
 }
 
 void launch_woodbury(const float* V, const float* g, const double* e, int64_t M, int r,

@@ -30,7 +30,8 @@ using namespace wssr;
 
 struct wssr_ctx {
   int64_t N = 0, M = 0;
-  int r = 0;
+  int r = 0;                   // working rank (r_max of the adaptive scheme)
+  int r_cap = 0;               // rank the workspace was sized for
   double lam = 0;
   wssr_options opt{};
   int dev = 0, num_sms = 0;
@@ -281,7 +282,7 @@ void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row
 
 // The r history rows of Y: Y[N + j, :] = gamma sigma_prev[j] (V_prev^T Xop)[j, :].
 void history_rows(wssr_ctx* h, const Hist* hist, const void* Xop, float* Y, cudaStream_t st) {
-  Timed tm(h, WSSR_KCAT_PASS_A, st);
+  Timed tm(h, WSSR_KCAT_HISTORY, st);
   const int r = h->r;
   int used = 0;
   tc_xgram_launch(h->Vhp, Xop, h->M, r, h->gram_splits_tc, h->tc_gram_part, h->opt.wait_cap, h->status, st,
@@ -294,7 +295,7 @@ void history_rows(wssr_ctx* h, const Hist* hist, const void* Xop, float* Y, cuda
 // History term of pass B, gamma V_prev diag(sigma_prev) Q_bot (M x r, FP32,
 // into h->Z), with Q_bot the history rows of the orthonormalised block.
 void history_pass_B_term(wssr_ctx* h, const Hist* hist, const float* Q, cudaStream_t st) {
-  Timed tm(h, WSSR_KCAT_PASS_B, st);
+  Timed tm(h, WSSR_KCAT_HISTORY, st);
   const int r = h->r;
   launch_scale_rows_r(Q + h->N * r, r, hist->sigma_prev, hist->gamma, r, h->TW, st);
   launch_split3_T(h->TW, r, h->TWT3, st);
@@ -415,7 +416,7 @@ wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const flo
                          : h->opt.apply_mode == WSSR_APPLY_PINV ? INFINITY
                                                                 : h->lam;
   launch_woodbury_coeffs(sigma, h->c, r, h->lam, h->opt.apply_mode, h->opt.sigma_floor, h->e,
-                         h->status, st);
+                         h->status, st, h->opt.r_reg);
   launch_woodbury(V, g, h->e, h->M, r, lam_eff, delta, st);
   h->launches += 4;
   return check_launch(h);
@@ -447,6 +448,32 @@ wssr_status prepare_op(wssr_ctx* h, const wssr_operator* op, cudaStream_t st) {
   h->launches += n;
   return s;
 }
+
+// Rank-dependent launch parameters: split counts of the forward products and
+// the pitch of the sample-side operand copy.
+void configure_rank(wssr_ctx* h, int r) {
+  h->r = r;
+  h->splits_simt = passA_simt_splits(h->N, h->M, r, h->num_sms);
+  h->splits_tc = h->use_tc ? tc_passA_splits(h->N, h->M, r, h->num_sms) : 1;
+  h->splits_mf = (h->use_tc && h->M % 64 == 0) ? tc_mf_jvp_splits(h->N, h->M / 64, r, h->num_sms) : 1;
+  h->ldy = (h->N + r + 7) / 8 * 8;  // the operand copy of Y also holds the history rows
+  h->mu_valid = false;
+  h->c_ready = false;
+}
+
+// Forward-product partials for every working rank up to r_cap (fewer columns
+// take more splits).
+int64_t yp_capacity(wssr_ctx* h) {
+  int64_t need = 0;
+  for (int r = 8; r <= h->r_cap; r += 8) {
+    configure_rank(h, r);
+    need = std::max(need, (int64_t)std::max(h->use_tc ? h->splits_tc : h->splits_simt, h->splits_mf) * h->N * r);
+  }
+  configure_rank(h, h->r_cap);
+  return need;
+}
+
+bool rank_ok(const wssr_ctx* h, int64_t r) { return r >= 8 && r % 8 == 0 && r <= h->r_cap; }
 
 }  // namespace
 
@@ -486,12 +513,14 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (opt.engine < WSSR_ENGINE_AUTO || opt.engine > WSSR_ENGINE_TCGEN05) return WSSR_ERR_INVALID_ARG;
   if (opt.wait_cap < 1) return WSSR_ERR_INVALID_ARG;
   if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;
+  if (!(opt.r_reg >= 0.0 && opt.r_reg <= 1.0)) return WSSR_ERR_INVALID_ARG;
 
   wssr_ctx* h = new (std::nothrow) wssr_ctx();
   if (!h) return WSSR_ERR_OOM;
   h->N = N;
   h->M = M;
   h->r = r;
+  h->r_cap = r;
   h->lam = lambda;
   h->opt = opt;
   if (cudaGetDevice(&h->dev) != cudaSuccess ||
@@ -511,13 +540,9 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   }
 
   const size_t f = sizeof(float), d = sizeof(double);
-  h->splits_simt = passA_simt_splits(N, M, r, h->num_sms);
-  h->splits_tc = h->use_tc ? tc_passA_splits(N, M, r, h->num_sms) : 1;
-  h->splits_mf = (h->use_tc && M % 64 == 0) ? tc_mf_jvp_splits(N, M / 64, r, h->num_sms) : 1;
   h->ldx = (M + 7) / 8 * 8;
-  h->ldy = (N + r + 7) / 8 * 8;  // the operand copy of Y also holds the history rows
-  // pass A partials: one N x r block per split
-  h->yp_elems = (int64_t)std::max(h->use_tc ? h->splits_tc : h->splits_simt, h->splits_mf) * N * r;
+  // pass A partials: one N x r block per split, for any working rank up to r
+  h->yp_elems = yp_capacity(h);
   // column-sum partials: split reduction (16-row blocks of Y), casts and applies (64-row blocks)
   const int64_t blocks64 = std::max(ceil_div(N, 16), ceil_div(std::max(N + r, M), 64));
   const int64_t gpart = std::max(gram_part_elems(N + r, r), gram_part_elems(M, r));
@@ -615,7 +640,7 @@ wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const flo
   const int r = h->r;
   {
     // gbar = (1 - w) g + w V_prev (sigma_prev * Lbar_prev)  (Eq. (barg), (Lhat))
-    Timed tm(h, WSSR_KCAT_APPLY, st);
+    Timed tm(h, WSSR_KCAT_HISTORY, st);
     launch_hist_coeffs(sigma_prev, Lbar_prev, weight, r, h->e, st);
     launch_woodbury(V_prev, g, h->e, h->M, r, 1.0 / (1.0 - weight), h->gbar, st);
     h->launches += 2;
@@ -644,7 +669,7 @@ wssr_status wssr_step_local_energy(wssr_handle h, const wssr_operator* op, const
   h->mu_valid = false;
   if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   {
-    Timed tm(h, WSSR_KCAT_APPLY, st);
+    Timed tm(h, WSSR_KCAT_GRADIENT, st);
     launch_energy_weights(E_loc, h->N, h->wE, h->wE_sum, st);
     h->launches++;
     if (op->kind == WSSR_OP_MLP) {
@@ -825,6 +850,60 @@ wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n) {
     out[i] = v;
   }
   return WSSR_OK;
+}
+
+wssr_status wssr_set_rank(wssr_handle h, int32_t r) {
+  if (!h || !rank_ok(h, r) || r > h->N - 1 || r > h->M) return WSSR_ERR_INVALID_ARG;
+  configure_rank(h, r);
+  return WSSR_OK;
+}
+
+int32_t wssr_get_rank(wssr_handle h) { return h ? h->r : -1; }
+
+wssr_status wssr_rank_next(wssr_handle h, const double* sigma, double r_reg, double eps, int32_t* r_sel,
+                           int32_t* r_next, wssr_stream_t stream) {
+  if (!h || !sigma || !r_next || !(r_reg >= 0.0 && r_reg <= 1.0) || !(eps > 0.0)) return WSSR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int r = h->r;
+  std::vector<double> sg((size_t)r);
+  if (cudaMemcpyAsync(sg.data(), sigma, (size_t)r * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return WSSR_ERR_CUDA;
+  // Eq. (ruler) on the S-eigenvalues sigma_i^2 (the same expressions as the apply's truncation)
+  const double s1 = sg[0] * sg[0];
+  int sel = 0;
+  if (s1 > 0.0)
+    for (int i = 0; i < r; ++i)
+      if (r_reg <= sg[i] * sg[i] / s1) sel = i + 1;
+  // Algorithm 3's expansion test: r_max <- (1 + eps) r_max, rounded up to a multiple of 8, capped
+  int nxt = r;
+  if (s1 > 0.0 && sg[r - 1] * sg[r - 1] > r_reg * s1) {
+    int64_t grown = (int64_t)ceil((1.0 + eps) * (double)r);
+    grown = (grown + 7) / 8 * 8;
+    nxt = (int)std::min<int64_t>(grown, h->r_cap);  // r_cap <= min(N - 1, M) by construction
+  }
+  if (r_sel) *r_sel = sel;
+  *r_next = nxt;
+  return WSSR_OK;
+}
+
+wssr_status wssr_extend_basis(const float* V_prev, int64_t M, int32_t r_prev, const float* G, int32_t r_new,
+                              float* V_out, wssr_stream_t stream) {
+  if (!V_prev || !V_out || M < 1 || r_prev < 1 || r_new < r_prev || (r_new > r_prev && !G))
+    return WSSR_ERR_INVALID_ARG;
+  // the row pitch changes: the output may not overlap the inputs
+  const char* o0 = (const char*)V_out;
+  const char* o1 = o0 + (size_t)M * r_new * sizeof(float);
+  const char* p0 = (const char*)V_prev;
+  const char* p1 = p0 + (size_t)M * r_prev * sizeof(float);
+  if (o0 < p1 && p0 < o1) return WSSR_ERR_INVALID_ARG;
+  if (G) {
+    const char* g0 = (const char*)G;
+    const char* g1 = g0 + (size_t)M * (r_new - r_prev) * sizeof(float);
+    if (o0 < g1 && g0 < o1) return WSSR_ERR_INVALID_ARG;
+  }
+  launch_extend_basis(V_prev, M, r_prev, G, r_new, V_out, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
 
 wssr_status wssr_profile_begin(wssr_handle h) {

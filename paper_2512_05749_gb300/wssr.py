@@ -42,12 +42,13 @@ EXPORTED = [
     "wssr_profile_end", "wssr_woodbury_noalloc", "wssr_get_stats", "wssr_mlp_param_count",
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
-    "wssr_step_local_energy", "wssr_randomized_svd",
+    "wssr_step_local_energy", "wssr_randomized_svd", "wssr_set_rank", "wssr_get_rank", "wssr_rank_next",
+    "wssr_extend_basis",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
 
-KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply", "source"]
+KCAT_NAMES = ["pass_A", "pass_B", "orth", "rayleigh_ritz", "apply", "source", "history", "gradient"]
 
 
 class wssr_options(ctypes.Structure):
@@ -62,6 +63,7 @@ class wssr_options(ctypes.Structure):
         ("jacobi_sweeps", ctypes.c_int32),
         ("history", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("r_reg", ctypes.c_double),
     ]
 
 
@@ -142,6 +144,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_profile_end": (i32, [vp, P(f64), P(i64), i32]),
         "wssr_woodbury_noalloc": (i32, [vp, vp, vp, vp, i64, i32, f64, i32, f64, vp]),
         "wssr_get_stats": (i32, [vp, P(i64), i32]),
+        "wssr_set_rank": (i32, [vp, i32]),
+        "wssr_get_rank": (i32, [vp]),
+        "wssr_rank_next": (i32, [vp, vp, f64, f64, P(ctypes.c_int32), P(ctypes.c_int32), vp]),
+        "wssr_extend_basis": (i32, [vp, i64, i32, vp, i32, vp, vp]),
         "wssr_mlp_param_count": (i64, [P(wssr_mlp_desc)]),
         "wssr_mlp_create": (i32, [P(wssr_mlp_desc), i64, P(vp)]),
         "wssr_mlp_destroy": (None, [vp]),
@@ -271,6 +277,38 @@ def wssr_woodbury_noalloc(V, sigma, g, delta, lam: float, apply_mode: int = WSSR
            "wssr_woodbury_noalloc")
 
 
+def wssr_set_rank(h: int, r: int):
+    _check(load().wssr_set_rank(h, int(r)), "wssr_set_rank")
+
+
+def wssr_get_rank(h: int) -> int:
+    return int(load().wssr_get_rank(h))
+
+
+def wssr_rank_next(h: int, sigma, r_reg: float, eps: float, stream=None):
+    """(r_sel, r_next): the rank of Eq. (ruler) and Algorithm 3's next maximum rank."""
+    sel, nxt = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().wssr_rank_next(h, _ptr(sigma), r_reg, eps, ctypes.byref(sel), ctypes.byref(nxt),
+                                 _stream(stream)), "wssr_rank_next")
+    return int(sel.value), int(nxt.value)
+
+
+def wssr_extend_basis(V_prev, G, V_out, stream=None):
+    M, r_prev = V_prev.shape
+    r_new = V_out.shape[1]
+    _check(load().wssr_extend_basis(_ptr(V_prev), M, r_prev, _ptr(G) if G is not None else None, r_new,
+                                    _ptr(V_out), _stream(stream)), "wssr_extend_basis")
+
+
+def extend_basis(V_prev, G, stream=None):
+    """[V_prev | G] (M x (r_prev + G.shape[1])): the warm start of a step whose
+    maximum rank grew (the next step's subspace iteration orthonormalises it)."""
+    import torch
+    V = torch.empty(V_prev.shape[0], V_prev.shape[1] + G.shape[1], device=V_prev.device, dtype=torch.float32)
+    wssr_extend_basis(V_prev.contiguous(), G.contiguous(), V, stream)
+    return V
+
+
 def wssr_sync(h: int) -> int:
     return int(load().wssr_sync(h))
 
@@ -363,8 +401,10 @@ class WSSR:
 
     def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
                  dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
-                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000, history: bool = False):
+                 engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000, history: bool = False,
+                 r_reg: float = 0.0):
         opt = wssr_default_options()
+        opt.r_reg = r_reg
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
         opt.history = 1 if history else 0
         opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]
@@ -374,6 +414,7 @@ class WSSR:
         opt.engine = {"auto": WSSR_ENGINE_AUTO, "simt": WSSR_ENGINE_SIMT,
                       "tcgen05": WSSR_ENGINE_TCGEN05}[engine]
         self.N, self.M, self.r, self.lam, self.dtype = N, M, r, lam, dtype
+        self.r_cap, self.r_reg = r, r_reg  # self.r is the working rank (set_rank)
         self.jacobi_sweeps = jacobi_sweeps
         self.handle = wssr_create(N, M, r, lam, opt)
 
@@ -441,13 +482,26 @@ class WSSR:
                            Lbar, gbar, stream)
         return delta, sigma, V, Lbar, gbar
 
-    def randomized_svd(self, O, Omega, q: int = 0, stream=None):
+    def randomized_svd(self, O, Omega, q: int = 0, out=None, stream=None):
         """Randomized sketching SVD from a sample-side block Omega (N x r): returns (V, sigma)."""
         import torch
-        V = torch.empty(self.M, self.r, device=Omega.device, dtype=torch.float32)
-        sigma = torch.empty(self.r, device=Omega.device, dtype=torch.float64)
+        if out is None:
+            V = torch.empty(self.M, self.r, device=Omega.device, dtype=torch.float32)
+            sigma = torch.empty(self.r, device=Omega.device, dtype=torch.float64)
+        else:
+            V, sigma = out
         wssr_randomized_svd(self.handle, self._op(O), Omega.contiguous(), q, V, sigma, stream)
         return V, sigma
+
+    def set_rank(self, r: int):
+        """Working rank of the following calls (Algorithm 3's r_max; 8 <= r <= r_cap, multiple of 8)."""
+        wssr_set_rank(self.handle, r)
+        self.r = int(r)
+
+    def rank_next(self, sigma, eps: float, stream=None):
+        """(r_sel, r_next) after a step: the rank of Eq. (ruler) the apply used, and
+        the next step's maximum rank by Algorithm 3's expansion test (synchronises)."""
+        return wssr_rank_next(self.handle, sigma, self.r_reg, eps, stream)
 
     def init_subspace(self, O, V_rand, stream=None):
         import torch

@@ -254,6 +254,17 @@ def gradient_torch(M: int, step: int, device, *key):
     return gaussian_torch((M,), device, "g", M, step, *key)
 
 
+def local_energies_torch(N: int, step: int, device, *key):
+    """Per-sample local energies E_L(x_n) ~ -2 + 0.3 N(0, 1) (a synthetic
+    stand-in for a molecule's local-energy distribution)."""
+    return gaussian_torch((N,), device, "EL", N, step, *key) * 0.3 - 2.0
+
+
+def sketch_block_torch(N: int, k: int, device, *key):
+    """Sample-side Gaussian block Omega (N x k) of the randomized sketch."""
+    return gaussian_torch((N, k), device, "Omega", N, k, *key)
+
+
 def start_subspace_torch(M: int, r: int, device, *key):
     return gaussian_torch((M, r), device, "V0", M, r, *key)
 
