@@ -186,6 +186,8 @@ def workload_config(w, args, engine):
     return {"workload": w.name, "N": w.N, "M": w.M, "r": w.r, "lambda": w.lam, "m": w.m,
             "path": args.path + (f"-q{args.rssr_q}" if args.path == "rssr" else ""),
             "history_weight": args.history, "apply": args.apply, "sigma_floor": args.sigma_floor,
+            **({"rank0": args.rank0, "r_reg": args.r_reg, "rank_eps": args.rank_eps, "r_cap": w.r}
+               if args.path == "adaptive" else {}),
             "o_dtype": args.dtype, "engine": engine, "parallelism": f"replicas{args.gpus}",
             "l2": f"inputs larger than L2 (O = {w.N * w.M * (2 if args.dtype == 'bf16' else 4) / 1e9:.1f} GB)"}
 
@@ -273,8 +275,10 @@ class Stepper:
         self.s, self.w, self.dev = s, w, dev
         M = w.M if M is None else M  # the network operator works in its padded parameter space
         self.path, self.weight, self.q = args.path, args.history, args.rssr_q
-        if self.path != "step" and self.weight > 0:
+        if self.path not in ("step", "adaptive") and self.weight > 0:
             raise SystemExit("--history applies to --path step only")
+        if self.path == "adaptive" and self.weight > 0:
+            raise SystemExit("--history is not combined with --path adaptive in the bench")
         self.sig = [torch.zeros(w.r, device=dev, dtype=torch.float64) for _ in range(2)]
         self.lb = [torch.zeros(w.r, device=dev, dtype=torch.float64) for _ in range(2)]
         self.gbar = torch.empty(M, device=dev) if self.weight > 0 else None
@@ -314,6 +318,66 @@ class Stepper:
         """The step's result read back to the host in the end-to-end run."""
         return V_out if self.path == "rssr" else delta
 
+    def extra_launches(self) -> int:
+        """Kernels this wrapper launched since the last call, outside the library's step."""
+        return 0
+
+
+class AdaptiveStepper(Stepper):
+    """Algorithm 2's rank control around the step: run at the working rank
+    r_max, read the rank of Eq. (ruler) and the expansion decision back
+    (wssr_rank_next synchronises), and on growth extend the basis by fresh
+    Gaussian columns (drawn before the timed region) and raise the working rank.
+    Keeps its own basis; sigma[:r_max] of the caller's buffer is written."""
+
+    def __init__(self, s, w, dev, args):
+        import torch
+        super().__init__(s, w, dev, args)
+        self.eps = args.rank_eps
+        self.r = args.rank0
+        self.Vbuf = [torch.empty(w.M * w.r, device=dev) for _ in range(2)]
+        self.G = wl_gaussian(w.M * w.r, dev)
+        self.sig = torch.empty(w.r, device=dev, dtype=torch.float64)
+        self.cur = 0
+        self.r_sel = 0
+        self.history = []
+        self.extra = 0
+
+    def start(self, O, V0):
+        self.s.set_rank(self.r)
+        V, _ = self.s.init_subspace(O, V0[:, :self.r].contiguous())
+        self.V(0).copy_(V)
+
+    def extra_launches(self) -> int:
+        n, self.extra = self.extra, 0
+        return n
+
+    def V(self, i):
+        return self.Vbuf[i][: self.w.M * self.r].view(self.w.M, self.r)
+
+    def __call__(self, O, inp, V, delta, sigma, V_out):
+        i, j = self.cur, self.cur ^ 1
+        sg = self.sig[: self.r]
+        self.s.step(O, inp, self.V(i), out=(delta, sg, self.V(j)))
+        sigma[: self.r].copy_(sg)
+        self.r_sel, r_next = self.s.rank_next(sg, self.eps)
+        self.history.append((self.r, self.r_sel))
+        self.cur = j
+        if r_next > self.r:
+            from paper_2512_05749_gb300.wssr import wssr_extend_basis
+            k = r_next - self.r
+            Vn = self.Vbuf[i][: self.w.M * r_next].view(self.w.M, r_next)
+            wssr_extend_basis(self.V(j), self.G[: self.w.M * k].view(self.w.M, k), Vn)
+            self.extra += 1
+            self.r = r_next
+            self.s.set_rank(r_next)
+            self.cur = i
+
+
+def wl_gaussian(n, dev):
+    from synth import workloads as wl
+    return wl.gaussian_torch((n,), dev, "bench", "extend")
+
 
 def run_ours(args, w):
     import numpy as np
@@ -338,13 +402,18 @@ def run_ours(args, w):
     O = wl.planted_O_torch(w, dev, out_dtype=dt, ld=ld, master=master)
     V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
     s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine,
-             history=args.history > 0, apply_mode=args.apply, sigma_floor=resolve_sigma_floor(args, w))
-    step = Stepper(s, w, dev, args)
+             history=args.history > 0, apply_mode=args.apply, sigma_floor=resolve_sigma_floor(args, w),
+             r_reg=args.r_reg if args.path == "adaptive" else 0.0)
+    step = AdaptiveStepper(s, w, dev, args) if args.path == "adaptive" else Stepper(s, w, dev, args)
     gs = step.inputs(max(1, args.steps))
     torch.cuda.synchronize()
     engine_name = "tcgen05" if (args.dtype == "bf16" and s.handle and args.engine != "simt"
                                 and _uses_tc(s)) else "simt"
-    V, _ = s.init_subspace(O, V0)
+    if args.path == "adaptive":
+        step.start(O, V0)
+        V = V0
+    else:
+        V, _ = s.init_subspace(O, V0)
     s.check("init_subspace")
     delta = torch.empty(w.M, device=dev)
     sigma = torch.empty(w.r, device=dev, dtype=torch.float64)
@@ -367,7 +436,7 @@ def run_ours(args, w):
     e0.record(stream)
     for t in range(args.steps):
         step(O, gs[t], V, delta, sigma, Vb)
-        launches += s.last_launch_count()
+        launches += s.last_launch_count() + step.extra_launches()
         V, Vb = Vb, V
     e1.record(stream)
     torch.cuda.synchronize()
@@ -483,6 +552,10 @@ def run_ours(args, w):
         "bf16_vs_fp32": compare,
         "cpu_baseline": cpu,
     }
+    if args.path == "adaptive":
+        line["adaptive_rank"] = {"r_max_per_step": [h[0] for h in step.history],
+                                 "r_used_per_step": [h[1] for h in step.history],
+                                 "timed_steps_r_max": step.history[-args.steps:][0][0] if args.steps else None}
     print(json.dumps(line), flush=True)
 
 
@@ -800,9 +873,13 @@ def main():
     ap.add_argument("--history", type=float, default=0.0,
                     help="history-averaging weight w in [0, 1) (Section 4.1): run wssr_step_averaged "
                          "with sigma and Lbar carried from step to step")
-    ap.add_argument("--path", default="step", choices=["step", "local-energy", "rssr"],
+    ap.add_argument("--path", default="step", choices=["step", "local-energy", "rssr", "adaptive"],
                     help="what one timed step runs: the WSSR step on a given gradient, the step with "
-                         "the gradient formed from local energies, or the randomized sketching SVD")
+                         "the gradient formed from local energies, the randomized sketching SVD, or the "
+                         "step under adaptive rank control (Algorithm 2; r_cap = the workload's r)")
+    ap.add_argument("--rank0", type=int, default=64, help="--path adaptive: initial maximum rank")
+    ap.add_argument("--r-reg", type=float, default=1e-5, help="--path adaptive: truncation ratio of Eq. (ruler)")
+    ap.add_argument("--rank-eps", type=float, default=0.5, help="--path adaptive: rank expansion factor")
     ap.add_argument("--rssr-q", type=int, default=2, help="power iterations of --path rssr")
     ap.add_argument("--apply", default="damped", choices=["damped", "cutoff", "pinv"],
                     help="regulariser of the apply (damped, the paper's cutoff, truncated pseudo-inverse)")

@@ -326,8 +326,8 @@ wssr_status wssr_mlp_pad(wssr_mlp_handle h, const float* src, int64_t cols, floa
 wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, float* dst,
                            wssr_stream_t stream);
 
-/* ---- Adaptive rank (Section 4.3, Eq. (ruler) and Algorithm 3) ----
- * wssr_create's r is the capacity r_cap; the working rank (Algorithm 3's
+/* ---- Adaptive rank (Section 4.3, Eq. (ruler) and Algorithm 2) ----
+ * wssr_create's r is the capacity r_cap; the working rank (Algorithm 2's
  * r_max, the number of columns every following call reads and writes) starts
  * at r_cap and is changed between calls. */
 
@@ -341,14 +341,14 @@ int32_t wssr_get_rank(wssr_handle h);
 /* From the r = working-rank Ritz values `sigma` (device, descending, as written
  * by the last step on `stream`): r_sel = max{i <= r : r_reg <= sigma_i^2 / sigma_1^2}
  * (Eq. (ruler); 0 when sigma_1 = 0), and r_next = the next step's maximum rank by
- * Algorithm 3's test: (1 + eps) r rounded up to a multiple of 8 and capped at
+ * Algorithm 2's test: (1 + eps) r rounded up to a multiple of 8 and capped at
  * r_cap when sigma_r^2 > r_reg sigma_1^2, else r. Synchronises `stream` (the
  * decision shapes the next step's launches). r_sel may be NULL. r_reg in [0, 1],
  * eps > 0, else INVALID_ARG. */
 wssr_status wssr_rank_next(wssr_handle h, const double* sigma, double r_reg, double eps, int32_t* r_sel,
                            int32_t* r_next, wssr_stream_t stream);
 
-/* Warm start at a larger maximum rank (Algorithm 3 leaves it open; reading:
+/* Warm start at a larger maximum rank (Algorithm 2 leaves it open; reading:
  * the previous basis followed by fresh seeded Gaussian columns, which the next
  * step's subspace iteration orthonormalises): V_out (M x r_new, row-major) =
  * [V_prev (M x r_prev) | G (M x (r_new - r_prev))]. Device pointers; V_out may

@@ -26,7 +26,7 @@ function following the passage it cites:
 * the low-rank-plus-damping apply of Eq. (updated_sr_1) (Section 4.1):
   damped reading delta = [V diag(1/(sigma^2+lam)) V^T + lam^-1 (I - V V^T)] g,
   and the paper's own cutoff reading (S^dagger + sigma_floor^-1 S^perp) g;
-* adaptive rank selection (Section 4.3, Eq. (ruler) and Algorithm 3): the
+* adaptive rank selection (Section 4.3, Eq. (ruler) and Algorithm 2): the
   rank r of the apply is the size of the ratio set I_reg within the r_max
   computed singular values, and r_max grows by (1 + eps) after a step whose
   r_max-th singular value still passes the ratio test.
@@ -266,7 +266,7 @@ def rank_select(sigma: np.ndarray, r_reg: float) -> int:
 
 
 def rank_expand(sigma: np.ndarray, r_max: int, r_reg: float, eps: float, r_cap: int, align: int = 8) -> int:
-    """Algorithm 3's expansion test after the SVD of a step at maximum rank
+    """Algorithm 2's expansion test after the SVD of a step at maximum rank
     r_max: when s_{r_max} > r_reg s_max (S-eigenvalues s = sigma^2) the next
     step uses (1 + eps) r_max. Readings: (1 + eps) r_max is rounded up to a
     multiple of `align` (the rank granularity of the kernels) and capped at
@@ -281,7 +281,7 @@ def rank_expand(sigma: np.ndarray, r_max: int, r_reg: float, eps: float, r_cap: 
 
 
 def extend_basis(V_prev: np.ndarray, G: np.ndarray) -> np.ndarray:
-    """Warm start of a step whose maximum rank grew (Algorithm 3 leaves this
+    """Warm start of a step whose maximum rank grew (Algorithm 2 leaves this
     open; reading): the previous basis followed by the columns of a seeded
     Gaussian block G; the subspace iteration orthonormalises the whole block."""
     return np.concatenate([np.asarray(V_prev, dtype=np.float64), np.asarray(G, dtype=np.float64)], axis=1)
@@ -289,7 +289,7 @@ def extend_basis(V_prev: np.ndarray, G: np.ndarray) -> np.ndarray:
 
 def wssr_step_adaptive(O: np.ndarray, g: np.ndarray, V_prev: np.ndarray, lam: float, m: int, r_reg: float,
                        eps: float, r_cap: int, mode: str = "damped", sigma_floor: float | None = None):
-    """One step of Algorithm 3 at maximum rank r_max = V_prev.shape[1]: the
+    """One step of Algorithm 2 at maximum rank r_max = V_prev.shape[1]: the
     SSI-SVD of rank r_max (Algorithm 1 + Rayleigh-Ritz), the rank r of
     Eq. (ruler), the apply of Eq. (updated_sr_1) on the leading r singular
     triplets, and the maximum rank of the next step.

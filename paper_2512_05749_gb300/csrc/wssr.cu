@@ -875,7 +875,7 @@ wssr_status wssr_rank_next(wssr_handle h, const double* sigma, double r_reg, dou
   if (s1 > 0.0)
     for (int i = 0; i < r; ++i)
       if (r_reg <= sg[i] * sg[i] / s1) sel = i + 1;
-  // Algorithm 3's expansion test: r_max <- (1 + eps) r_max, rounded up to a multiple of 8, capped
+  // Algorithm 2's expansion test: r_max <- (1 + eps) r_max, rounded up to a multiple of 8, capped
   int nxt = r;
   if (s1 > 0.0 && sg[r - 1] * sg[r - 1] > r_reg * s1) {
     int64_t grown = (int64_t)ceil((1.0 + eps) * (double)r);

@@ -286,7 +286,7 @@ def wssr_get_rank(h: int) -> int:
 
 
 def wssr_rank_next(h: int, sigma, r_reg: float, eps: float, stream=None):
-    """(r_sel, r_next): the rank of Eq. (ruler) and Algorithm 3's next maximum rank."""
+    """(r_sel, r_next): the rank of Eq. (ruler) and Algorithm 2's next maximum rank."""
     sel, nxt = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(load().wssr_rank_next(h, _ptr(sigma), r_reg, eps, ctypes.byref(sel), ctypes.byref(nxt),
                                  _stream(stream)), "wssr_rank_next")
@@ -494,13 +494,13 @@ class WSSR:
         return V, sigma
 
     def set_rank(self, r: int):
-        """Working rank of the following calls (Algorithm 3's r_max; 8 <= r <= r_cap, multiple of 8)."""
+        """Working rank of the following calls (Algorithm 2's r_max; 8 <= r <= r_cap, multiple of 8)."""
         wssr_set_rank(self.handle, r)
         self.r = int(r)
 
     def rank_next(self, sigma, eps: float, stream=None):
         """(r_sel, r_next) after a step: the rank of Eq. (ruler) the apply used, and
-        the next step's maximum rank by Algorithm 3's expansion test (synchronises)."""
+        the next step's maximum rank by Algorithm 2's expansion test (synchronises)."""
         return wssr_rank_next(self.handle, sigma, self.r_reg, eps, stream)
 
     def init_subspace(self, O, V_rand, stream=None):

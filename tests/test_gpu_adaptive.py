@@ -1,5 +1,5 @@
 """GPU parity of adaptive rank selection (Section 4.3, Eq. (ruler) and
-Algorithm 3): the working rank, the truncated apply, the expansion decision and
+Algorithm 2): the working rank, the truncated apply, the expansion decision and
 the extended warm start, against the oracle's wssr_step_adaptive.
 
 The planted spectrum is geometric (sigma_k = 0.93^k), so consecutive

@@ -1,5 +1,5 @@
 """Pins of the oracle's adaptive rank selection (Section 4.3, Eq. (ruler) and
-the expansion test of Algorithm 3) to closed forms, hand-derived sequences and
+the expansion test of Algorithm 2) to closed forms, hand-derived sequences and
 dense solves through LAPACK's symmetric eigensolver."""
 import math
 
