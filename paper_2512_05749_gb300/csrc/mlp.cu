@@ -32,7 +32,8 @@ struct wssr_mlp_ctx {
   int64_t del_cols = 0;
   float* acts = nullptr;   // N_max x act_cols: a_0 (features), a_1, ..., a_{L-1}, f
   float* dels = nullptr;   // N_max x del_cols: delta_1 .. delta_{L-1}
-  float* wtmp = nullptr;   // N_max x max width: weighted adjoints for the VJP
+  float* wpart = nullptr;  // split partials of the weighted-gradient GEMMs
+  int num_sms = 0;
   int* meta = nullptr;     // per-layer metadata of the Jacobian writer (8 ints per layer)
 
   // ---- matrix-free operator: padded parameter space ----
@@ -93,86 +94,171 @@ __global__ void k_features(const float* __restrict__ x, int64_t N, int ne, float
 }
 
 // ---------------------------------------------------------------------------
-// Tiled SIMT GEMM, C (Mr x Nc) = op(A) op(B), 64 x 64 tiles, 4 x 4 per thread.
-//   TA: A stored K x Mr (use A^T);  TB: B stored Nc x K (use B^T).
-// Epilogues: 0 store; 1 bias + tanh; 2 bias (linear); 3 multiply by (1 - E^2)
-// (E = the activation the adjoint belongs to).
+// Tiled SIMT GEMM of the network passes, C (Mr x Nc) = op(A) op(B) in FP32:
+// 128 x 128 tiles, 16-deep K steps double-buffered in shared memory (the next
+// tile is fetched into registers while the current one is multiplied), 256
+// threads with 8 x 8 outputs each as a 2 x 2 arrangement of 4 x 4 blocks
+// (rows ty*4 and 64 + ty*4, columns tx*4 and 64 + tx*4), so every shared-memory
+// read is a conflict-free float4.
+//   G_FWD_TANH / G_FWD_LIN: C = A B^T (A: N x K activations, B: the weight
+//     matrix, Nc x K), epilogue tanh(. + bias) or . + bias;
+//   G_BWD: C = A B (A: N x K adjoints, B: K x Nc weights), epilogue * (1 - E^2);
+//   G_WGRAD: C = (w * A)^T [B | 1] over the K = samples of this split
+//     (A: K x Mr adjoints or all ones when A is null, B: K x (Nc - 1)
+//     activations, the last column of ones gives the bias gradient); each
+//     split (blockIdx.z) writes its own Mr x Nc partial, summed in fixed order.
 // ---------------------------------------------------------------------------
-constexpr int GT = 64, GKK = 16;
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16;
+enum { G_FWD_TANH = 1, G_FWD_LIN = 2, G_BWD = 3, G_WGRAD = 4 };
 
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(256) k_gemm(const float* __restrict__ A, int64_t lda,
-                                              const float* __restrict__ B, int64_t ldb,
-                                              float* __restrict__ C, int64_t ldc, int64_t Mr, int Nc,
-                                              int K, const float* __restrict__ bias,
-                                              const float* __restrict__ E, int64_t lde) {
-  __shared__ __align__(16) float As[GKK][GT + 4];
-  __shared__ __align__(16) float Bs[GKK][GT + 4];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = (int64_t)blockIdx.x * GT;
-  const int n0 = blockIdx.y * GT;
-  float acc[4][4];
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sgemm(const float* __restrict__ A, int64_t lda,
+                                               const float* __restrict__ B, int64_t ldb,
+                                               float* __restrict__ C, int64_t ldc, int64_t Mr, int Nc, int K,
+                                               int kchunk, const float* __restrict__ aux,
+                                               const float* __restrict__ E, int64_t lde) {
+  __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
+  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * SG_BM;
+  const int n0 = blockIdx.y * SG_BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  float ra[8], rb[8];
+  // A tile as As[k][m]; B tile as Bs[k][n]. Index maps keep consecutive
+  // threads on consecutive addresses of the stored layout.
+  auto fetch = [&](int k0) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GKK) {
-    for (int e = tid; e < GT * GKK; e += 256) {
-      int row, kk;
-      if (TA) { kk = e / GT; row = e % GT; } else { row = e / GKK; kk = e % GKK; }
-      const int64_t m = m0 + row;
-      const int k = k0 + kk;
-      float v = 0.f;
-      if (m < Mr && k < K) v = TA ? A[(int64_t)k * lda + m] : A[m * lda + k];
-      As[kk][row] = v;
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      float va = 0.f, vb = 0.f;
+      if (MODE == G_WGRAD) {
+        const int kk = e >> 7, mm = e & 127;  // A stored K x Mr
+        const int k = k0 + kk;
+        const int64_t m = m0 + mm;
+        if (k < kend && m < Mr) va = aux[k] * (A ? A[(int64_t)k * lda + m] : 1.f);
+        const int nn = e & 127, n = n0 + nn;  // B stored K x (Nc - 1), last column = 1
+        if (k < kend && n < Nc) vb = n == Nc - 1 ? 1.f : B[(int64_t)k * ldb + n];
+      } else {
+        const int kk = e & 15, mm = e >> 4;  // A stored Mr x K
+        const int k = k0 + kk;
+        const int64_t m = m0 + mm;
+        if (k < kend && m < Mr) va = A[m * lda + k];
+        if (MODE == G_BWD) {
+          const int kb = e >> 7, nn = e & 127;  // B stored K x Nc
+          const int kq = k0 + kb, n = n0 + nn;
+          if (kq < kend && n < Nc) vb = B[(int64_t)kq * ldb + n];
+        } else {
+          const int n = n0 + mm;  // B stored Nc x K
+          if (k < kend && n < Nc) vb = B[(int64_t)n * ldb + k];
+        }
+      }
+      ra[u] = va;
+      rb[u] = vb;
     }
-    for (int e = tid; e < GT * GKK; e += 256) {
-      int col, kk;
-      if (TB) { col = e / GKK; kk = e % GKK; } else { kk = e / GT; col = e % GT; }
-      const int n = n0 + col;
-      const int k = k0 + kk;
-      float v = 0.f;
-      if (n < Nc && k < K) v = TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n];
-      Bs[kk][col] = v;
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      if (MODE == G_WGRAD) {
+        As[buf][e >> 7][e & 127] = ra[u];
+        Bs[buf][e >> 7][e & 127] = rb[u];
+      } else {
+        As[buf][e & 15][e >> 4] = ra[u];
+        if (MODE == G_BWD) Bs[buf][e >> 7][e & 127] = rb[u];
+        else Bs[buf][e & 15][e >> 4] = rb[u];
+      }
     }
-    __syncthreads();
+  };
+  float acc[8][8];
 #pragma unroll
-    for (int kk = 0; kk < GKK; ++kk) {
-      const float4 u = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float ua[4] = {u.x, u.y, u.z, u.w}, va[4] = {v.x, v.y, v.z, v.w};
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ua[a], va[b], acc[a][b]);
-    }
-    __syncthreads();
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
   }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += SG_BK) {
+    const bool more = k0 + SG_BK < kend;
+    if (more) fetch(k0 + SG_BK);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t m = m0 + ty * 4 + a;
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* Cz = MODE == G_WGRAD ? C + (int64_t)blockIdx.z * Mr * ldc : C;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t m = m0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + a - 4);
     if (m >= Mr) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int n = n0 + tx * 4 + b;
+    for (int b = 0; b < 8; ++b) {
+      const int n = n0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
       if (n >= Nc) continue;
       float v = acc[a][b];
-      if (EPI == 1) v = tanhf(v + bias[n]);
-      if (EPI == 2) v = v + bias[n];
-      if (EPI == 3) {
+      if (MODE == G_FWD_TANH) v = tanhf(v + aux[n]);
+      if (MODE == G_FWD_LIN) v = v + aux[n];
+      if (MODE == G_BWD) {
         const float e = E[m * lde + n];
         v *= (1.f - e * e);
       }
-      C[m * ldc + n] = v;
+      Cz[m * ldc + n] = v;
     }
   }
 }
 
-template <bool TA, bool TB, int EPI>
-void gemm(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int64_t Mr,
-          int Nc, int K, const float* bias, const float* E, int64_t lde, cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(Mr, GT), (unsigned)ceil_div(Nc, GT));
-  k_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, Nc, K, bias, E, lde);
+// Returns the number of K splits launched (<= splits).
+template <int MODE>
+int sgemm(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int64_t Mr, int Nc,
+          int K, const float* aux, const float* E, int64_t lde, cudaStream_t st, int splits = 1) {
+  const int kchunk = (int)(ceil_div(ceil_div(K, splits), SG_BK) * SG_BK);
+  dim3 grid((unsigned)ceil_div(Mr, SG_BM), (unsigned)ceil_div(Nc, SG_BN), (unsigned)ceil_div(K, kchunk));
+  k_sgemm<MODE><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, Nc, K, kchunk, aux, E, lde);
+  return (int)grid.z;
+}
+
+// Split count of the weighted-gradient GEMM of a dout x (dp + 1) output over K
+// samples: about two CTAs per SM (wgrad_max_splits), at least 256 samples per split.
+int64_t wgrad_max_splits(int dout, int dp, int num_sms) {
+  const int64_t tiles = ceil_div(dout, SG_BM) * ceil_div(dp + 1, SG_BN);
+  const int64_t s = ceil_div(2LL * num_sms, tiles);
+  return s < 1 ? 1 : s;
+}
+int wgrad_splits(int dout, int dp, int64_t K, int num_sms) {
+  int64_t s = wgrad_max_splits(dout, dp, num_sms);
+  const int64_t kmax = ceil_div(K, 256);
+  if (s > kmax) s = kmax;
+  return (int)(s < 1 ? 1 : s);
+}
+
+// out[W block] and out[bias block] from the split partials of one layer
+// (each partial dout x (dp + 1), the last column the bias gradient).
+__global__ void k_wgrad_reduce(const float* __restrict__ P, int nsplit, int dout, int dp,
+                               float* __restrict__ gw, float* __restrict__ gb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cols = dp + 1, tot = (int64_t)dout * cols;
+  if (e >= tot) return;
+  float v = 0.f;
+  for (int z = 0; z < nsplit; ++z) v += P[(int64_t)z * tot + e];
+  const int i = (int)(e / cols), j = (int)(e % cols);
+  if (j < dp) gw[(int64_t)i * dp + j] = v;
+  else gb[i] = v;
 }
 
 // delta_{L-1}[n][i] = W_L[0][i] (1 - a_{L-1}[n][i]^2) for the scalar output layer
@@ -215,26 +301,6 @@ __global__ void __launch_bounds__(256) k_jacobian_rows(const float* __restrict__
     row[off_w + e] = from_f32<T>(d_s[i] * a_s[j]);
   }
   for (int i = threadIdx.x; i < dout; i += blockDim.x) row[off_b + i] = from_f32<T>(d_s[i]);
-}
-
-// w-scaled adjoints: out[n][i] = w[n] * del[n][i] (delta_L = 1 when del == nullptr)
-__global__ void k_scale_rows(const float* __restrict__ del, int64_t ldd, const float* __restrict__ w,
-                             int64_t N, int d, float* __restrict__ out, int64_t ldo) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * d) return;
-  const int64_t n = e / d;
-  const int i = (int)(e % d);
-  out[n * ldo + i] = w[n] * (del ? del[n * ldd + i] : 1.f);
-}
-
-// db[i] = sum_n s[n][i] (column sums, FP64 accumulation in fixed order)
-__global__ void k_colsum_rows(const float* __restrict__ s, int64_t lds, int64_t N, int d,
-                              float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d) return;
-  double acc = 0.0;
-  for (int64_t n = 0; n < N; ++n) acc += (double)s[n * lds + i];
-  out[i] = (float)acc;
 }
 
 // S[n][col] for the activations/adjoints of one sample, bf16, zero padded.
@@ -333,9 +399,9 @@ wssr_status run_forward_backward(wssr_mlp_ctx* h, const float* theta, const floa
     const float* Wl = theta + h->off_w[l - 1];
     const float* bl = theta + h->off_b[l - 1];
     if (l < L)
-      gemm<false, true, 1>(Al, ac, Wl, w[l - 1], Cl, ac, N, w[l], w[l - 1], bl, nullptr, 0, st);
+      sgemm<G_FWD_TANH>(Al, ac, Wl, w[l - 1], Cl, ac, N, w[l], w[l - 1], bl, nullptr, 0, st);
     else
-      gemm<false, true, 2>(Al, ac, Wl, w[l - 1], Cl, ac, N, w[l], w[l - 1], bl, nullptr, 0, st);
+      sgemm<G_FWD_LIN>(Al, ac, Wl, w[l - 1], Cl, ac, N, w[l], w[l - 1], bl, nullptr, 0, st);
   }
   if (want_delta && L > 1) {
     // delta_{L-1} = W_L^T (1 - a_{L-1}^2) (scalar output), then down to delta_1
@@ -344,8 +410,8 @@ wssr_status run_forward_backward(wssr_mlp_ctx* h, const float* theta, const floa
         theta + h->off_w[L - 1], h->acts + h->act_off[L - 1], ac, N, dlast, h->dels + h->del_off[L - 1], dc);
     for (int l = L - 2; l >= 1; --l) {
       // delta_l = (delta_{l+1} W_{l+1}) * (1 - a_l^2)
-      gemm<false, false, 3>(h->dels + h->del_off[l + 1], dc, theta + h->off_w[l], w[l], h->dels + h->del_off[l],
-                            dc, N, w[l], w[l + 1], nullptr, h->acts + h->act_off[l], ac, st);
+      sgemm<G_BWD>(h->dels + h->del_off[l + 1], dc, theta + h->off_w[l], w[l], h->dels + h->del_off[l], dc, N,
+                   w[l], w[l + 1], nullptr, h->acts + h->act_off[l], ac, st);
     }
   }
   return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
@@ -360,10 +426,11 @@ wssr_status weighted_grad(wssr_mlp_ctx* h, const float* w, int64_t N, float* gra
   for (int l = 1; l <= h->L; ++l) {
     const int dout = wd[l], dp = wd[l - 1];
     const float* del = l < h->L ? h->dels + h->del_off[l] : nullptr;
-    k_scale_rows<<<(unsigned)ceil_div(N * dout, 256), 256, 0, st>>>(del, h->del_cols, w, N, dout, h->wtmp, dout);
-    gemm<true, false, 0>(h->wtmp, dout, h->acts + h->act_off[l - 1], h->act_cols, grad + h->off_w[l - 1], dp,
-                         dout, dp, (int)N, nullptr, nullptr, 0, st);
-    k_colsum_rows<<<(unsigned)ceil_div(dout, 256), 256, 0, st>>>(h->wtmp, dout, N, dout, grad + h->off_b[l - 1]);
+    const int used = sgemm<G_WGRAD>(del, h->del_cols, h->acts + h->act_off[l - 1], h->act_cols, h->wpart, dp + 1,
+                                    dout, dp + 1, (int)N, w, nullptr, 0, st, wgrad_splits(dout, dp, N, h->num_sms));
+    const int64_t tot = (int64_t)dout * (dp + 1);
+    k_wgrad_reduce<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(h->wpart, used, dout, dp, grad + h->off_w[l - 1],
+                                                                  grad + h->off_b[l - 1]);
   }
   return cudaGetLastError() == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
@@ -484,7 +551,7 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
   h->desc = *d;
   h->L = d->nlayers;
   h->N_max = N_max;
-  int64_t off = 0, ao = 0, dof = 0, wmax = 1;
+  int64_t off = 0, ao = 0, dof = 0;
   for (int l = 1; l <= h->L; ++l) {
     h->off_w[l - 1] = off;
     off += (int64_t)d->widths[l] * d->widths[l - 1];
@@ -495,7 +562,6 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
   for (int l = 0; l <= h->L; ++l) {
     h->act_off[l] = ao;
     ao += d->widths[l];
-    if (d->widths[l] > wmax) wmax = d->widths[l];
   }
   h->act_cols = ao;
   for (int l = 1; l < h->L; ++l) {
@@ -505,7 +571,16 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
   h->del_cols = dof > 0 ? dof : 1;
   cudaError_t e = cudaMalloc(&h->acts, (size_t)N_max * h->act_cols * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->dels, (size_t)N_max * h->del_cols * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&h->wtmp, (size_t)N_max * wmax * sizeof(float));
+  {
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t wp = 1;
+    for (int l = 1; l <= h->L; ++l)
+      wp = std::max<int64_t>(wp, wgrad_max_splits(d->widths[l], d->widths[l - 1], h->num_sms) * d->widths[l] *
+                                     (d->widths[l - 1] + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->wpart, (size_t)wp * sizeof(float));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&h->meta, WSSR_MLP_MAX_LAYERS * 8 * sizeof(int));
   // ---- padded parameter space, source and scale matrices, schedules ----
   mlp_layout(h);
@@ -528,7 +603,7 @@ wssr_status wssr_mlp_create(const wssr_mlp_desc* d, int64_t N_max, wssr_mlp_hand
     cudaGetLastError();
     if (h->acts) cudaFree(h->acts);
     if (h->dels) cudaFree(h->dels);
-    if (h->wtmp) cudaFree(h->wtmp);
+    if (h->wpart) cudaFree(h->wpart);
     if (h->meta) cudaFree(h->meta);
     mlp_free_mf(h);
     delete h;
@@ -543,7 +618,7 @@ void wssr_mlp_destroy(wssr_mlp_handle h) {
   cudaDeviceSynchronize();
   cudaFree(h->acts);
   cudaFree(h->dels);
-  cudaFree(h->wtmp);
+  cudaFree(h->wpart);
   cudaFree(h->meta);
   mlp_free_mf(h);
   delete h;

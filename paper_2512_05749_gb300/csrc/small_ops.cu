@@ -66,13 +66,32 @@ __global__ void __launch_bounds__(256) k_reduce_splits(const float* __restrict__
   }
 }
 
-__global__ void k_colsum_finalize(const double* __restrict__ part, int64_t nblocks, int r,
-                                  double scale, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= r) return;
-  double s = 0.0;
-  for (int64_t b = 0; b < nblocks; ++b) s += part[b * r + j];
-  out[j] = s * scale;
+// out[j] = scale * sum_b part[b][j]: CTA = 32 columns (lane = column), its 32
+// warps stride the partial rows with 4 independent accumulators each, then
+// warp sums are combined in warp order (a fixed summation order).
+__global__ void __launch_bounds__(1024) k_colsum_finalize(const double* __restrict__ part, int64_t nblocks, int r,
+                                                          double scale, double* __restrict__ out) {
+  __shared__ double red[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (j < r) {
+    int64_t b = warp;
+    for (; b + 96 < nblocks; b += 128) {
+      s0 += part[b * r + j];
+      s1 += part[(b + 32) * r + j];
+      s2 += part[(b + 64) * r + j];
+      s3 += part[(b + 96) * r + j];
+    }
+    for (; b < nblocks; b += 32) s0 += part[b * r + j];
+  }
+  red[warp][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (warp == 0 && j < r) {
+    double t = 0.0;
+    for (int w = 0; w < 32; ++w) t += red[w][lane];
+    out[j] = t * scale;
+  }
 }
 
 __global__ void k_subtract_mean(float* __restrict__ Y, int64_t N, int r,
@@ -93,12 +112,12 @@ void launch_reduce_splits(const float* Yp, int nsplit, int64_t N, int r, float* 
 
 void launch_colsum_finalize(const double* part, int64_t nblocks, int r, double* out,
                             cudaStream_t st) {
-  k_colsum_finalize<<<1, 256, 0, st>>>(part, nblocks, r, 1.0, out);
+  k_colsum_finalize<<<(unsigned)ceil_div(r, 32), 1024, 0, st>>>(part, nblocks, r, 1.0, out);
 }
 
 void launch_centre(float* Y, int64_t N, int r, const double* csum_part, int64_t nblocks,
                    double* mean_out, cudaStream_t st) {
-  k_colsum_finalize<<<1, 256, 0, st>>>(csum_part, nblocks, r, 1.0 / (double)N, mean_out);
+  k_colsum_finalize<<<(unsigned)ceil_div(r, 32), 1024, 0, st>>>(csum_part, nblocks, r, 1.0 / (double)N, mean_out);
   const int64_t tot = N * r;
   k_subtract_mean<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Y, N, r, mean_out);
 }
@@ -1207,7 +1226,7 @@ void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, 
   const int64_t chunk = ceil_div(M, nb);
   const int nbe = (int)ceil_div(M, chunk);
   k_dot_part<<<nbe, 256, 0, st>>>(V, g, M, r, chunk, part);
-  k_colsum_finalize<<<1, 256, 0, st>>>(part, nbe, r, 1.0, c);
+  k_colsum_finalize<<<(unsigned)ceil_div(r, 32), 1024, 0, st>>>(part, nbe, r, 1.0, c);
 }
 
 void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t st) {

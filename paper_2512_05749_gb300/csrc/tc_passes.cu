@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Each CTA covers MT x 128 parameters: its stage holds 2 MT 64-parameter O
 // boxes (8 KB apart) and one operand tile; accumulator a uses boxes 2a, 2a+1.
-template <bool WITH_MU, int MT>
+// MU: 0 reads mu; 1 sums the column means from the O tiles; 2 also sums the
+// weighted columns O^T w (the fused gradient) on the same tiles.
+template <int MU, int MT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_passB(const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmY,
                int64_t N, int64_t M, int r, int nmma, int tmem_cols, int stages,
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], WITH_MU ? 2 : 1);
+      mbar_init(&ctl->empty[s], MU ? 2 : 1);
     }
     mbar_init(&ctl->accum, 1);
     ctl->abort = 0;
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     const int et = threadIdx.x - 64;  // 0..127
     for (int j = et; j < r; j += 128) ctl->ysum[j] = (float)ysum[j];
-    if (WITH_MU) {
+    if (MU) {
       // Column sums of the O tiles: thread = 8 parameters (16 B chunk `c` of
       // box `box`) over SG-sample runs of every stage.
       constexpr int PG = 16 * MT;          // parameter groups of 8
@@ -301,15 +303,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = sg * RPS + j;
             const uint4 v = *reinterpret_cast<const uint4*>(sa + row * 128 + ((c ^ (row & 7)) << 4));
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            const int64_t n = (int64_t)i * BK + row;
-            const float wn = (wgt && n < N) ? __ldg(wgt + n) : 0.f;
+            float wn = 0.f;
+            if (MU == 2) {
+              const int64_t n = (int64_t)i * BK + row;
+              wn = n < N ? __ldg(wgt + n) : 0.f;
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float lo = __uint_as_float(w[e] << 16), hi = __uint_as_float(w[e] & 0xFFFF0000u);
               acc[2 * e] += lo;
               acc[2 * e + 1] += hi;
-              accw[2 * e] = fmaf(lo, wn, accw[2 * e]);
-              accw[2 * e + 1] = fmaf(hi, wn, accw[2 * e + 1]);
+              if (MU == 2) {
+                accw[2 * e] = fmaf(lo, wn, accw[2 * e]);
+                accw[2 * e + 1] = fmaf(hi, wn, accw[2 * e + 1]);
+              }
             }
           }
         }
@@ -321,8 +328,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (et == 0) mbar_arrive(&ctl->empty[s]);
         if ((i & 15) == 15) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            acc64[e] += (double)acc[e], acc[e] = 0.f, accw64[e] += (double)accw[e], accw[e] = 0.f;
+          for (int e = 0; e < 8; ++e) {
+            acc64[e] += (double)acc[e], acc[e] = 0.f;
+            if (MU == 2) accw64[e] += (double)accw[e], accw[e] = 0.f;
+          }
         }
       }
       double* red = &ctl->red[0][0];  // [NSG][PG * 8]
@@ -336,7 +345,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         ctl->mu[p] = mu;
         if (m0 + p < M) mu_io[m0 + p] = mu;
       }
-      if (g_out) {
+      if (MU == 2) {
         // (O_c^T w)[p] = sum_n O[n, p] w[n] - mu_p sum_n w[n]; the weights sum to zero
         // up to their rounding, which the second term removes
         epi_bar();
@@ -359,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int a = 0; a < MT; ++a) {
       const int row = a * BM + q * 32 + lane;
       const int64_t m = m0 + row;
-      const float mu = WITH_MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
+      const float mu = MU ? ctl->mu[row] : (m < M ? mu_io[m] : 0.f);
       for (int c = 0; c < nmma; c += 16) {
         float v[16];
         tmem_ld16(tmem + (uint32_t)(a * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
@@ -738,19 +747,22 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
   const size_t smem = 1024 + stages * stage + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_passB<true, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_tc_passB<false, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<2, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<1, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<0, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
   dim3 grid((unsigned)ceil_div(M, (int64_t)BM * MT));
-  if (compute_mu)
-    k_tc_passB<true, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                      (bf16*)ZT, ldz, mu_io, Zadd, wgt, g_out, wsum,
-                                                      (uint64_t)wait_us * 1000ull, status);
+  const uint64_t lim = (uint64_t)wait_us * 1000ull;
+  if (compute_mu && wgt && g_out && wsum)
+    k_tc_passB<2, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
+                                                   ldz, mu_io, Zadd, wgt, g_out, wsum, lim, status);
+  else if (compute_mu)
+    k_tc_passB<1, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
+                                                   ldz, mu_io, Zadd, nullptr, nullptr, nullptr, lim, status);
   else
-    k_tc_passB<false, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,
-                                                       (bf16*)ZT, ldz, mu_io, Zadd, nullptr, nullptr, nullptr,
-                                                       (uint64_t)wait_us * 1000ull, status);
+    k_tc_passB<0, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
+                                                   ldz, mu_io, Zadd, nullptr, nullptr, nullptr, lim, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

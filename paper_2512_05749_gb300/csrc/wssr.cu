@@ -675,7 +675,7 @@ wssr_status wssr_step_local_energy(wssr_handle h, const wssr_operator* op, const
     if (op->kind == WSSR_OP_MLP) {
       // the weighted backward pass of the network from the activations and adjoints just recomputed
       if ((s = mlp_weighted_grad_padded(op->mlp, h->wE, h->N, g_out, st)) != WSSR_OK) return s;
-      h->launches += 3 * mlp_layers(op->mlp) + 1;  // per layer: scale, GEMM, column sums; then the padding
+      h->launches += 2 * mlp_layers(op->mlp) + 1;  // per layer: split-K GEMM, reduce; then the padding
     } else if (!h->use_tc) {
       launch_gemv_t(op->O, is_bf16(h) ? 1 : 0, op->ld, h->N, h->M, h->wE, h->wE_sum, g_out, st);
       h->launches++;
