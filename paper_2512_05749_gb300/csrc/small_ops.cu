@@ -823,12 +823,6 @@ void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf
 // A <- J^T A J, W <- W J; t = tan(theta) zeroes a_pq (smaller root).
 // ---------------------------------------------------------------------------
 namespace {
-__device__ __forceinline__ void rr_pair(int k, int i, int r, int& p, int& q) {
-  const int n1 = r - 1;
-  p = (i == 0) ? 0 : ((i + k - 1) % n1) + 1;
-  q = ((r - 2 - i + k) % n1) + 1;
-}
-
 // Rotation zeroing a_pq of [[app, apq], [apq, aqq]]: rotate when the pair is
 // not yet orthogonal relative to its diagonal (tol) and a_pq is above the
 // FP32 rounding noise that rotations of the larger element leave behind (a
@@ -846,34 +840,35 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
 }
 
 // One CTA of 1024 threads; A = packed upper triangle in shared memory
-// (A[rb[i] + j], j >= i, rb[i] = i r - i (i + 1) / 2). Per round: the r/2
-// rotations go into a table {c, s, p, q} + {rb[p], rb[q]} (+ t for the
-// diagonal blocks); then every warp updates the 2 x 2 blocks (i1, i2 >= i1)
-// of its (at most 4) block rows i1, enumerated as one flat index range so
-// that lanes stay busy across row ends; blocks whose two pairs are both idle
-// are skipped.
+// (A[rb(i) + j], j >= i, rb(i) = i r - i (i + 1) / 2). Per round: the r/2
+// rotation threads (one per pair, following their ring positions from round
+// to round) put {c, s, p, q} + {rb(p), rb(q)} (+ t for the diagonal blocks)
+// into a table, __syncthreads_count gives every thread the number of active
+// rotations; then every warp updates the 2 x 2 blocks (i1, i2 >= i1) of its
+// (at most 4) block rows, holding row i1's table entry in registers while its
+// lanes walk i2. Blocks whose two pairs are both idle are skipped.
+__device__ __forceinline__ int packed_row(int i, int r) { return i * r - i * (i + 1) / 2; }
+
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
                                                  float2* __restrict__ rot_log, int* nsweeps_out,
                                                  float* __restrict__ evals, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);
   __shared__ float4 tab[128];  // {c, s, p, q} (p, q as int bits)
-  __shared__ int2 tabrb[128];  // {rb[p], rb[q]}
+  __shared__ int2 tabrb[128];  // {rb(p), rb(q)}
   __shared__ float tabt[128];  // t = tan(theta)
-  __shared__ int rb[256];
-  __shared__ int warp_act[4], rot_sweep, bad;
+  __shared__ int bad;
   int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * (r - 1) * (r / 2));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int h = r / 2, n1 = r - 1;
   if (tid == 0) bad = 0;
-  if (tid < r) rb[tid] = tid * r - tid * (tid + 1) / 2;
   __syncthreads();
   for (int e = tid; e < r * r; e += 1024) {
     const int i = e / r, j = e % r;
     if (i <= j) {
       const double v = H[e];
       if (!isfinite(v)) bad = 1;
-      A[rb[i] + j] = (float)v;
+      A[packed_row(i, r) + j] = (float)v;
     }
   }
   __syncthreads();
@@ -885,25 +880,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     return;
   }
   // this warp's block rows (balanced when h % 64 == 0: w, 63-w, 64+w, 127-w)
-  // and the start of each in the warp's flat block index
-  int row_i1[4], row_start[4], n_blocks = 0;
+  int row_i1[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
-    row_start[t] = n_blocks;
-    row_i1[t] = i1;
-    if (i1 < h) n_blocks += h - i1;
-    else row_start[t] = 1 << 30;
-  }
+  for (int t = 0; t < 4; ++t) row_i1[t] = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
+  // ring positions of this thread's pair in round 0 (round-robin: pair 0 keeps
+  // index 0; every other position advances by one on the ring 1..r-1 per round)
+  int pp = tid == 0 ? 0 : tid, qq = r - 1 - tid;
 
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) rot_sweep = 0;
+    bool rotated = false;
     for (int k = 0; k < n1; ++k) {
+      int act = 0;
       if (tid < h) {
-        int p, q;
-        rr_pair(k, tid, r, p, q);
-        const int rbp = rb[p], rbq = rb[q];
+        const int p = pp, q = qq;
+        const int rbp = packed_row(p, r), rbq = packed_row(q, r);
         const float app = A[rbp + p], aqq = A[rbq + q];
         const float apq = A[p < q ? rbp + q : rbq + p];
         float c, s, t;
@@ -912,63 +903,62 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
         tabrb[tid] = make_int2(rbp, rbq);
         tabt[tid] = t;
         rot_log[((int64_t)sweep * n1 + k) * h + tid] = make_float2(c, s);
-        const unsigned act = __ballot_sync(__activemask(), s != 0.f);
-        if ((tid & 31) == 0) warp_act[tid >> 5] = __popc(act);
+        act = s != 0.f;
+        if (tid != 0) pp = pp == n1 ? 1 : pp + 1;
+        qq = qq == n1 ? 1 : qq + 1;
       }
-      __syncthreads();
-      const int nact = (h > 0 ? warp_act[0] : 0) + (h > 32 ? warp_act[1] : 0) + (h > 64 ? warp_act[2] : 0) +
-                       (h > 96 ? warp_act[3] : 0);
-      if (tid == 0) {
-        round_nact[sweep * n1 + k] = nact;
-        if (nact) rot_sweep = 1;
-      }
+      const int nact = __syncthreads_count(act);
+      if (tid == 0) round_nact[sweep * n1 + k] = nact;
       if (nact) {
-        for (int e = lane; e < n_blocks; e += 32) {
-          const int j = (e >= row_start[1]) + (e >= row_start[2]) + (e >= row_start[3]);
-          const int i1 = j == 0 ? row_i1[0] : (j == 1 ? row_i1[1] : (j == 2 ? row_i1[2] : row_i1[3]));
-          const int st_j = j == 0 ? row_start[0] : (j == 1 ? row_start[1] : (j == 2 ? row_start[2] : row_start[3]));
-          const int i2 = i1 + (e - st_j);
-          const float4 t1 = tab[i1], t2 = tab[i2];
-          if (t1.y == 0.f && t2.y == 0.f) continue;
-          const int p1 = __float_as_int(t1.z), q1 = __float_as_int(t1.w);
+        rotated = true;
+#pragma unroll 1
+        for (int t = 0; t < 4; ++t) {
+          const int i1 = row_i1[t];
+          if (i1 >= h) continue;
+          const float4 t1 = tab[i1];
           const int2 rb1 = tabrb[i1];
-          if (i2 == i1) {
-            const float tt = tabt[i1];
-            const int ipq = p1 < q1 ? rb1.x + q1 : rb1.y + p1;
-            const float apq = A[ipq];
-            A[rb1.x + p1] -= tt * apq;
-            A[rb1.y + q1] += tt * apq;
-            A[ipq] = 0.f;
-          } else {
-            const int p2 = __float_as_int(t2.z), q2 = __float_as_int(t2.w);
-            const int2 rb2 = tabrb[i2];
-            const int i_pp = p1 <= p2 ? rb1.x + p2 : rb2.x + p1;
-            const int i_pq = p1 <= q2 ? rb1.x + q2 : rb2.y + p1;
-            const int i_qp = q1 <= p2 ? rb1.y + p2 : rb2.x + q1;
-            const int i_qq = q1 <= q2 ? rb1.y + q2 : rb2.y + q1;
-            const float c1 = t1.x, s1 = t1.y, c2 = t2.x, s2 = t2.y;
-            const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
-            // B J2 (columns p2, q2), then J1^T (rows p1, q1)
-            const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
-            const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
-            A[i_pp] = c1 * xpp - s1 * xqp;
-            A[i_qp] = s1 * xpp + c1 * xqp;
-            A[i_pq] = c1 * xpq - s1 * xqq;
-            A[i_qq] = s1 * xpq + c1 * xqq;
+          const int p1 = __float_as_int(t1.z), q1 = __float_as_int(t1.w);
+          const float c1 = t1.x, s1 = t1.y;
+          for (int i2 = i1 + lane; i2 < h; i2 += 32) {
+            const float4 t2 = tab[i2];
+            if (s1 == 0.f && t2.y == 0.f) continue;
+            if (i2 == i1) {
+              const float tt = tabt[i1];
+              const int ipq = p1 < q1 ? rb1.x + q1 : rb1.y + p1;
+              const float apq = A[ipq];
+              A[rb1.x + p1] -= tt * apq;
+              A[rb1.y + q1] += tt * apq;
+              A[ipq] = 0.f;
+            } else {
+              const int p2 = __float_as_int(t2.z), q2 = __float_as_int(t2.w);
+              const int2 rb2 = tabrb[i2];
+              const int i_pp = p1 <= p2 ? rb1.x + p2 : rb2.x + p1;
+              const int i_pq = p1 <= q2 ? rb1.x + q2 : rb2.y + p1;
+              const int i_qp = q1 <= p2 ? rb1.y + p2 : rb2.x + q1;
+              const int i_qq = q1 <= q2 ? rb1.y + q2 : rb2.y + q1;
+              const float c2 = t2.x, s2 = t2.y;
+              const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
+              // B J2 (columns p2, q2), then J1^T (rows p1, q1)
+              const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
+              const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
+              A[i_pp] = c1 * xpp - s1 * xqp;
+              A[i_qp] = s1 * xpp + c1 * xqp;
+              A[i_pq] = c1 * xpq - s1 * xqq;
+              A[i_qq] = s1 * xpq + c1 * xqq;
+            }
           }
         }
       }
       __syncthreads();
     }
-    __syncthreads();
-    if (!rot_sweep) {
+    if (!rotated) {
       ++sweep;  // this sweep did no rotation
       break;
     }
   }
 
   if (tid == 0) *nsweeps_out = sweep;
-  for (int i = tid; i < r; i += 1024) evals[i] = A[rb[i] + i];
+  for (int i = tid; i < r; i += 1024) evals[i] = A[packed_row(i, r) + i];
 }
 
 // Replays the logged rotations on rows of the identity: one warp per row of
