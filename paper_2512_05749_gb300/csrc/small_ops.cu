@@ -238,9 +238,16 @@ __global__ void k_sum_partials(const float* __restrict__ Gp, int S, int64_t n, d
                                double* __restrict__ G) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  double s = 0.0;
-  for (int k = 0; k < S; ++k) s += (double)Gp[(int64_t)k * n + e];
-  G[e] = s * scale;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = 0;
+  for (; k + 3 < S; k += 4) {
+    s0 += (double)Gp[(int64_t)k * n + e];
+    s1 += (double)Gp[(int64_t)(k + 1) * n + e];
+    s2 += (double)Gp[(int64_t)(k + 2) * n + e];
+    s3 += (double)Gp[(int64_t)(k + 3) * n + e];
+  }
+  for (; k < S; ++k) s0 += (double)Gp[(int64_t)k * n + e];
+  G[e] = ((s0 + s1) + (s2 + s3)) * scale;
 }
 }  // namespace
 
@@ -834,7 +841,10 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
   if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > noise) {
     const float tau = (aqq - app) / (2.f * apq);
     t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-    c = rsqrtf(1.f + t * t);
+    // correctly rounded 1/sqrt: c^2 + s^2 - 1 is then an unbiased rounding error,
+    // so the norms of the accumulated rotation W only random-walk over the
+    // thousands of rotations a column takes part in (a biased 1/sqrt drifts them)
+    c = __frsqrt_rn(1.f + t * t);
     s = t * c;
   }
 }
