@@ -767,12 +767,12 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
 }
 
 // Splits of the r x r Gram over the L rows: at least 16 chunks of 64 rows per
-// CTA, at most 8 CTAs per SM. Each CTA's FP32 TMEM accumulator runs over its
+// CTA, at most 4 CTAs per SM. Each CTA's FP32 TMEM accumulator runs over its
 // own chunk only (the accumulator's rounding is not to nearest, so the error
-// of a run grows with its length); the partials are summed in FP64.
+// of a run grows with its length); the partials are then summed in fixed order.
 int tc_gram_splits(int64_t L, int num_sms) {
   int64_t S = ceil_div(L, BK * 16);
-  if (S > 8LL * num_sms) S = 8LL * num_sms;
+  if (S > 4LL * num_sms) S = 4LL * num_sms;
   if (S < 1) S = 1;
   return (int)S;
 }
