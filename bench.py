@@ -245,11 +245,14 @@ def measured_traffic(w, kernel):
     return float(kv[key]) if key in kv else None
 
 
-def step_roofline_ms(w, args, peaks):
+def step_roofline_ms(w, args, peaks, engine_name="tcgen05"):
+    """O passes x max(bytes of O / HBM, 2NMr / compute peak); the compute peak is
+    the bf16 tensor rate for the tcgen05 engine and FP32 FFMA for SIMT."""
     esz = 2 if args.dtype == "bf16" else 4
     passes = 2 * args.rssr_q + 2 if args.path == "rssr" else 2 * w.m + 1
     t_bytes = w.N * w.M * esz / (peaks["hbm_gbs"] * 1e9)
-    t_flop = 2.0 * w.N * w.M * w.r / (peaks["bf16_tflops"] * 1e12)
+    peak = peaks["bf16_tflops"] if engine_name == "tcgen05" else FP32_SIMT_PEAK_TFLOPS
+    t_flop = 2.0 * w.N * w.M * w.r / (peak * 1e12)
     return passes * max(t_bytes, t_flop) * 1e3
 
 
@@ -407,8 +410,7 @@ def run_ours(args, w):
     step = AdaptiveStepper(s, w, dev, args) if args.path == "adaptive" else Stepper(s, w, dev, args)
     gs = step.inputs(max(1, args.steps))
     torch.cuda.synchronize()
-    engine_name = "tcgen05" if (args.dtype == "bf16" and s.handle and args.engine != "simt"
-                                and _uses_tc(s)) else "simt"
+    engine_name = s.engine
     if args.path == "adaptive":
         step.start(O, V0)
         V = V0
@@ -525,7 +527,7 @@ def run_ours(args, w):
     roof["peak_source"] += f" ({src})"
     if engine_name == "tcgen05":
         roof["traffic"] = measured_traffic(w, roof["kernel"])
-    step_roof = step_roofline_ms(w, args, peaks)
+    step_roof = step_roofline_ms(w, args, peaks, engine_name)
     s.close()
 
     if rank != 0:
@@ -545,7 +547,7 @@ def run_ours(args, w):
         "roofline": roof,
         "step_roofline": {"ms": step_roof, "frac": step_roof / ms_step,
                           "model": f"{2 * args.rssr_q + 2 if args.path == 'rssr' else 2 * w.m + 1} O passes "
-                                   "x max(bytes(O)/HBM, 2NMr/bf16 peak)"},
+                                   f"x max(bytes(O)/HBM, 2NMr/{'bf16 tensor' if engine_name == 'tcgen05' else 'FP32 FFMA'} peak)"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
         "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
@@ -841,18 +843,6 @@ def run_mlp_mf(args, w):
             "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
             "vs_materialised_fp32": compare, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
-
-
-def _uses_tc(s) -> bool:
-    from paper_2512_05749_gb300 import wssr as W
-    import ctypes
-    # engine resolution is internal; AUTO uses tcgen05 whenever it is supported for BF16
-    try:
-        probe = W.WSSR(64, 64, 8, 1e-3, dtype="bf16", engine="tcgen05")
-        probe.close()
-        return True
-    except W.WSSRError:
-        return False
 
 
 def main():

@@ -123,7 +123,12 @@ typedef struct {
 void wssr_default_options(wssr_options* opt);
 
 /* Create a context for N samples, M parameters, rank r, damping lambda > 0.
- * Constraints: 2 <= N, 1 <= r <= 256, r % 8 == 0, r <= N - 1, r <= M.
+ * Constraints: 2 <= N, 8 <= r <= 1024, r % 8 == 0, r <= N - 1, r <= M.
+ * The tensor-core engine (and with it history averaging and the matrix-free
+ * operator) takes r <= 256: WSSR_ENGINE_TCGEN05 with a larger r returns
+ * WSSR_ERR_UNSUPPORTED, WSSR_ENGINE_AUTO selects the SIMT engine. Above
+ * r = 256 the r x r Cholesky factor and the Rayleigh-Ritz eigensolve keep
+ * their matrix in the workspace instead of shared memory (slower).
  * Allocates the whole workspace (about 3 M r floats + small terms).
  * opt may be NULL (defaults). On failure *out is NULL. */
 wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda,
@@ -330,6 +335,10 @@ wssr_status wssr_mlp_unpad(wssr_mlp_handle h, const float* src, int64_t cols, fl
  * wssr_create's r is the capacity r_cap; the working rank (Algorithm 2's
  * r_max, the number of columns every following call reads and writes) starts
  * at r_cap and is changed between calls. */
+
+/* The engine the handle runs its products on: WSSR_ENGINE_TCGEN05 or
+ * WSSR_ENGINE_SIMT (AUTO resolved at wssr_create), or -1 for NULL. */
+int32_t wssr_get_engine(wssr_handle h);
 
 /* Set the working rank: 8 <= r <= r_cap, r a multiple of 8. The next call's
  * V_prev / V_out / sigma have r columns / entries. INVALID_ARG otherwise. */

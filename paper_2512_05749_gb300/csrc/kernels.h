@@ -110,9 +110,12 @@ int64_t gram_part_elems(int64_t L, int r);
 void launch_gram(const float* X, int64_t L, int r, double* part, double* G, double scale,
                  cudaStream_t st);
 // Cholesky of the equilibrated Gram + inverse factor: T = R^-1 (FP32 r x r, upper).
+// Above r = WSSR_SMEM_RANK_MAX the factor's blocks live in the device workspace ws
+// (chol_ws_floats(r) floats).
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
-                     cudaStream_t st);
+                     cudaStream_t st, float* ws = nullptr);
 size_t chol_inv_smem(int r);
+int64_t chol_ws_floats(int r);
 // Xo = X T (L x r times r x r), optional bf16 copies (row-major L x r, transposed r x ldT)
 // and FP64 column-sum partials of the bf16/f32 operand values written.
 void launch_apply(const float* X, int64_t L, int r, const float* T, float* Xo, void* out_lp_rowmajor,
@@ -138,9 +141,10 @@ void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf
 // Symmetric eigensolve of H (FP64 r x r) by FP32 cyclic Jacobi on one CTA.
 // Writes the rotation log and eigenvalues; launch_jacobi_vectors builds the sorted W.
 size_t jacobi_smem(int r);
+int64_t jacobi_ws_floats(int r);  // device workspace of the packed matrix above WSSR_SMEM_RANK_MAX
 int64_t jacobi_log_elems(int r, int max_sweeps);
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
-                   float* evals, int* status, cudaStream_t st);
+                   float* evals, int* status, cudaStream_t st, float* ws = nullptr);
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
                            int max_sweeps, float* W, cudaStream_t st);
 // c = V^T g (FP64), M x r V.

@@ -266,7 +266,7 @@ void launch_sum_partials(const float* Gp, int S, int r, double scale, double* G,
 // ---------------------------------------------------------------------------
 namespace {
 
-// Blocked algorithm with 32 x 32 blocks (nb = ceil(r / 32) <= 8):
+// Blocked algorithm with 32 x 32 blocks (nb = ceil(r / 32)):
 //   factor:   for each K, one warp factors the diagonal block A_KK = R_KK^T R_KK
 //             and inverts it (T_KK); the panel R_KJ = T_KK^T A_KJ and the
 //             trailing update A_IJ -= R_KI^T R_KJ run as strip GEMMs on all
@@ -292,16 +292,19 @@ __device__ __forceinline__ void strip(const float* L, const float* Rm, int i0, i
   }
 }
 
+// The blocks live in shared memory up to r = WSSR_SMEM_RANK_MAX, above it in
+// the device workspace gws (same layout; the CTA's accesses stay coherent
+// across __syncthreads).
 __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int r,
                                                    float* __restrict__ T, int* status,
-                                                   int* shift_count) {
+                                                   int* shift_count, float* __restrict__ gws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = (r + CB - 1) / CB;
   const int nblk = nb * (nb + 1) / 2;
-  double* d = reinterpret_cast<double*>(smem_raw);                 // 256 doubles
-  float* B = reinterpret_cast<float*>(smem_raw + 256 * sizeof(double));  // nblk blocks
-  float* TMP = B + (size_t)nblk * CBE;                               // nb - 1 blocks
-  float* TKK = TMP + (size_t)(nb - 1 > 0 ? nb - 1 : 1) * CBE;         // nb blocks
+  double* d = reinterpret_cast<double*>(smem_raw);                               // r doubles
+  float* B = gws ? gws : reinterpret_cast<float*>(smem_raw + (size_t)r * sizeof(double));  // nblk blocks
+  float* TMP = B + (size_t)nblk * CBE;                                           // nb - 1 blocks
+  float* TKK = TMP + (size_t)(nb - 1 > 0 ? nb - 1 : 1) * CBE;                     // nb blocks
   __shared__ int flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) flag = 0;
@@ -460,25 +463,33 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
 }
 }  // namespace
 
-size_t chol_inv_smem(int r) {
+// floats of the r x r factor's blocks (packed upper blocks, panel, diagonal inverses)
+int64_t chol_blocks_floats(int r) {
   const int nb = (r + CB - 1) / CB;
   const int nblk = nb * (nb + 1) / 2;
   const int ntmp = nb - 1 > 0 ? nb - 1 : 1;
-  return 256 * sizeof(double) + (size_t)(nblk + ntmp + nb) * CBE * sizeof(float);
+  return (int64_t)(nblk + ntmp + nb) * CBE;
 }
 
+size_t chol_inv_smem(int r) {
+  return (size_t)r * sizeof(double) +
+         (r <= WSSR_SMEM_RANK_MAX ? (size_t)chol_blocks_floats(r) * sizeof(float) : 0);
+}
+
+int64_t chol_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : chol_blocks_floats(r); }
+
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
-                     cudaStream_t st) {
+                     cudaStream_t st, float* ws) {
   const size_t sm = chol_inv_smem(r);
   static bool attr_set = false;
   if (!attr_set) {
-    // the largest request (r = 256); the kernel also has a few bytes of static shared memory
+    // the largest request (r = WSSR_SMEM_RANK_MAX); the kernel also has a few bytes of static shared memory
     if (cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chol_inv_smem(256)) != cudaSuccess)
+                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess)
       return;  // the error stays pending and is reported by the caller's launch check
     attr_set = true;
   }
-  k_chol_inv<<<1, 1024, sm, st>>>(G, r, T, status, shift_count);
+  k_chol_inv<<<1, 1024, sm, st>>>(G, r, T, status, shift_count, r <= WSSR_SMEM_RANK_MAX ? nullptr : ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,10 +654,10 @@ void launch_scale_rows_r(const float* in, int64_t ld_in, const double* sigma_pre
 }
 void launch_hist_coeffs(const double* sigma_prev, const double* Lbar_prev, double weight, int r, double* e,
                         cudaStream_t st) {
-  k_hist_coeffs<<<1, 256, 0, st>>>(sigma_prev, Lbar_prev, weight, r, e);
+  k_hist_coeffs<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(sigma_prev, Lbar_prev, weight, r, e);
 }
 void launch_lbar(const double* c, const double* sigma, int r, double* Lbar, cudaStream_t st) {
-  k_lbar<<<1, 256, 0, st>>>(c, sigma, r, Lbar);
+  k_lbar<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(c, sigma, r, Lbar);
 }
 
 // ---------------------------------------------------------------------------
@@ -864,12 +875,13 @@ __device__ __forceinline__ int packed_row(int i, int r) { return i * r - i * (i 
 
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
                                                  float2* __restrict__ rot_log, int* nsweeps_out,
-                                                 float* __restrict__ evals, int* status) {
+                                                 float* __restrict__ evals, int* status, float* __restrict__ gA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* A = reinterpret_cast<float*>(smem_raw);
-  __shared__ float4 tab[128];  // {c, s, p, q} (p, q as int bits)
-  __shared__ int2 tabrb[128];  // {rb(p), rb(q)}
-  __shared__ float tabt[128];  // t = tan(theta)
+  // packed matrix in shared memory up to r = WSSR_SMEM_RANK_MAX, else in the device workspace gA
+  float* A = gA ? gA : reinterpret_cast<float*>(smem_raw);
+  __shared__ float4 tab[WSSR_RANK_MAX / 2];  // {c, s, p, q} (p, q as int bits)
+  __shared__ int2 tabrb[WSSR_RANK_MAX / 2];  // {rb(p), rb(q)}
+  __shared__ float tabt[WSSR_RANK_MAX / 2];  // t = tan(theta)
   __shared__ int bad;
   int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * (r - 1) * (r / 2));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -892,10 +904,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     }
     return;
   }
-  // this warp's block rows (balanced when h % 64 == 0: w, 63-w, 64+w, 127-w)
-  int row_i1[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) row_i1[t] = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
+  // this warp's block rows: 32 t + w for t even and 32 t + 31 - w for t odd
+  // (balanced row lengths when h % 64 == 0; h = 128: w, 63-w, 64+w, 127-w)
+  const int nrow_t = (h + 31) / 32;
   // ring positions of this thread's pair in round 0 (round-robin: pair 0 keeps
   // index 0; every other position advances by one on the ring 1..r-1 per round)
   int pp = tid == 0 ? 0 : tid, qq = r - 1 - tid;
@@ -925,8 +936,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
       if (nact) {
         rotated = true;
 #pragma unroll 1
-        for (int t = 0; t < 4; ++t) {
-          const int i1 = row_i1[t];
+        for (int t = 0; t < nrow_t; ++t) {
+          const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
           if (i1 >= h) continue;
           const float4 t1 = tab[i1];
           const int2 rb1 = tabrb[i1];
@@ -977,14 +988,16 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
 // Replays the logged rotations on rows of the identity: one warp per row of
 // W (JV_WARPS rows per CTA), each row in shared memory, rounds separated by
 // __syncwarp only (the r/2 rotations of a round touch disjoint columns).
-// The CTA stages the log through shared memory in chunks of JV_CHUNK rounds
+// The CTA stages the log through shared memory in chunks of up to JV_CHUNK rounds
 // with double-buffered cp.async, so the L2 latency of the next chunk overlaps
 // the rotations of the current one. A lane follows its pairs' indices from
 // round to round incrementally (each advances by one on the ring of r - 1).
 // Idle rounds and idle pairs are skipped. Then writes W with columns sorted
 // by descending eigenvalue.
-constexpr int JV_CHUNK = 16;
+constexpr int JV_CHUNK = 16;     // most rounds staged at once
+constexpr int JV_STAGE = 2048;   // (c, s) pairs per staging buffer: rounds per chunk = min(16, 2048 / (r/2))
 constexpr int JV_WARPS = 4;
+constexpr int JV_M = WSSR_RANK_MAX / 64;  // pairs per lane (r/2 pairs over 32 lanes)
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
@@ -999,14 +1012,16 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
                                                                   const int* __restrict__ nsweeps,
                                                                   const float* __restrict__ evals, int r,
                                                                   int max_sweeps, float* __restrict__ W) {
-  __shared__ __align__(16) float2 stage[2][JV_CHUNK * 128];
+  __shared__ __align__(16) float2 stage[2][JV_STAGE];
   __shared__ int stage_cnt[2][JV_CHUNK];
-  __shared__ float wr_all[JV_WARPS][256];
-  __shared__ int rank_of[256];
+  __shared__ int rank_of[WSSR_RANK_MAX];
+  extern __shared__ float wr_all[];  // JV_WARPS rows of W, r floats each
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = blockIdx.x * JV_WARPS + warp;
   const int h = r / 2, n1 = r - 1;
-  float* wr = wr_all[warp];
+  const int chunk = JV_STAGE / h < JV_CHUNK ? JV_STAGE / h : JV_CHUNK;
+  const int mcount = (h + 31) / 32;
+  float* wr = wr_all + (size_t)warp * r;
   for (int i = tid; i < r; i += 32 * JV_WARPS) {
     const float li = evals[i];
     int rk = 0;
@@ -1019,9 +1034,9 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
   for (int c = lane; c < r; c += 32) wr[c] = (c == row) ? 1.f : 0.f;
   const int total = nsweeps[0] * n1;
   const int* round_nact = reinterpret_cast<const int*>(rot_log + (int64_t)max_sweeps * n1 * h);
-  const int nchunks = (total + JV_CHUNK - 1) / JV_CHUNK;
+  const int nchunks = (total + chunk - 1) / chunk;
   auto issue = [&](int c) {
-    const int t0 = c * JV_CHUNK, nt = min(JV_CHUNK, total - t0);
+    const int t0 = c * chunk, nt = min(chunk, total - t0);
     const float2* src = rot_log + (int64_t)t0 * h;
     float2* dst = stage[c & 1];
     for (int e = 2 * tid; e < nt * h; e += 64 * JV_WARPS) cp_async16(dst + e, src + e);
@@ -1030,9 +1045,9 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
   };
   // ring positions (index - 1) of this lane's pairs i = lane + 32 m in round 0;
   // pair 0's first index is the fixed index 0
-  int pu[4], qu[4];
+  int pu[JV_M], qu[JV_M];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
+  for (int m = 0; m < JV_M; ++m) {
     const int i = lane + 32 * m;
     pu[m] = (i + n1 - 1) % n1;
     qu[m] = (r - 2 - i + n1) % n1;
@@ -1046,15 +1061,15 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int t0 = c * JV_CHUNK, nt = min(JV_CHUNK, total - t0);
+    const int t0 = c * chunk, nt = min(chunk, total - t0);
     const float2* cs_chunk = stage[c & 1];
     if (row < r) {
       for (int j = 0; j < nt; ++j) {
         if (stage_cnt[c & 1][j] != 0) {
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
+          for (int m = 0; m < JV_M; ++m) {
             const int i = lane + 32 * m;
-            if (i < h) {
+            if (m < mcount && i < h) {
               const float2 cs = cs_chunk[j * h + i];
               if (cs.y != 0.f) {
                 const int p = (i == 0) ? 0 : pu[m] + 1, q = qu[m] + 1;
@@ -1067,7 +1082,7 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
           __syncwarp();
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < JV_M; ++m) {
           pu[m] = pu[m] + 1 == n1 ? 0 : pu[m] + 1;
           qu[m] = qu[m] + 1 == n1 ? 0 : qu[m] + 1;
         }
@@ -1080,27 +1095,34 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
 }
 }  // namespace
 
-size_t jacobi_smem(int r) { return sizeof(float) * (size_t)r * (r + 1) / 2; }
+size_t jacobi_smem(int r) { return r <= WSSR_SMEM_RANK_MAX ? sizeof(float) * (size_t)r * (r + 1) / 2 : 0; }
+int64_t jacobi_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : (int64_t)r * (r + 1) / 2; }
 // rotation log: max_sweeps x (r - 1) rounds x r/2 (c, s) pairs, then one int per round
 int64_t jacobi_log_elems(int r, int max_sweeps) {
   return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + 1) / 2;
 }
 
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
-                   float* evals, int* status, cudaStream_t st) {
+                   float* evals, int* status, cudaStream_t st, float* ws) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   k_jacobi<<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals,
-                                            status);
+                                            status, r <= WSSR_SMEM_RANK_MAX ? nullptr : ws);
 }
 
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
                            int max_sweeps, float* W, cudaStream_t st) {
-  k_jacobi_vectors<<<(unsigned)ceil_div(r, JV_WARPS), 32 * JV_WARPS, 0, st>>>((const float2*)rot_log, nsweeps,
-                                                                               evals, r, max_sweeps, W);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_jacobi_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(JV_WARPS * WSSR_RANK_MAX * sizeof(float)));
+    attr_set = true;
+  }
+  k_jacobi_vectors<<<(unsigned)ceil_div(r, JV_WARPS), 32 * JV_WARPS, JV_WARPS * r * sizeof(float), st>>>(
+      (const float2*)rot_log, nsweeps, evals, r, max_sweeps, W);
 }
 
 // ---------------------------------------------------------------------------
@@ -1140,24 +1162,24 @@ int dot_nb(int64_t M) {
 
 __global__ void k_dot_part(const float* __restrict__ V, const float* __restrict__ g, int64_t M, int r,
                            int64_t chunk, double* __restrict__ part) {
-  const int j = threadIdx.x;
-  if (j >= r) return;
   const int64_t mb = (int64_t)blockIdx.x * chunk;
   const int64_t me = mb + chunk < M ? mb + chunk : M;
-  double s64 = 0.0;
-  int64_t m = mb;
-  // 8 rows in flight per thread; FP32 partial sums over 64 rows, then FP64
-  while (m < me) {
-    const int64_t mend = m + 64 < me ? m + 64 : me;
-    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (; m + 8 <= mend; m += 8) {
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    double s64 = 0.0;
+    int64_t m = mb;
+    // 8 rows in flight per thread; FP32 partial sums over 64 rows, then FP64
+    while (m < me) {
+      const int64_t mend = m + 64 < me ? m + 64 : me;
+      float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (; m + 8 <= mend; m += 8) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = fmaf(V[(m + u) * r + j], g[m + u], a[u]);
+        for (int u = 0; u < 8; ++u) a[u] = fmaf(V[(m + u) * r + j], g[m + u], a[u]);
+      }
+      for (; m < mend; ++m) a[0] = fmaf(V[m * r + j], g[m], a[0]);
+      s64 += (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
     }
-    for (; m < mend; ++m) a[0] = fmaf(V[m * r + j], g[m], a[0]);
-    s64 += (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+    part[(int64_t)blockIdx.x * r + j] = s64;
   }
-  part[(int64_t)blockIdx.x * r + j] = s64;
 }
 
 __global__ void k_finalize_sigma(const double* __restrict__ Hp, int r, double* __restrict__ sigma) {
@@ -1200,7 +1222,7 @@ __global__ void k_woodbury_coeffs(const double* __restrict__ sigma, const double
 __global__ void __launch_bounds__(256) k_woodbury(const float* __restrict__ V, const float* __restrict__ g,
                                                   const double* __restrict__ e, int64_t M, int r,
                                                   float inv_lam, float* __restrict__ delta) {
-  __shared__ float es[256];
+  __shared__ float es[WSSR_RANK_MAX];
   for (int i = threadIdx.x; i < r; i += blockDim.x) es[i] = (float)e[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -1233,7 +1255,7 @@ void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, 
 }
 
 void launch_finalize_sigma(const double* Hp, int r, double* sigma, cudaStream_t st) {
-  k_finalize_sigma<<<1, 256, 0, st>>>(Hp, r, sigma);
+  k_finalize_sigma<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(Hp, r, sigma);
 }
 
 void launch_woodbury_coeffs(const double* sigma, const double* c, int r, double lam, int mode,

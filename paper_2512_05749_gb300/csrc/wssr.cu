@@ -73,6 +73,8 @@ struct wssr_ctx {
   float* TY = nullptr;         // r x r: Cholesky-QR factor of Y
   float* TW = nullptr;         // r x r: TX W
   float* tc_gram_part = nullptr;  // tcgen05 Gram partials (splits x r x r)
+  float* chol_ws = nullptr;       // r x r factor blocks above the shared-memory rank
+  float* jac_ws = nullptr;        // packed Jacobi matrix above the shared-memory rank
   void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
   double* cpart = nullptr;        // per-tile partials of V^T g fused into the rotation
   bool c_ready = false;           // h->c already holds V_out^T g
@@ -109,7 +111,8 @@ void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar, h->wE, h->wE_sum};
+                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar, h->wE, h->wE_sum,
+                  h->chol_ws, h->jac_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -253,7 +256,7 @@ void factor_operand(wssr_ctx* h, const void* Xop, float* T_out, cudaStream_t st)
   } else {
     launch_gram_any(Xop, is_bf16(h) ? 1 : 0, h->M, r, h->gram_part, h->G, 1.0, st);
   }
-  launch_chol_inv(h->G, r, T_out, h->status, h->status + 1, st);
+  launch_chol_inv(h->G, r, T_out, h->status, h->status + 1, st, h->chol_ws);
   h->launches += 3;
 }
 
@@ -275,7 +278,7 @@ void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_ORTH, st);
   launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
-  launch_chol_inv(h->G, r, h->TY, h->status, h->status + 1, st);
+  launch_chol_inv(h->G, r, h->TY, h->status, h->status + 1, st, h->chol_ws);
   launch_apply(X, L, r, h->TY, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st, csum_rows);
   h->launches += 4;
 }
@@ -359,7 +362,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   right_multiply_Y(h, h->Y, h->TX, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
-  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st);
+  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st, h->jac_ws);
   launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->opt.jacobi_sweeps, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
@@ -500,7 +503,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   wssr_options opt;
   if (opt_in) opt = *opt_in;
   else wssr_default_options(&opt);
-  if (N < 2 || M < 1 || r < 8 || r > 256 || r % 8 != 0 || r > N - 1 || r > M) return WSSR_ERR_INVALID_ARG;
+  if (N < 2 || M < 1 || r < 8 || r > WSSR_RANK_MAX || r % 8 != 0 || r > N - 1 || r > M) return WSSR_ERR_INVALID_ARG;
   if (!(lambda > 0.0)) return WSSR_ERR_INVALID_ARG;
   if (opt.m < 1 || opt.m_init < 1 || opt.jacobi_sweeps < 1 || opt.jacobi_sweeps > 64) return WSSR_ERR_INVALID_ARG;
   if (opt.dtype != WSSR_DTYPE_F32 && opt.dtype != WSSR_DTYPE_BF16) return WSSR_ERR_INVALID_ARG;
@@ -528,7 +531,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
     delete h;
     return WSSR_ERR_CUDA;
   }
-  const bool tc_ok = tc_supported(h->dev);
+  // the tensor-core engine holds 128 x r accumulators in TMEM: r <= WSSR_TC_RANK_MAX
+  const bool tc_ok = tc_supported(h->dev) && r <= WSSR_TC_RANK_MAX;
   if (opt.engine == WSSR_ENGINE_TCGEN05) {
     if (!tc_ok || opt.dtype != WSSR_DTYPE_BF16) {
       delete h;
@@ -578,6 +582,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(c, (size_t)r * d);
   ALLOC(e, (size_t)r * d);
   ALLOC(dot_part, (size_t)dot_part_elems(M, r) * d);
+  if (chol_ws_floats(r) > 0) ALLOC(chol_ws, (size_t)chol_ws_floats(r) * f);
+  if (jacobi_ws_floats(r) > 0) ALLOC(jac_ws, (size_t)jacobi_ws_floats(r) * f);
   ALLOC(TX, (size_t)r * r * f);
   ALLOC(TY, (size_t)r * r * f);
   ALLOC(TW, (size_t)r * r * f);
@@ -859,6 +865,11 @@ wssr_status wssr_set_rank(wssr_handle h, int32_t r) {
 }
 
 int32_t wssr_get_rank(wssr_handle h) { return h ? h->r : -1; }
+
+int32_t wssr_get_engine(wssr_handle h) {
+  if (!h) return -1;
+  return h->use_tc ? WSSR_ENGINE_TCGEN05 : WSSR_ENGINE_SIMT;
+}
 
 wssr_status wssr_rank_next(wssr_handle h, const double* sigma, double r_reg, double eps, int32_t* r_sel,
                            int32_t* r_next, wssr_stream_t stream) {

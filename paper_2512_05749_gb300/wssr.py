@@ -43,7 +43,7 @@ EXPORTED = [
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
     "wssr_step_local_energy", "wssr_randomized_svd", "wssr_set_rank", "wssr_get_rank", "wssr_rank_next",
-    "wssr_extend_basis",
+    "wssr_extend_basis", "wssr_get_engine",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_get_stats": (i32, [vp, P(i64), i32]),
         "wssr_set_rank": (i32, [vp, i32]),
         "wssr_get_rank": (i32, [vp]),
+        "wssr_get_engine": (i32, [vp]),
         "wssr_rank_next": (i32, [vp, vp, f64, f64, P(ctypes.c_int32), P(ctypes.c_int32), vp]),
         "wssr_extend_basis": (i32, [vp, i64, i32, vp, i32, vp, vp]),
         "wssr_mlp_param_count": (i64, [P(wssr_mlp_desc)]),
@@ -492,6 +493,11 @@ class WSSR:
             V, sigma = out
         wssr_randomized_svd(self.handle, self._op(O), Omega.contiguous(), q, V, sigma, stream)
         return V, sigma
+
+    @property
+    def engine(self) -> str:
+        """The engine the products run on: "tcgen05" or "simt"."""
+        return "tcgen05" if int(load().wssr_get_engine(self.handle)) == WSSR_ENGINE_TCGEN05 else "simt"
 
     def set_rank(self, r: int):
         """Working rank of the following calls (Algorithm 2's r_max; 8 <= r <= r_cap, multiple of 8)."""

@@ -110,6 +110,11 @@ WORKLOADS = {
     "planted-n16384-m1m-r256": Planted(
         "planted-n16384-m1m-r256", N=16384, M=1_000_000, r=256, lam=1e-4, m=2, steps=20,
         sigma_power=1.2, K=1024, noise=1e-3, dtype="bf16"),
+    # The same matrix at twice the rank (the upper range of the paper's
+    # adaptive runs): above 256 the step runs on the SIMT engine.
+    "planted-n16384-m1m-r512": Planted(
+        "planted-n16384-m1m-r512", N=16384, M=1_000_000, r=512, lam=1e-4, m=2, steps=20,
+        sigma_power=1.2, K=1024, noise=1e-3, dtype="bf16"),
     # Same shape family at 1/7.6 of the parameters (O = 4.3 GB, above L2): the
     # case ncu captures of the O-pass kernels run on.
     "planted-n16384-m131k-r256": Planted(

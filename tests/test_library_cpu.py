@@ -46,7 +46,7 @@ def test_status_strings():
 @pytest.mark.parametrize("N,M,r,lam", [
     (1, 10, 8, 1e-3),      # N < 2
     (100, 50, 12, 1e-3),   # r not a multiple of 8
-    (100, 50, 264, 1e-3),  # r > 256
+    (100, 50, 264, 1e-3),  # r > M and r > N - 1
     (8, 50, 8, 1e-3),      # r > N - 1
     (100, 4, 8, 1e-3),     # r > M
     (100, 50, 8, 0.0),     # lambda <= 0
