@@ -48,6 +48,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over the ranks of the process group (x itself without
+    one): a replicated job takes as long as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks / throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -448,12 +462,7 @@ def run_ours(args, w):
     prof = s.profile_end()
     s.check("timed steps")
     stats = s.stats()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
+    ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
 
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
@@ -479,11 +488,7 @@ def run_ours(args, w):
         e3.record(stream)
         torch.cuda.synchronize()
         s.check("e2e")
-        e2e_ms = e2.elapsed_time(e3) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2.elapsed_time(e3) / args.e2e_steps)
         e2e = {"value": e2e_ms, "unit": "ms",
                "h2d_bytes_per_step": int(O.numel() * O.element_size() + gs[0].numel() * gs[0].element_size()),
                "d2h_bytes_per_step": int(step.d2h_bytes()), "steps": args.e2e_steps}
@@ -729,11 +734,7 @@ def run_mlp_mf(args, w):
     prof = s.profile_end()
     s.check("timed steps")
     stats = s.stats()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
 
     # ---- end to end: theta and the samples from pinned host memory, delta (user order) back ----
     e2e = None
@@ -759,7 +760,7 @@ def run_mlp_mf(args, w):
         e3.record(stream)
         torch.cuda.synchronize()
         s.check("e2e")
-        e2e = {"value": e2.elapsed_time(e3) / args.e2e_steps, "unit": "ms",
+        e2e = {"value": max_over_ranks(e2.elapsed_time(e3) / args.e2e_steps), "unit": "ms",
                "h2d_bytes_per_step": int(4 * w.M + xs[0].numel() * 4 + ins[0].numel() * 4),
                "d2h_bytes_per_step": int(4 * w.M + 8 * w.r), "steps": args.e2e_steps}
 
