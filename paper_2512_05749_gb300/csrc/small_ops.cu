@@ -137,25 +137,35 @@ int gram_nb(int64_t L) {
   return (int)nb;
 }
 
+// Exact FP32 sum: s + e = a + b (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Gram partial of one chunk of rows: 64 x 64 tile pairs (ti <= tj), 4 x 4
+// entries per thread, FP32 products summed over runs of GFLUSH rows, each run
+// added into a double-float (hi + lo, exact TwoSum: FP64 adds are 1/64 rate here).
 template <typename TIn>
 __global__ void __launch_bounds__(256) k_gram_part(const TIn* __restrict__ X, int64_t L, int r,
                                                    int64_t chunk, double* __restrict__ part) {
   __shared__ __align__(16) float Xi[GK][GT];
   __shared__ __align__(16) float Xj[GK][GT];
-  // tile pair (ti <= tj) from blockIdx.y
+  // tile pair (ti <= tj) from blockIdx.x: a chunk's tile pairs run together
+  // and share its rows through L2
   const int T = (r + GT - 1) / GT;
-  int p = blockIdx.y, ti = 0;
+  int p = blockIdx.x, ti = 0;
   while (p >= T - ti) { p -= T - ti; ++ti; }
   const int tj = ti + p;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t rb = (int64_t)blockIdx.x * chunk;
+  const int64_t rb = (int64_t)blockIdx.y * chunk;
   const int64_t re = rb + chunk < L ? rb + chunk : L;
-  float a32[4][4];
-  double a64[4][4];
+  float a32[4][4], hi[4][4], lo[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) a32[a][b] = 0.f, a64[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) a32[a][b] = 0.f, hi[a][b] = 0.f, lo[a][b] = 0.f;
   int64_t since = 0;
   for (int64_t k0 = rb; k0 < re; k0 += GK) {
     for (int e = tid; e < GK * GT; e += 256) {
@@ -183,10 +193,16 @@ __global__ void __launch_bounds__(256) k_gram_part(const TIn* __restrict__ X, in
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) a64[a][b] += (double)a32[a][b], a32[a][b] = 0.f;
+        for (int b = 0; b < 4; ++b) {
+          float sum, err;
+          two_sum(hi[a][b], a32[a][b], sum, err);
+          hi[a][b] = sum;
+          lo[a][b] += err;
+          a32[a][b] = 0.f;
+        }
     }
   }
-  double* out = part + (int64_t)blockIdx.x * r * r;
+  double* out = part + (int64_t)blockIdx.y * r * r;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = ti * GT + ty * 4 + a;
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const TIn* __restrict__ X, in
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = tj * GT + tx * 4 + b;
-      if (j < r) out[(int64_t)i * r + j] = a64[a][b] + (double)a32[a][b];
+      if (j < r) out[(int64_t)i * r + j] = ((double)hi[a][b] + (double)lo[a][b]) + (double)a32[a][b];
     }
   }
 }
@@ -220,7 +236,7 @@ void launch_gram_any(const void* X, int x_bf16, int64_t L, int r, double* part, 
   const int64_t chunk = ceil_div(ceil_div(L, nb), GK) * GK;
   const int nbe = (int)ceil_div(L, chunk);
   const int T = (r + GT - 1) / GT;
-  dim3 grid((unsigned)nbe, (unsigned)(T * (T + 1) / 2));
+  dim3 grid((unsigned)(T * (T + 1) / 2), (unsigned)nbe);
   if (x_bf16)
     k_gram_part<bf16><<<grid, 256, 0, st>>>((const bf16*)X, L, r, chunk, part);
   else
@@ -496,68 +512,109 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
 // Tall apply Xo = X T with optional low-precision copies and column sums
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int AM = 64, AN = 64, AK = 32;
+constexpr int AM = 128, AN = 64, AK = 16;
 
-// Input layouts of the tall block X: 0 = float row-major (L x r), 1 = bf16
-// row-major (L x r), 2 = bf16 K-blocked (blk_index).
+// Xo = X T for a tall block X (L x r) and T (r x r): 128 x 64 output tiles,
+// 16-deep K steps double-buffered (the next one fetched into registers while
+// the current one is multiplied), 256 threads with 8 x 4 outputs each (rows
+// ty*4 and 64 + ty*4, columns tx*4). Optional outputs, from the tile staged in
+// shared memory after the main loop (reusing the operand buffers): a low
+// precision row-major copy, a bf16 transposed copy (row pitch ldT) and FP64
+// column sums per 128-row block over the rows below csum_rows.
+// Input layouts of X: 0 = float row-major (L x r), 1 = bf16 row-major (L x r),
+// 2 = bf16 K-blocked (blk_index).
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int64_t ldx, int64_t L, int r,
                                                const float* __restrict__ T, float* __restrict__ Xo,
                                                void* lp_row, int lp_bf16, bf16* __restrict__ outT,
                                                int64_t ldT, double* __restrict__ colsum_part, int64_t csum_rows) {
-  __shared__ __align__(16) float As[AK][AM + 4];
-  __shared__ __align__(16) float Bs[AK][AN];
-  __shared__ float Cs[AN][AM + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = (int64_t)blockIdx.x * AM;
-  const int j0 = blockIdx.y * AN;
-  float acc[4][4];
+  constexpr int A_FLOATS = 2 * AK * (AM + 4), B_FLOATS = 2 * AK * (AN + 4), C_FLOATS = AN * (AM + 1);
+  constexpr int SM_FLOATS = (A_FLOATS + B_FLOATS) > C_FLOATS ? (A_FLOATS + B_FLOATS) : C_FLOATS;
+  __shared__ __align__(16) float sm[SM_FLOATS];
+  float (*As)[AK][AM + 4] = reinterpret_cast<float (*)[AK][AM + 4]>(sm);
+  float (*Bs)[AK][AN + 4] = reinterpret_cast<float (*)[AK][AN + 4]>(sm + A_FLOATS);
+  float (*Cs)[AM + 1] = reinterpret_cast<float (*)[AM + 1]>(sm);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // one-dimensional grid, column tile fastest: the column tiles of a row block
+  // run together and share its rows through L2
+  const int ntj = (r + AN - 1) / AN;
+  const int64_t rblk = blockIdx.x / ntj;
+  const int64_t m0 = rblk * AM;
+  const int j0 = (int)(blockIdx.x % ntj) * AN;
+  float ra[8], rb[4];
+  auto fetch = [&](int k0) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int k0 = 0; k0 < r; k0 += AK) {
-    if (LAYOUT == 2) {
-      const bf16* X = reinterpret_cast<const bf16*>(Xv);
-      for (int e = tid; e < AM * AK; e += 256) {
-        const int col = e / AM, row = e % AM;  // coalesced along the parameters
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      float v = 0.f;
+      if (LAYOUT == 2) {
+        const int col = e >> 7, row = e & 127;  // coalesced along the parameters
         const int64_t m = m0 + row;
         const int k = k0 + col;
-        As[col][row] = (m < L && k < r) ? __bfloat162float(X[blk_index(m, k, r)]) : 0.f;
-      }
-    } else {
-      for (int e = tid; e < AM * AK; e += 256) {
-        const int row = e / AK, col = e % AK;
+        if (m < L && k < r) v = __bfloat162float(reinterpret_cast<const bf16*>(Xv)[blk_index(m, k, r)]);
+      } else {
+        const int row = e >> 4, col = e & 15;
         const int64_t m = m0 + row;
         const int k = k0 + col;
-        float v = 0.f;
         if (m < L && k < r)
           v = LAYOUT == 1 ? __bfloat162float(reinterpret_cast<const bf16*>(Xv)[m * r + k])
                           : reinterpret_cast<const float*>(Xv)[m * r + k];
-        As[col][row] = v;
       }
+      ra[u] = v;
     }
-    for (int e = tid; e < AK * AN; e += 256) {
-      const int row = e / AN, col = e % AN;
-      const int k = k0 + row, j = j0 + col;
-      Bs[row][col] = (k < r && j < r) ? T[(int64_t)k * r + j] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < AK; ++kk) {
-      float4 u = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      float ua[4] = {u.x, u.y, u.z, u.w}, va[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u;
+      const int row = e >> 6, col = e & 63;
+      const int k = k0 + row, j = j0 + col;
+      rb[u] = (k < r && j < r) ? T[(int64_t)k * r + j] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      if (LAYOUT == 2) As[buf][e >> 7][e & 127] = ra[u];
+      else As[buf][e & 15][e >> 4] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u;
+      Bs[buf][e >> 6][e & 63] = rb[u];
+    }
+  };
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < r; k0 += AK) {
+    const bool more = k0 + AK < r;
+    if (more) fetch(k0 + AK);
+#pragma unroll
+    for (int kk = 0; kk < AK; ++kk) {
+      const float4 u0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 u1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 v = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float ua[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w}, va[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ua[a], va[b], acc[a][b]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
+  const bool staged = outT != nullptr || colsum_part != nullptr;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t m = m0 + ty * 4 + a;
+  for (int a = 0; a < 8; ++a) {
+    const int rl = a < 4 ? ty * 4 + a : 64 + ty * 4 + (a - 4);
+    const int64_t m = m0 + rl;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx * 4 + b;
@@ -568,10 +625,10 @@ __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int6
       if (ok && lp_row) {
         if (lp_bf16) reinterpret_cast<bf16*>(lp_row)[m * r + j] = __float2bfloat16_rn(v);
       }
-      Cs[tx * 4 + b][ty * 4 + a] = ok ? v : 0.f;
+      if (staged) Cs[tx * 4 + b][rl] = ok ? v : 0.f;  // the operand buffers are free after the loop
     }
   }
-  if (outT == nullptr && colsum_part == nullptr) return;
+  if (!staged) return;
   __syncthreads();
   if (outT) {
     for (int e = tid; e < AM * AN; e += 256) {
@@ -589,7 +646,7 @@ __global__ void __launch_bounds__(256) k_apply(const void* __restrict__ Xv, int6
       double s = 0.0;
       const int64_t lim = csum_rows - m0;
       for (int rr = 0; rr < AM && rr < lim; ++rr) s += (double)Cs[tid][rr];
-      colsum_part[(int64_t)blockIdx.x * r + j] = s;
+      colsum_part[rblk * r + j] = s;
     }
   }
 }
@@ -599,7 +656,7 @@ void launch_apply_any(const void* X, int layout, int64_t ldx, int64_t L, int r, 
                       float* Xo, void* out_lp_rowmajor, int lp_is_bf16, void* out_bf16_T, int64_t ldT,
                       double* colsum_part, int64_t* nblocks_out, cudaStream_t st, int64_t csum_rows) {
   if (csum_rows < 0) csum_rows = L;
-  dim3 grid((unsigned)ceil_div(L, AM), (unsigned)ceil_div(r, AN));
+  dim3 grid((unsigned)(ceil_div(L, AM) * ceil_div(r, AN)));
   if (layout == 2)
     k_apply<2><<<grid, 256, 0, st>>>(X, ldx, L, r, T, Xo, out_lp_rowmajor, lp_is_bf16, (bf16*)out_bf16_T,
                                      ldT, colsum_part, csum_rows);
