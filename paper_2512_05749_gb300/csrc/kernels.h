@@ -141,7 +141,7 @@ void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf
 // Symmetric eigensolve of H (FP64 r x r) by FP32 cyclic Jacobi on one CTA.
 // Writes the rotation log and eigenvalues; launch_jacobi_vectors builds the sorted W.
 size_t jacobi_smem(int r);
-int64_t jacobi_ws_floats(int r);  // device workspace of the packed matrix above WSSR_SMEM_RANK_MAX
+int64_t jacobi_ws_floats(int r);  // device workspace of the matrix above WSSR_SMEM_RANK_MAX
 int64_t jacobi_log_elems(int r, int max_sweeps);
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
                    float* evals, int* status, cudaStream_t st, float* ws = nullptr);

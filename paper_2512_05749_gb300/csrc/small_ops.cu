@@ -920,29 +920,49 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
   }
 }
 
-// One CTA of 1024 threads; A = packed upper triangle in shared memory
-// (A[rb(i) + j], j >= i, rb(i) = i r - i (i + 1) / 2). Per round: the r/2
-// rotation threads (one per pair, following their ring positions from round
-// to round) put {c, s, p, q} + {rb(p), rb(q)} (+ t for the diagonal blocks)
-// into a table, __syncthreads_count gives every thread the number of active
-// rotations; then every warp updates the 2 x 2 blocks (i1, i2 >= i1) of its
-// (at most 4) block rows, holding row i1's table entry in registers while its
-// lanes walk i2. Blocks whose two pairs are both idle are skipped.
-__device__ __forceinline__ int packed_row(int i, int r) { return i * r - i * (i + 1) / 2; }
+// Storage of the symmetric matrix in the round-robin's own coordinates. Index
+// 0 never moves; indices 1..n1 (n1 = r - 1) sit on a ring, u = index - 1, and
+// in round k pair i >= 1 is (p, q) with u(p) = i - 1 + k, u(q) = n1 - 1 - i + k
+// (mod n1), pair 0 is (0, q) with u(q) = n1 - 1 + k. Element (x, y) of the
+// ring part is kept once, at row u and "distance" d = (u(y) - u(x)) mod n1
+// when d < h (h = r / 2), else at row u(y) and distance n1 - d:
+// S[u L + d], L = h rounded up to 32. Row 0 of the matrix is Z[u(y)], a_00 a
+// scalar. For the 2 x 2 block of pairs I <= J the four distances are J - I,
+// I + J and n1 - I - J whatever the round, and the rows are u(p_I), u(q_I),
+// u(p_J), u(q_J): a warp walking J over its lanes reads and writes addresses
+// 1 or L - 1 apart (no shared-memory bank conflicts), from closed-form
+// offsets instead of per-pair row tables.
+__device__ __forceinline__ int ring_add(int a, int b, int n1) {  // (a + b) mod n1, 0 <= a, b < n1
+  const int s = a + b;
+  return s >= n1 ? s - n1 : s;
+}
+__device__ __forceinline__ int jacobi_lds(int h) { return (h + 31) / 32 * 32; }
+// offset of ring element (u, v) (any order) in S
+__device__ __forceinline__ int skew_at(int u, int v, int n1, int h, int L) {
+  const int d = v >= u ? v - u : v - u + n1;
+  return d < h ? u * L + d : v * L + (n1 - d);
+}
 
+// One CTA of 1024 threads. Per round: the r/2 rotation threads put {c, s}
+// (+ t for the diagonal blocks) of their pair into a table and
+// __syncthreads_count gives every thread the number of active rotations; then
+// every warp updates the 2 x 2 blocks (I, J >= I) of its (at most
+// ceil(h / 32)) block rows, holding row I's rotation in registers while its
+// lanes walk J. Blocks whose two pairs are both idle are skipped. The matrix
+// lives in shared memory up to r = WSSR_SMEM_RANK_MAX, else in the device
+// workspace gA (same layout).
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
                                                  float2* __restrict__ rot_log, int* nsweeps_out,
                                                  float* __restrict__ evals, int* status, float* __restrict__ gA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // packed matrix in shared memory up to r = WSSR_SMEM_RANK_MAX, else in the device workspace gA
-  float* A = gA ? gA : reinterpret_cast<float*>(smem_raw);
-  __shared__ float4 tab[WSSR_RANK_MAX / 2];  // {c, s, p, q} (p, q as int bits)
-  __shared__ int2 tabrb[WSSR_RANK_MAX / 2];  // {rb(p), rb(q)}
+  const int h = r / 2, n1 = r - 1, L = jacobi_lds(h);
+  float* S = gA ? gA : reinterpret_cast<float*>(smem_raw);
+  float* Z = S + (size_t)n1 * L;  // row 0: Z[u], u = 0..n1-1; a_00 = Z[n1]
+  __shared__ float2 tab[WSSR_RANK_MAX / 2];  // {c, s}
   __shared__ float tabt[WSSR_RANK_MAX / 2];  // t = tan(theta)
   __shared__ int bad;
-  int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * (r - 1) * (r / 2));
+  int* round_nact = reinterpret_cast<int*>(rot_log + (int64_t)max_sweeps * n1 * h);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int h = r / 2, n1 = r - 1;
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int e = tid; e < r * r; e += 1024) {
@@ -950,7 +970,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     if (i <= j) {
       const double v = H[e];
       if (!isfinite(v)) bad = 1;
-      A[packed_row(i, r) + j] = (float)v;
+      const int off = i == 0 ? (j == 0 ? n1 : j - 1) + n1 * L : skew_at(i - 1, j - 1, n1, h, L);
+      S[off] = (float)v;
     }
   }
   __syncthreads();
@@ -964,9 +985,6 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
   // this warp's block rows: 32 t + w for t even and 32 t + 31 - w for t odd
   // (balanced row lengths when h % 64 == 0; h = 128: w, 63-w, 64+w, 127-w)
   const int nrow_t = (h + 31) / 32;
-  // ring positions of this thread's pair in round 0 (round-robin: pair 0 keeps
-  // index 0; every other position advances by one on the ring 1..r-1 per round)
-  int pp = tid == 0 ? 0 : tid, qq = r - 1 - tid;
 
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -974,58 +992,63 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     for (int k = 0; k < n1; ++k) {
       int act = 0;
       if (tid < h) {
-        const int p = pp, q = qq;
-        const int rbp = packed_row(p, r), rbq = packed_row(q, r);
-        const float app = A[rbp + p], aqq = A[rbq + q];
-        const float apq = A[p < q ? rbp + q : rbq + p];
+        const int uq = ring_add(n1 - 1 - tid, k, n1);
+        float app, apq;
+        if (tid == 0) {
+          app = Z[n1];
+          apq = Z[uq];
+        } else {
+          const int up = ring_add(tid - 1, k, n1);
+          app = S[up * L];
+          apq = S[2 * tid >= h ? up * L + n1 - 2 * tid : uq * L + 2 * tid];
+        }
+        const float aqq = S[uq * L];
         float c, s, t;
         jacobi_rotation(app, aqq, apq, c, s, t);
-        tab[tid] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
-        tabrb[tid] = make_int2(rbp, rbq);
+        tab[tid] = make_float2(c, s);
         tabt[tid] = t;
         rot_log[((int64_t)sweep * n1 + k) * h + tid] = make_float2(c, s);
         act = s != 0.f;
-        if (tid != 0) pp = pp == n1 ? 1 : pp + 1;
-        qq = qq == n1 ? 1 : qq + 1;
       }
       const int nact = __syncthreads_count(act);
       if (tid == 0) round_nact[sweep * n1 + k] = nact;
       if (nact) {
         rotated = true;
 #pragma unroll 1
-        for (int t = 0; t < nrow_t; ++t) {
-          const int i1 = ((h & 63) == 0 && (t & 1)) ? 32 * t + 31 - warp : 32 * t + warp;
-          if (i1 >= h) continue;
-          const float4 t1 = tab[i1];
-          const int2 rb1 = tabrb[i1];
-          const int p1 = __float_as_int(t1.z), q1 = __float_as_int(t1.w);
+        for (int rt = 0; rt < nrow_t; ++rt) {
+          const int I = ((h & 63) == 0 && (rt & 1)) ? 32 * rt + 31 - warp : 32 * rt + warp;
+          if (I >= h) continue;
+          const float2 t1 = tab[I];
           const float c1 = t1.x, s1 = t1.y;
-          for (int i2 = i1 + lane; i2 < h; i2 += 32) {
-            const float4 t2 = tab[i2];
+          const int uqI = ring_add(n1 - 1 - I, k, n1);
+          const int upI = I ? ring_add(I - 1, k, n1) : 0;
+          for (int J = I + lane; J < h; J += 32) {
+            const float2 t2 = tab[J];
             if (s1 == 0.f && t2.y == 0.f) continue;
-            if (i2 == i1) {
-              const float tt = tabt[i1];
-              const int ipq = p1 < q1 ? rb1.x + q1 : rb1.y + p1;
-              const float apq = A[ipq];
-              A[rb1.x + p1] -= tt * apq;
-              A[rb1.y + q1] += tt * apq;
-              A[ipq] = 0.f;
+            if (J == I) {
+              const float tt = tabt[I];
+              const int ipp = I ? upI * L : n1 * L + n1;
+              const int ipq = I ? (2 * I >= h ? upI * L + n1 - 2 * I : uqI * L + 2 * I) : n1 * L + uqI;
+              const float apq = S[ipq];
+              S[ipp] -= tt * apq;
+              S[uqI * L] += tt * apq;
+              S[ipq] = 0.f;
             } else {
-              const int p2 = __float_as_int(t2.z), q2 = __float_as_int(t2.w);
-              const int2 rb2 = tabrb[i2];
-              const int i_pp = p1 <= p2 ? rb1.x + p2 : rb2.x + p1;
-              const int i_pq = p1 <= q2 ? rb1.x + q2 : rb2.y + p1;
-              const int i_qp = q1 <= p2 ? rb1.y + p2 : rb2.x + q1;
-              const int i_qq = q1 <= q2 ? rb1.y + q2 : rb2.y + q1;
+              const int upJ = ring_add(J - 1, k, n1), uqJ = ring_add(n1 - 1 - J, k, n1);
+              const int IJ = I + J;
+              const int i_pp = I ? upI * L + (J - I) : n1 * L + upJ;
+              const int i_pq = I ? (IJ >= h ? upI * L + n1 - IJ : uqJ * L + IJ) : n1 * L + uqJ;
+              const int i_qp = IJ < h ? uqI * L + IJ : upJ * L + n1 - IJ;
+              const int i_qq = uqJ * L + (J - I);
               const float c2 = t2.x, s2 = t2.y;
-              const float bpp = A[i_pp], bpq = A[i_pq], bqp = A[i_qp], bqq = A[i_qq];
+              const float bpp = S[i_pp], bpq = S[i_pq], bqp = S[i_qp], bqq = S[i_qq];
               // B J2 (columns p2, q2), then J1^T (rows p1, q1)
               const float xpp = c2 * bpp - s2 * bpq, xpq = s2 * bpp + c2 * bpq;
               const float xqp = c2 * bqp - s2 * bqq, xqq = s2 * bqp + c2 * bqq;
-              A[i_pp] = c1 * xpp - s1 * xqp;
-              A[i_qp] = s1 * xpp + c1 * xqp;
-              A[i_pq] = c1 * xpq - s1 * xqq;
-              A[i_qq] = s1 * xpq + c1 * xqq;
+              S[i_pp] = c1 * xpp - s1 * xqp;
+              S[i_qp] = s1 * xpp + c1 * xqp;
+              S[i_pq] = c1 * xpq - s1 * xqq;
+              S[i_qq] = s1 * xpq + c1 * xqq;
             }
           }
         }
@@ -1039,7 +1062,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
   }
 
   if (tid == 0) *nsweeps_out = sweep;
-  for (int i = tid; i < r; i += 1024) evals[i] = A[packed_row(i, r) + i];
+  for (int i = tid; i < r; i += 1024) evals[i] = i == 0 ? Z[n1] : S[(i - 1) * L];
 }
 
 // Replays the logged rotations on rows of the identity: one warp per row of
@@ -1152,8 +1175,10 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
 }
 }  // namespace
 
-size_t jacobi_smem(int r) { return r <= WSSR_SMEM_RANK_MAX ? sizeof(float) * (size_t)r * (r + 1) / 2 : 0; }
-int64_t jacobi_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : (int64_t)r * (r + 1) / 2; }
+// the ring part (r - 1) x L (L = r / 2 rounded up to 32), row 0 and a_00
+static int64_t jacobi_floats(int r) { return (int64_t)(r - 1) * ((r / 2 + 31) / 32 * 32) + r; }
+size_t jacobi_smem(int r) { return r <= WSSR_SMEM_RANK_MAX ? sizeof(float) * (size_t)jacobi_floats(r) : 0; }
+int64_t jacobi_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : jacobi_floats(r); }
 // rotation log: max_sweeps x (r - 1) rounds x r/2 (c, s) pairs, then one int per round
 int64_t jacobi_log_elems(int r, int max_sweeps) {
   return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + 1) / 2;
