@@ -311,6 +311,10 @@ __device__ __forceinline__ void strip(const float* L, const float* Rm, int i0, i
 // The blocks live in shared memory up to r = WSSR_SMEM_RANK_MAX, above it in
 // the device workspace gws (same layout; the CTA's accesses stay coherent
 // across __syncthreads).
+// GWS: the blocks live in gws; otherwise in shared memory, where the pointer's
+// address space is known at compile time (shared-memory loads and stores
+// instead of generic ones).
+template <bool GWS>
 __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int r,
                                                    float* __restrict__ T, int* status,
                                                    int* shift_count, float* __restrict__ gws) {
@@ -318,7 +322,8 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
   const int nb = (r + CB - 1) / CB;
   const int nblk = nb * (nb + 1) / 2;
   double* d = reinterpret_cast<double*>(smem_raw);                               // r doubles
-  float* B = gws ? gws : reinterpret_cast<float*>(smem_raw + (size_t)r * sizeof(double));  // nblk blocks
+  // (the workspace instantiation keeps a run-time choice: its generic accesses compile without spills)
+  float* B = (GWS && gws) ? gws : reinterpret_cast<float*>(smem_raw + (size_t)r * sizeof(double));  // nblk blocks
   float* TMP = B + (size_t)nblk * CBE;                                           // nb - 1 blocks
   float* TKK = TMP + (size_t)(nb - 1 > 0 ? nb - 1 : 1) * CBE;                     // nb blocks
   __shared__ int flag;
@@ -500,12 +505,17 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
   static bool attr_set = false;
   if (!attr_set) {
     // the largest request (r = WSSR_SMEM_RANK_MAX); the kernel also has a few bytes of static shared memory
-    if (cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_chol_inv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_chol_inv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_inv_smem(WSSR_RANK_MAX)) != cudaSuccess)
       return;  // the error stays pending and is reported by the caller's launch check
     attr_set = true;
   }
-  k_chol_inv<<<1, 1024, sm, st>>>(G, r, T, status, shift_count, r <= WSSR_SMEM_RANK_MAX ? nullptr : ws);
+  if (r <= WSSR_SMEM_RANK_MAX)
+    k_chol_inv<false><<<1, 1024, sm, st>>>(G, r, T, status, shift_count, nullptr);
+  else
+    k_chol_inv<true><<<1, 1024, sm, st>>>(G, r, T, status, shift_count, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -951,12 +961,13 @@ __device__ __forceinline__ int skew_at(int u, int v, int n1, int h, int L) {
 // lanes walk J. Blocks whose two pairs are both idle are skipped. The matrix
 // lives in shared memory up to r = WSSR_SMEM_RANK_MAX, else in the device
 // workspace gA (same layout).
+template <bool GWS>
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
                                                  float2* __restrict__ rot_log, int* nsweeps_out,
                                                  float* __restrict__ evals, int* status, float* __restrict__ gA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int h = r / 2, n1 = r - 1, L = jacobi_lds(h);
-  float* S = gA ? gA : reinterpret_cast<float*>(smem_raw);
+  float* S = GWS ? gA : reinterpret_cast<float*>(smem_raw);
   float* Z = S + (size_t)n1 * L;  // row 0: Z[u], u = 0..n1-1; a_00 = Z[n1]
   __shared__ float2 tab[WSSR_RANK_MAX / 2];  // {c, s}
   __shared__ float tabt[WSSR_RANK_MAX / 2];  // t = tan(theta)
@@ -1188,11 +1199,14 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
                    float* evals, int* status, cudaStream_t st, float* ws) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  k_jacobi<<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals,
-                                            status, r <= WSSR_SMEM_RANK_MAX ? nullptr : ws);
+  if (r <= WSSR_SMEM_RANK_MAX)
+    k_jacobi<false><<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals, status,
+                                                     nullptr);
+  else
+    k_jacobi<true><<<1, 1024, 0, st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals, status, ws);
 }
 
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
