@@ -986,11 +986,13 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
     }
   }
   __syncthreads();
+  int* rank_of = round_nact + max_sweeps * n1;
   if (bad) {
     if (tid == 0) {
       set_status(status, WSSR_ERR_NONFINITE);
       *nsweeps_out = 0;
     }
+    for (int i = tid; i < r; i += 1024) rank_of[i] = i;
     return;
   }
   // this warp's block rows: 32 t + w for t even and 32 t + 31 - w for t odd
@@ -1073,22 +1075,38 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
   }
 
   if (tid == 0) *nsweeps_out = sweep;
-  for (int i = tid; i < r; i += 1024) evals[i] = i == 0 ? Z[n1] : S[(i - 1) * L];
+  // eigenvalues, and their ranks (descending, ties by index) for the replay's column order
+  __shared__ float lam[WSSR_RANK_MAX];
+  for (int i = tid; i < r; i += 1024) {
+    lam[i] = i == 0 ? Z[n1] : S[(i - 1) * L];
+    evals[i] = lam[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += 1024) {
+    const float li = lam[i];
+    int rk = 0;
+    for (int j = 0; j < r; ++j) {
+      const float lj = lam[j];
+      rk += (lj > li) || (lj == li && j < i);
+    }
+    rank_of[i] = rk;
+  }
 }
 
-// Replays the logged rotations on rows of the identity: one warp per row of
-// W (JV_WARPS rows per CTA), each row in shared memory, rounds separated by
-// __syncwarp only (the r/2 rotations of a round touch disjoint columns).
-// The CTA stages the log through shared memory in chunks of up to JV_CHUNK rounds
-// with double-buffered cp.async, so the L2 latency of the next chunk overlaps
-// the rotations of the current one. A lane follows its pairs' indices from
+// Replays the logged rotations on rows of the identity (W <- W J per round;
+// every row of W is an independent chain): one CTA of JV_THREADS threads per
+// row, held in shared memory; thread t takes the pairs t, t + JV_THREADS, ...
+// of every round and a CTA barrier separates rounds. The CTA stages the log
+// through shared memory in chunks of up to JV_CHUNK rounds with double-
+// buffered cp.async, so the L2 latency of the next chunk overlaps the
+// rotations of the current one. A thread follows its pairs' indices from
 // round to round incrementally (each advances by one on the ring of r - 1).
 // Idle rounds and idle pairs are skipped. Then writes W with columns sorted
-// by descending eigenvalue.
+// by descending eigenvalue (ranks from k_jacobi).
 constexpr int JV_CHUNK = 16;     // most rounds staged at once
 constexpr int JV_STAGE = 2048;   // (c, s) pairs per staging buffer: rounds per chunk = min(16, 2048 / (r/2))
-constexpr int JV_WARPS = 4;
-constexpr int JV_M = WSSR_RANK_MAX / 64;  // pairs per lane (r/2 pairs over 32 lanes)
+constexpr int JV_THREADS = 128;
+constexpr int JV_M = WSSR_RANK_MAX / 2 / JV_THREADS;  // pairs per thread
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
@@ -1099,47 +1117,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* __restrict__ rot_log,
-                                                                  const int* __restrict__ nsweeps,
-                                                                  const float* __restrict__ evals, int r,
-                                                                  int max_sweeps, float* __restrict__ W) {
+__global__ void __launch_bounds__(JV_THREADS) k_jacobi_vectors(const float2* __restrict__ rot_log,
+                                                               const int* __restrict__ nsweeps, int r,
+                                                               int max_sweeps, float* __restrict__ W) {
   __shared__ __align__(16) float2 stage[2][JV_STAGE];
   __shared__ int stage_cnt[2][JV_CHUNK];
-  __shared__ int rank_of[WSSR_RANK_MAX];
-  extern __shared__ float wr_all[];  // JV_WARPS rows of W, r floats each
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row = blockIdx.x * JV_WARPS + warp;
+  __shared__ float wr[WSSR_RANK_MAX];  // this CTA's row of W
+  const int tid = threadIdx.x;
+  const int row = blockIdx.x;
   const int h = r / 2, n1 = r - 1;
   const int chunk = JV_STAGE / h < JV_CHUNK ? JV_STAGE / h : JV_CHUNK;
-  const int mcount = (h + 31) / 32;
-  float* wr = wr_all + (size_t)warp * r;
-  for (int i = tid; i < r; i += 32 * JV_WARPS) {
-    const float li = evals[i];
-    int rk = 0;
-    for (int j = 0; j < r; ++j) {
-      const float lj = evals[j];
-      rk += (lj > li) || (lj == li && j < i);
-    }
-    rank_of[i] = rk;
-  }
-  for (int c = lane; c < r; c += 32) wr[c] = (c == row) ? 1.f : 0.f;
+  for (int c = tid; c < r; c += JV_THREADS) wr[c] = (c == row) ? 1.f : 0.f;
   const int total = nsweeps[0] * n1;
   const int* round_nact = reinterpret_cast<const int*>(rot_log + (int64_t)max_sweeps * n1 * h);
+  const int* rank_of = round_nact + max_sweeps * n1;
   const int nchunks = (total + chunk - 1) / chunk;
   auto issue = [&](int c) {
     const int t0 = c * chunk, nt = min(chunk, total - t0);
     const float2* src = rot_log + (int64_t)t0 * h;
     float2* dst = stage[c & 1];
-    for (int e = 2 * tid; e < nt * h; e += 64 * JV_WARPS) cp_async16(dst + e, src + e);
+    for (int e = 2 * tid; e < nt * h; e += 2 * JV_THREADS) cp_async16(dst + e, src + e);
     cp_async_commit();
     if (tid < JV_CHUNK) stage_cnt[c & 1][tid] = (tid < nt) ? round_nact[t0 + tid] : 0;
   };
-  // ring positions (index - 1) of this lane's pairs i = lane + 32 m in round 0;
-  // pair 0's first index is the fixed index 0
+  // ring positions (index - 1) of this thread's pairs i = tid + JV_THREADS m in
+  // round 0; pair 0's first index is the fixed index 0
   int pu[JV_M], qu[JV_M];
 #pragma unroll
   for (int m = 0; m < JV_M; ++m) {
-    const int i = lane + 32 * m;
+    const int i = tid + JV_THREADS * m;
     pu[m] = (i + n1 - 1) % n1;
     qu[m] = (r - 2 - i + n1) % n1;
   }
@@ -1152,37 +1158,37 @@ __global__ void __launch_bounds__(32 * JV_WARPS) k_jacobi_vectors(const float2* 
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int t0 = c * chunk, nt = min(chunk, total - t0);
+    const int nt = min(chunk, total - c * chunk);
     const float2* cs_chunk = stage[c & 1];
-    if (row < r) {
-      for (int j = 0; j < nt; ++j) {
-        if (stage_cnt[c & 1][j] != 0) {
-#pragma unroll
-          for (int m = 0; m < JV_M; ++m) {
-            const int i = lane + 32 * m;
-            if (m < mcount && i < h) {
-              const float2 cs = cs_chunk[j * h + i];
-              if (cs.y != 0.f) {
-                const int p = (i == 0) ? 0 : pu[m] + 1, q = qu[m] + 1;
-                const float wp = wr[p], wq = wr[q];
-                wr[p] = cs.x * wp - cs.y * wq;
-                wr[q] = cs.y * wp + cs.x * wq;
-              }
-            }
-          }
-          __syncwarp();
-        }
+    for (int j = 0; j < nt; ++j) {
+      if (stage_cnt[c & 1][j] != 0) {  // the same for the whole CTA
 #pragma unroll
         for (int m = 0; m < JV_M; ++m) {
-          pu[m] = pu[m] + 1 == n1 ? 0 : pu[m] + 1;
-          qu[m] = qu[m] + 1 == n1 ? 0 : qu[m] + 1;
+          const int i = tid + JV_THREADS * m;
+          if (i < h) {
+            const float2 cs = cs_chunk[j * h + i];
+            if (cs.y != 0.f) {
+              const int p = (i == 0) ? 0 : pu[m] + 1, q = qu[m] + 1;
+              const float wp = wr[p], wq = wr[q];
+              wr[p] = cs.x * wp - cs.y * wq;
+              wr[q] = cs.y * wp + cs.x * wq;
+            }
+          }
         }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int m = 0; m < JV_M; ++m) {
+        pu[m] = pu[m] + 1 == n1 ? 0 : pu[m] + 1;
+        qu[m] = qu[m] + 1 == n1 ? 0 : qu[m] + 1;
       }
     }
     __syncthreads();  // the stage just read is refilled by the next issue
   }
-  if (row < r)
-    for (int c = lane; c < r; c += 32) W[(int64_t)row * r + rank_of[c]] = wr[c];
+  for (int c = tid; c < r; c += JV_THREADS) {
+    const int rk = rank_of[c];
+    if (rk >= 0 && rk < r) W[(int64_t)row * r + rk] = wr[c];
+  }
 }
 }  // namespace
 
@@ -1191,8 +1197,9 @@ static int64_t jacobi_floats(int r) { return (int64_t)(r - 1) * ((r / 2 + 31) / 
 size_t jacobi_smem(int r) { return r <= WSSR_SMEM_RANK_MAX ? sizeof(float) * (size_t)jacobi_floats(r) : 0; }
 int64_t jacobi_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : jacobi_floats(r); }
 // rotation log: max_sweeps x (r - 1) rounds x r/2 (c, s) pairs, then one int per round
+// (its number of rotations) and the r eigenvalue ranks
 int64_t jacobi_log_elems(int r, int max_sweeps) {
-  return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + 1) / 2;
+  return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + r + 1) / 2;
 }
 
 void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
@@ -1209,16 +1216,9 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
     k_jacobi<true><<<1, 1024, 0, st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals, status, ws);
 }
 
-void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, const float* evals, int r,
-                           int max_sweeps, float* W, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(JV_WARPS * WSSR_RANK_MAX * sizeof(float)));
-    attr_set = true;
-  }
-  k_jacobi_vectors<<<(unsigned)ceil_div(r, JV_WARPS), 32 * JV_WARPS, JV_WARPS * r * sizeof(float), st>>>(
-      (const float2*)rot_log, nsweeps, evals, r, max_sweeps, W);
+void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int max_sweeps, float* W,
+                           cudaStream_t st) {
+  k_jacobi_vectors<<<(unsigned)r, JV_THREADS, 0, st>>>((const float2*)rot_log, nsweeps, r, max_sweeps, W);
 }
 
 // ---------------------------------------------------------------------------

@@ -363,7 +363,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
   launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st, h->jac_ws);
-  launch_jacobi_vectors(h->rot_log, h->nsweeps, h->evals, r, h->opt.jacobi_sweeps, h->W, st);
+  launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
   if (h->use_tc) {
