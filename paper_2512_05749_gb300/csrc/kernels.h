@@ -90,11 +90,9 @@ int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, flo
                    int* status, cudaStream_t st, int* splits_used);
 
 // V (M x r floats) = Xblk (K-blocked bf16) * TW, with TWT3 = three bf16 terms
-// (hi, mid, lo; each r x r, row n = column n of TW). If cpart != nullptr also
-// writes cpart[tile][n] = sum over the tile's 128 rows of V[m][n] g[m].
-int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, const float* g,
-                     double* cpart, int64_t wait_us, int* status, cudaStream_t st);
-int64_t tc_rotate_cpart_rows(int64_t M);
+// (hi, mid, lo; each r x r, row n = column n of TW). Persistent, one CTA per SM.
+int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, int64_t wait_us,
+                     int* status, cudaStream_t st);
 
 // ---- small / tall-skinny kernels (small_ops.cu) ----
 // TWT3[t][n][k] = t-th bf16 term of TW[k][n] (hi, mid, lo), r x r each.

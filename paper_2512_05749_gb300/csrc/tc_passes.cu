@@ -497,99 +497,163 @@ __global__ void __launch_bounds__(THREADS, 1)
 // 24 significant bits), so the product is FP32-accurate with exact bf16 A.
 // A tile: 128 parameters x 64 basis columns, MN-major (two 64-parameter
 // boxes of the blocked layout, 8 KB apart); B tiles: NB output columns x 64,
-// K-major. Optionally fuses cpart[tile][n] = sum over the tile's rows of
-// V[m][n] g[m] (the Woodbury c = V^T g without re-reading V).
+// K-major. Persistent: one CTA per SM walks the tiles (128 parameters x NB
+// columns, the column halves of a parameter tile back to back) with two TMEM
+// accumulators, so the epilogue of one tile overlaps the loads and MMAs of
+// the next: producer -> stage ring -> MMA -> tfull[b] -> epilogue -> tempty[b].
 // ---------------------------------------------------------------------------
+struct RCtl {
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drained;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void rtimeout(RCtl* ctl, int* status) {
+  *(volatile int*)&ctl->abort = 1;
+  set_status(status, WSSR_ERR_DEVICE_TIMEOUT);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_rotate(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmHi,
                 const __grid_constant__ CUtensorMap tmMid, const __grid_constant__ CUtensorMap tmLo,
-                int64_t M, int r, int NB, int tmem_cols, int stages, float* __restrict__ V,
-                const float* __restrict__ g, double* __restrict__ cpart, uint64_t limit_ns, int* status) {
+                int64_t M, int r, int NB, int acc_cols, int stages, int n_halves, int64_t n_tiles,
+                float* __restrict__ V, uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t bbytes = (uint32_t)NB * BK * 2;
   const uint32_t stage_bytes = A_BYTES + 3 * bbytes;
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  RCtl* ctl = reinterpret_cast<RCtl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
-  const int n0 = blockIdx.y * NB;
   const int nk = (r + BK - 1) / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
-    mbar_init(&ctl->accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->tfull[b], 1);
+      mbar_init(&ctl->tempty[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&ctl->drained, 1);
     ctl->abort = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)tmem_cols);
+  if (warp == 1) tmem_alloc(&ctl->tmem, (uint32_t)(2 * acc_cols));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem;
+
   if (warp == 0) {
-    if (lane == 0)
-      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](int i, uint8_t* st, uint64_t* bar) {
-        const int k = i * BK;
-        tma_load_3d(st, &tmX, bar, 0, k, (int)(m0 >> 6));
-        tma_load_3d(st + 8192, &tmX, bar, 0, k, (int)(m0 >> 6) + 1);
-        tma_load_2d(st + A_BYTES, &tmHi, bar, k, n0);
-        tma_load_2d(st + A_BYTES + bbytes, &tmMid, bar, k, n0);
-        tma_load_2d(st + A_BYTES + 2 * bbytes, &tmLo, bar, k, n0);
-      });
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t m0 = (t / n_halves) * BM;
+        const int n0 = (int)(t % n_halves) * NB;
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % stages, u = it / stages;
+          if (u > 0 && !mbar_wait(&ctl->empty[s], (u - 1) & 1, limit_ns, &ctl->abort)) {
+            rtimeout(ctl, status);
+            ok = false;
+            break;
+          }
+          uint8_t* st = base + (size_t)s * stage_bytes;
+          uint64_t* bar = &ctl->full[s];
+          const int k = kk * BK;
+          mbar_expect_tx(bar, stage_bytes);
+          tma_load_3d(st, &tmX, bar, 0, k, (int)(m0 >> 6));
+          tma_load_3d(st + 8192, &tmX, bar, 0, k, (int)(m0 >> 6) + 1);
+          tma_load_2d(st + A_BYTES, &tmHi, bar, k, n0);
+          tma_load_2d(st + A_BYTES + bbytes, &tmMid, bar, k, n0);
+          tma_load_2d(st + A_BYTES + 2 * bbytes, &tmLo, bar, k, n0);
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA can exit
+        int no_abort = 0;
+        const int j0 = it > stages ? it - stages : 0;
+        for (int j = j0; j < it; ++j)
+          mbar_wait(&ctl->full[j % stages], (j / stages) & 1, limit_ns, (volatile int*)&no_abort);
+      }
+    }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = make_idesc(BM, NB, 1, 0);
-      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
-#pragma unroll
-        for (int kk = 0; kk < BK / UK; ++kk) {
-          const uint64_t da = smem_desc(sa + kk * 2048, 8192, 1024);
-          for (int t = 0; t < 3; ++t)
-            mma_bf16(tmem, da, smem_desc(sa + A_BYTES + t * bbytes + kk * 32, 16, 1024), idesc,
-                     (!first || kk > 0 || t > 0) ? 1u : 0u);
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tl) {
+        const int b = tl & 1, ub = tl >> 1;
+        if (ub > 0 && !mbar_wait(&ctl->tempty[b], (ub - 1) & 1, limit_ns, &ctl->abort)) {
+          rtimeout(ctl, status);
+          break;
         }
-      });
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * acc_cols);
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % stages, u = it / stages;
+          if (!mbar_wait(&ctl->full[s], u & 1, limit_ns, &ctl->abort)) {
+            rtimeout(ctl, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = saddr(base + (size_t)s * stage_bytes);
+#pragma unroll
+          for (int k2 = 0; k2 < BK / UK; ++k2) {
+            const uint64_t da = smem_desc(sa + k2 * 2048, 8192, 1024);
+            for (int q = 0; q < 3; ++q)
+              mma_bf16(acc, da, smem_desc(sa + A_BYTES + q * bbytes + k2 * 32, 16, 1024), idesc,
+                       (kk > 0 || k2 > 0 || q > 0) ? 1u : 0u);
+          }
+          mma_commit(&ctl->empty[s]);
+        }
+        if (ok) mma_commit(&ctl->tfull[b]);
+      }
+      // every MMA issued above has completed before TMEM can be freed
+      mma_commit(&ctl->drained);
+      int no_abort = 0;
+      mbar_wait(&ctl->drained, 0, limit_ns, (volatile int*)&no_abort);
     }
   } else {
-    const int q = warp & 3, et = threadIdx.x - 64;
-    const bool ok = mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
-    if (!ok) timeout(ctl, status);
-    tc_fence_after();
-    const int row = q * 32 + lane;
-    const int64_t m = m0 + row;
-    const float gm = (g && m < M) ? g[m] : 0.f;
-    for (int c = 0; c < NB; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-      if (ok && m < M) {
-        float* out = V + m * r + n0;
-#pragma unroll
-        for (int i = 0; i < 16; i += 4)
-          if (n0 + c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    const int q = warp & 3;
+    int tl = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tl) {
+      const int b = tl & 1, ub = tl >> 1;
+      // the warp decides together: tcgen05.ld below needs all 32 lanes
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[b], ub & 1, limit_ns, &ctl->abort));
+      if (!ok) {
+        if (lane == 0) rtimeout(ctl, status);
+        break;
       }
-      if (cpart) {
-        // column sums of V * g over the tile's 128 rows: warp shuffle, then smem
+      tc_fence_after();
+      const int64_t m = (t / n_halves) * BM + q * 32 + lane;
+      const int n0 = (int)(t % n_halves) * NB;
+      const uint32_t acc = tmem + (uint32_t)(b * acc_cols) + ((uint32_t)(q * 32) << 16);
+      for (int c = 0; c < NB; c += 16) {
+        float v[16];
+        tmem_ld16(acc + (uint32_t)c, v);
+        if (m < M) {
+          float* out = V + m * r + n0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float x = (ok && m < M) ? v[i] * gm : 0.f;
-          x = warp_sum(x);
-          if (lane == 0) ctl->red[q][c + i] = (double)x;  // red[4][128] used as [warp][column]
+          for (int i = 0; i < 16; i += 4)
+            if (n0 + c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
       }
-    }
-    if (cpart) {
-      epi_bar();
-      for (int n = et; n < NB; n += 128)
-        if (n0 + n < r)
-          cpart[(int64_t)blockIdx.x * r + n0 + n] = ((ctl->red[0][n] + ctl->red[1][n]) + ctl->red[2][n]) + ctl->red[3][n];
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->tempty[b]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, (uint32_t)tmem_cols);
+    tmem_dealloc(tmem, (uint32_t)(2 * acc_cols));
   }
 }
 
@@ -822,13 +886,14 @@ int tc_xgram_launch(const void* XA, const void* XB, int64_t L, int r, int splits
   return gram_launch_impl(XA, XB, L, r, splits, Gp, wait_us, status, st, splits_used);
 }
 
-int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, const float* g,
-                     double* cpart, int64_t wait_us, int* status, cudaStream_t st) {
+int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, int64_t wait_us,
+                     int* status, cudaStream_t st) {
   const int nmma = nmma_for(r);
   const int NB = nmma <= 128 ? nmma : 128;
+  const int acc_cols = tmem_cols_for(NB);  // two accumulators: 2 acc_cols <= 256 TMEM columns
   const uint32_t bbytes = (uint32_t)NB * BK * 2;
   const size_t stage = A_BYTES + 3 * (size_t)bbytes;
-  size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+  size_t stages = (227 * 1024 - 1024 - sizeof(RCtl)) / stage;
   if (stages > 4) stages = 4;
   const bf16* T3 = reinterpret_cast<const bf16*>(TWT3);
   CUtensorMap tmX, tmHi, tmMid, tmLo;
@@ -838,18 +903,23 @@ int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float
     if (!encode_2d(mp, T3 + (size_t)t * r * r, (uint64_t)r, (uint64_t)r, (uint64_t)r * 2, BK, (uint32_t)NB, true))
       return -1;
   }
-  const size_t smem = 1024 + stages * stage + sizeof(Ctl);
+  const size_t smem = 1024 + stages * stage + sizeof(RCtl);
   static bool attr = false;
+  static int num_sms = 0;
   if (!attr) {
     cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (num_sms < 1) num_sms = 1;
     attr = true;
   }
-  dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(nmma, NB));
-  k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, M, r, NB, tmem_cols_for(NB), (int)stages,
-                                           V, g, cpart, (uint64_t)wait_us * 1000ull, status);
+  const int n_halves = (int)ceil_div(nmma, NB);
+  const int64_t n_tiles = ceil_div(M, BM) * n_halves;
+  const unsigned grid = (unsigned)(n_tiles < num_sms ? n_tiles : num_sms);
+  k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, M, r, NB, acc_cols, (int)stages, n_halves,
+                                           n_tiles, V, (uint64_t)wait_us * 1000ull, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
-
-int64_t tc_rotate_cpart_rows(int64_t M) { return ceil_div(M, BM); }
 
 }  // namespace wssr

@@ -76,7 +76,6 @@ struct wssr_ctx {
   float* chol_ws = nullptr;       // r x r factor blocks above the shared-memory rank
   float* jac_ws = nullptr;        // packed Jacobi matrix above the shared-memory rank
   void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
-  double* cpart = nullptr;        // per-tile partials of V^T g fused into the rotation
   bool c_ready = false;           // h->c already holds V_out^T g
   void* Vhp = nullptr;            // history averaging: bf16 K-blocked copy of V_prev
   float* wE = nullptr;            // VMC gradient weights 2 (E - mean E) / N (N floats)
@@ -111,7 +110,7 @@ void free_all(wssr_ctx* h) {
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->cpart, h->Vhp, h->gbar, h->wE, h->wE_sum,
+                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->Vhp, h->gbar, h->wE, h->wE_sum,
                   h->chol_ws, h->jac_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -302,7 +301,7 @@ void history_pass_B_term(wssr_ctx* h, const Hist* hist, const float* Q, cudaStre
   const int r = h->r;
   launch_scale_rows_r(Q + h->N * r, r, hist->sigma_prev, hist->gamma, r, h->TW, st);
   launch_split3_T(h->TW, r, h->TWT3, st);
-  tc_rotate_launch(h->Vhp, h->M, r, h->TWT3, h->Z, nullptr, nullptr, h->opt.wait_cap, h->status, st);
+  tc_rotate_launch(h->Vhp, h->M, r, h->TWT3, h->Z, h->opt.wait_cap, h->status, st);
   h->launches += 3;
 }
 
@@ -371,7 +370,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     // bandwidth-bound pass: fusing its column sums into this epilogue costs
     // more warp shuffles than re-reading V_out)
     launch_split3_T(h->TW, r, h->TWT3, st);
-    if (tc_rotate_launch(Xop, M, r, h->TWT3, V_out, nullptr, nullptr, h->opt.wait_cap, h->status, st) != 0)
+    if (tc_rotate_launch(Xop, M, r, h->TWT3, V_out, h->opt.wait_cap, h->status, st) != 0)
       return WSSR_ERR_UNSUPPORTED;
     h->launches += 2;
   } else {
@@ -591,7 +590,6 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
     h->gram_splits_tc = tc_gram_splits(M, h->num_sms);
     ALLOC(tc_gram_part, (size_t)h->gram_splits_tc * r * r * f);
     ALLOC(TWT3, (size_t)3 * r * r * 2);
-    ALLOC(cpart, (size_t)tc_rotate_cpart_rows(M) * r * d);
     if (opt.history) {
       ALLOC(Vhp, (size_t)blk_elems(M, r) * 2);
       ALLOC(gbar, (size_t)M * f);
