@@ -472,6 +472,11 @@ def run_ours(args, w):
         g_host = [g.cpu().pin_memory() for g in gs[:args.e2e_steps]]
         d_host = torch.empty(step.result(delta, Vb).shape, pin_memory=True)
         s_host = torch.empty(w.r, dtype=torch.float64, pin_memory=True)
+        host_call = args.path == "step" and args.history == 0
+        if host_call:
+            # untimed: the first host-buffer call allocates its two device input slots
+            s.step_host(O_host, g_host[0], V, Vb, d_host, s_host, stream=stream)
+            V, Vb = Vb, V
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -479,12 +484,19 @@ def run_ours(args, w):
         e3 = torch.cuda.Event(enable_timing=True)
         e2.record(stream)
         for t in range(args.e2e_steps):
-            O.copy_(O_host, non_blocking=True)
-            gs[t].copy_(g_host[t], non_blocking=True)
-            step(O, gs[t], V, delta, sigma, Vb)
+            if host_call:
+                # the C-ABI host-buffer step: copies O and g in, delta and sigma out; the
+                # next step's input copy overlaps this step's compute
+                nxt = t + 1 < args.e2e_steps
+                s.step_host(O_host, g_host[t], V, Vb, d_host, s_host, O_next=O_host if nxt else None,
+                            g_next=g_host[t + 1] if nxt else None, stream=stream)
+            else:
+                O.copy_(O_host, non_blocking=True)
+                gs[t].copy_(g_host[t], non_blocking=True)
+                step(O, gs[t], V, delta, sigma, Vb)
+                d_host.copy_(step.result(delta, Vb), non_blocking=True)
+                s_host.copy_(sigma, non_blocking=True)
             V, Vb = Vb, V
-            d_host.copy_(step.result(delta, Vb), non_blocking=True)
-            s_host.copy_(sigma, non_blocking=True)
         e3.record(stream)
         torch.cuda.synchronize()
         s.check("e2e")

@@ -149,6 +149,30 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g,
                       const float* V_prev, float* delta, double* sigma, float* V_out,
                       wssr_stream_t stream);
 
+/* wssr_step from host memory (dense operator; the step itself is Section 4.2
+ * Algorithm 1 + Eq. (updated_sr_1) as in wssr_step).
+ *   O_host       N x ld elements of options.dtype, host memory (page-locked for
+ *                the copy to run asynchronously); ld >= M
+ *   g_host       M floats, host
+ *   O_next_host, g_next_host   optional (both or neither): the next step's
+ *                inputs. Their copy into the handle's second device slot starts
+ *                on the handle's copy stream while this step computes; the next
+ *                call that passes the same two pointers as O_host / g_host uses
+ *                that slot without copying again. The host buffers must not
+ *                change until the copy has run (until the next call returns is
+ *                not enough: until the stream work of that call completes).
+ *   V_prev, V_out  M x r floats, device (the subspace stays on the device)
+ *   delta_host   out, M floats, host; sigma_host out, r doubles, host
+ * Copies of this step's inputs (unless prefetched), the step and the copies of
+ * delta and sigma back are enqueued on `stream`'s order; the results are in
+ * the host buffers once `stream` has completed (wssr_sync). The first call
+ * allocates two device slots of N * ld elements plus M + r_cap values and a
+ * copy stream (freed by wssr_destroy; re-allocated when ld changes);
+ * WSSR_ERR_OOM if they do not fit. */
+wssr_status wssr_step_host(wssr_handle h, const void* O_host, int64_t ld, const float* g_host,
+                           const void* O_next_host, const float* g_next_host, const float* V_prev, float* V_out,
+                           float* delta_host, double* sigma_host, wssr_stream_t stream);
+
 /* Randomized sketching SVD (Appendix A, Eq. (randsvd); the paper's RSSR and
  * a cold start in place of wssr_init_subspace): the sketch Y = O_c^T Omega
  * of a caller-supplied block Omega over the samples (N x r floats, device,

@@ -85,6 +85,22 @@ struct wssr_ctx {
   float* gbar = nullptr;          // history averaging: the averaged gradient (M)
   int gram_splits_tc = 1;
 
+  // wssr_step_host: two device slots for a step's inputs (O, g), the host
+  // buffers each slot was filled from, a copy stream and its events
+  struct HostFeed {
+    bool ready = false;
+    void* O[2] = {nullptr, nullptr};
+    float* g[2] = {nullptr, nullptr};
+    const void* O_src[2] = {nullptr, nullptr};
+    const float* g_src[2] = {nullptr, nullptr};
+    float* delta = nullptr;
+    double* sigma = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t filled[2] = {nullptr, nullptr};
+    cudaEvent_t used[2] = {nullptr, nullptr};
+    int64_t bytes_O = 0;
+  } feed;
+
   // profiling: event pairs around kernel groups
   bool prof = false;
   struct Mark {
@@ -106,7 +122,22 @@ cudaError_t dalloc(P** p, size_t bytes) {
   return cudaMalloc((void**)p, bytes < 256 ? 256 : bytes);
 }
 
+void free_feed(wssr_ctx* h) {
+  auto& f = h->feed;
+  for (int i = 0; i < 2; ++i) {
+    if (f.O[i]) cudaFree(f.O[i]);
+    if (f.g[i]) cudaFree(f.g[i]);
+    if (f.filled[i]) cudaEventDestroy(f.filled[i]);
+    if (f.used[i]) cudaEventDestroy(f.used[i]);
+  }
+  if (f.delta) cudaFree(f.delta);
+  if (f.sigma) cudaFree(f.sigma);
+  if (f.cs) cudaStreamDestroy(f.cs);
+  f = wssr_ctx::HostFeed{};
+}
+
 void free_all(wssr_ctx* h) {
+  free_feed(h);
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
                   h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
@@ -624,6 +655,74 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g, st)) != WSSR_OK) return s;
   return woodbury(h, V_out, sigma, g, delta, st);
+}
+
+wssr_status wssr_step_host(wssr_handle h, const void* O_host, int64_t ld, const float* g_host,
+                           const void* O_next_host, const float* g_next_host, const float* V_prev, float* V_out,
+                           float* delta_host, double* sigma_host, wssr_stream_t stream) {
+  if (!h || !O_host || !g_host || !V_prev || !V_out || !delta_host || !sigma_host) return WSSR_ERR_INVALID_ARG;
+  if (ld < h->M || (O_next_host && !g_next_host)) return WSSR_ERR_INVALID_ARG;
+  const size_t esz = is_bf16(h) ? 2 : 4;
+  const int64_t bytes_O = h->N * ld * (int64_t)esz;
+  auto& f = h->feed;
+  if (f.ready && f.bytes_O != bytes_O) free_feed(h);  // the row pitch changed
+  if (!f.ready) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaMalloc(&f.O[i], (size_t)bytes_O);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&f.g[i], (size_t)h->M * sizeof(float));
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.filled[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.used[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&f.delta, (size_t)h->M * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&f.sigma, (size_t)h->r_cap * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_feed(h);
+      return e == cudaErrorMemoryAllocation ? WSSR_ERR_OOM : WSSR_ERR_CUDA;
+    }
+    f.bytes_O = bytes_O;
+    f.ready = true;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // fill slot i from host buffers on the copy stream, after the last step that read slot i
+  auto fill = [&](int i, const void* Oh, const float* gh) -> bool {
+    if (cudaStreamWaitEvent(f.cs, f.used[i], 0) != cudaSuccess) return false;
+    if (cudaMemcpyAsync(f.O[i], Oh, (size_t)bytes_O, cudaMemcpyHostToDevice, f.cs) != cudaSuccess) return false;
+    if (cudaMemcpyAsync(f.g[i], gh, (size_t)h->M * sizeof(float), cudaMemcpyHostToDevice, f.cs) != cudaSuccess)
+      return false;
+    if (cudaEventRecord(f.filled[i], f.cs) != cudaSuccess) return false;
+    f.O_src[i] = Oh;
+    f.g_src[i] = gh;
+    return true;
+  };
+  // this step's slot: the one a previous call prefetched these buffers into, else fill one now
+  int s = -1;
+  for (int i = 0; i < 2; ++i)
+    if (f.O_src[i] == O_host && f.g_src[i] == g_host) s = i;
+  if (s < 0) {
+    s = f.O_src[0] ? 1 : 0;
+    if (!fill(s, O_host, g_host)) return WSSR_ERR_CUDA;
+  }
+  // the next step's inputs go into the other slot while this step computes
+  if (O_next_host && !fill(1 - s, O_next_host, g_next_host)) return WSSR_ERR_CUDA;
+  if (cudaStreamWaitEvent(st, f.filled[s], 0) != cudaSuccess) return WSSR_ERR_CUDA;
+  wssr_operator op{};
+  op.kind = WSSR_OP_DENSE;
+  op.O = f.O[s];
+  op.ld = ld;
+  wssr_status rs = wssr_step(h, &op, f.g[s], V_prev, f.delta, f.sigma, V_out, stream);
+  f.O_src[s] = nullptr;  // consumed: a later call with the same buffers copies them again
+  f.g_src[s] = nullptr;
+  if (cudaEventRecord(f.used[s], st) != cudaSuccess) return WSSR_ERR_CUDA;
+  if (rs != WSSR_OK) return rs;
+  if (cudaMemcpyAsync(delta_host, f.delta, (size_t)h->M * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(sigma_host, f.sigma, (size_t)h->r * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
+    return WSSR_ERR_CUDA;
+  return WSSR_OK;
 }
 
 wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const float* g, const float* V_prev,

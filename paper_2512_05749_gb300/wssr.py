@@ -43,7 +43,7 @@ EXPORTED = [
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
     "wssr_step_local_energy", "wssr_randomized_svd", "wssr_set_rank", "wssr_get_rank", "wssr_rank_next",
-    "wssr_extend_basis", "wssr_get_engine",
+    "wssr_extend_basis", "wssr_get_engine", "wssr_step_host",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -127,6 +127,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_default_options": (None, [P(wssr_options)]),
         "wssr_create": (i32, [i64, i64, i32, f64, P(wssr_options), P(vp)]),
         "wssr_step": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp]),
+        "wssr_step_host": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "wssr_init_subspace": (i32, [vp, P(wssr_operator), vp, vp, vp, vp]),
         "wssr_step_averaged": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, vp]),
         "wssr_step_local_energy": (i32, [vp, P(wssr_operator), vp, vp, vp, vp, vp, vp, vp]),
@@ -224,6 +225,13 @@ def wssr_create(N: int, M: int, r: int, lam: float, opt: Optional[wssr_options] 
 def wssr_step(h: int, op: wssr_operator, g, V_prev, delta, sigma, V_out, stream=None):
     _check(load().wssr_step(h, ctypes.byref(op), _ptr(g), _ptr(V_prev), _ptr(delta), _ptr(sigma),
                             _ptr(V_out), _stream(stream)), "wssr_step")
+
+
+def wssr_step_host(h: int, O_host, ld: int, g_host, O_next_host, g_next_host, V_prev, V_out, delta_host, sigma_host,
+                   stream=None):
+    _check(load().wssr_step_host(h, _ptr(O_host), int(ld), _ptr(g_host), _ptr(O_next_host), _ptr(g_next_host),
+                                 _ptr(V_prev), _ptr(V_out), _ptr(delta_host), _ptr(sigma_host), _stream(stream)),
+           "wssr_step_host")
 
 
 def wssr_step_averaged(h: int, op: wssr_operator, g, V_prev, sigma_prev, Lbar_prev, weight: float, delta, sigma,
@@ -451,6 +459,30 @@ class WSSR:
             delta, sigma, V = out
         wssr_step(self.handle, self._op(O), g, V_prev, delta, sigma, V, stream)
         return delta, sigma, V
+
+    def step_host(self, O_host, g_host, V_prev, V_out, delta_host, sigma_host, O_next=None, g_next=None,
+                  stream=None):
+        """Step from host (CPU, preferably pinned) tensors O_host (N x ld) and g_host (M);
+        delta_host (M floats) and sigma_host (r doubles) are host outputs, V_prev / V_out
+        stay on the device. O_next / g_next (host) start the next step's input copy
+        while this step computes. Results are valid after the stream completes."""
+        import torch
+        want = torch.bfloat16 if self.dtype == "bf16" else torch.float32
+        for name, t in (("O_host", O_host), ("O_next", O_next)):
+            if t is not None and (t.is_cuda or t.dtype != want or t.stride(1) != 1 or t.shape[0] != self.N
+                                  or t.stride(0) != O_host.stride(0)):
+                raise ValueError(f"{name} must be a host {want} tensor of shape ({self.N}, >= {self.M}) "
+                                 "with unit column stride and the row pitch of O_host")
+        for name, t in (("g_host", g_host), ("g_next", g_next), ("delta_host", delta_host)):
+            if t is not None and (t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous host float32 tensor")
+        if sigma_host.is_cuda or sigma_host.dtype != torch.float64:
+            raise ValueError("sigma_host must be a host float64 tensor")
+        if (O_next is None) != (g_next is None):
+            raise ValueError("O_next and g_next go together")
+        wssr_step_host(self.handle, O_host, O_host.stride(0), g_host, O_next, g_next, V_prev, V_out, delta_host,
+                       sigma_host, stream)
+        return delta_host, sigma_host, V_out
 
     def step_local_energy(self, O, E_loc, V_prev, out=None, stream=None):
         """Step with the VMC gradient formed from the local energies (Eq. (gradient:vmc)):
