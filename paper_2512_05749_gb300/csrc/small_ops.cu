@@ -1250,8 +1250,10 @@ void launch_split3_T(const float* TW, int r, void* TWT3, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 namespace {
 int dot_nb(int64_t M) {
-  int64_t nb = ceil_div(M, 2048);
-  if (nb > 512) nb = 512;
+  // enough CTAs (8 per SM on 152 SMs, 256 threads each) and rows in flight per
+  // thread to keep HBM busy on the M x r read
+  int64_t nb = ceil_div(M, 512);
+  if (nb > 1216) nb = 1216;
   if (nb < 1) nb = 1;
   return (int)nb;
 }
@@ -1263,15 +1265,22 @@ __global__ void k_dot_part(const float* __restrict__ V, const float* __restrict_
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     double s64 = 0.0;
     int64_t m = mb;
-    // 8 rows in flight per thread; FP32 partial sums over 64 rows, then FP64
+    // 16 rows in flight per thread; FP32 partial sums over 64 rows, then FP64
     while (m < me) {
       const int64_t mend = m + 64 < me ? m + 64 : me;
-      float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (; m + 8 <= mend; m += 8) {
+      float a[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = fmaf(V[(m + u) * r + j], g[m + u], a[u]);
+      for (int u = 0; u < 16; ++u) a[u] = 0.f;
+      for (; m + 16 <= mend; m += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = __ldcs(V + (m + u) * r + j);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) a[u] = fmaf(v[u], g[m + u], a[u]);
       }
       for (; m < mend; ++m) a[0] = fmaf(V[m * r + j], g[m], a[0]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += a[u + 8];
       s64 += (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
     }
     part[(int64_t)blockIdx.x * r + j] = s64;

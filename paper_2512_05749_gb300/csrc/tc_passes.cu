@@ -502,6 +502,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // accumulators, so the epilogue of one tile overlaps the loads and MMAs of
 // the next: producer -> stage ring -> MMA -> tfull[b] -> epilogue -> tempty[b].
 // ---------------------------------------------------------------------------
+constexpr uint32_t ROT_STAGING_BYTES = 2 * BM * 32 * 4;  // two 128 x 32 FP32 boxes
+
 struct RCtl {
   uint64_t full[MAX_STAGES];
   uint64_t empty[MAX_STAGES];
@@ -520,13 +522,15 @@ __device__ __forceinline__ void rtimeout(RCtl* ctl, int* status) {
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_rotate(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmHi,
                 const __grid_constant__ CUtensorMap tmMid, const __grid_constant__ CUtensorMap tmLo,
-                int64_t M, int r, int NB, int acc_cols, int stages, int n_halves, int64_t n_tiles,
-                float* __restrict__ V, uint64_t limit_ns, int* status) {
+                const __grid_constant__ CUtensorMap tmV, int64_t M, int r, int NB, int acc_cols, int stages,
+                int n_halves, int64_t n_tiles, uint64_t limit_ns, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t bbytes = (uint32_t)NB * BK * 2;
   const uint32_t stage_bytes = A_BYTES + 3 * bbytes;
-  RCtl* ctl = reinterpret_cast<RCtl*>(base + (size_t)stages * stage_bytes);
+  // two 128 x 32 FP32 staging boxes of the epilogue (128-byte swizzle), then the barriers
+  float* stg = reinterpret_cast<float*>(base + (size_t)stages * stage_bytes);
+  RCtl* ctl = reinterpret_cast<RCtl*>(base + (size_t)stages * stage_bytes + ROT_STAGING_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (r + BK - 1) / BK;
   if (threadIdx.x == 0) {
@@ -620,34 +624,55 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(&ctl->drained, 0, limit_ns, (volatile int*)&no_abort);
     }
   } else {
-    const int q = warp & 3;
-    int tl = 0;
+    // Epilogue: TMEM -> registers -> a swizzled 128 x 32 staging box -> one TMA
+    // store per 32 columns (coalesced full lines; rows >= M and columns >= r are
+    // clipped by the tensor map). Two boxes alternate: before a box is rewritten
+    // the store issued from it two boxes earlier must have read it.
+    const int q = warp & 3, et = threadIdx.x - 64;
+    const int row = q * 32 + lane;
+    int tl = 0, nbox = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tl) {
       const int b = tl & 1, ub = tl >> 1;
-      // the warp decides together: tcgen05.ld below needs all 32 lanes
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ctl->tfull[b], ub & 1, limit_ns, &ctl->abort));
+      // all 128 epilogue threads decide together: the named barriers below need every one
+      const bool ok = epi_bar_and(mbar_wait(&ctl->tfull[b], ub & 1, limit_ns, &ctl->abort));
       if (!ok) {
-        if (lane == 0) rtimeout(ctl, status);
+        if (et == 0) rtimeout(ctl, status);
         break;
       }
       tc_fence_after();
-      const int64_t m = (t / n_halves) * BM + q * 32 + lane;
+      const int m0 = (int)((t / n_halves) * BM);
       const int n0 = (int)(t % n_halves) * NB;
       const uint32_t acc = tmem + (uint32_t)(b * acc_cols) + ((uint32_t)(q * 32) << 16);
-      for (int c = 0; c < NB; c += 16) {
-        float v[16];
-        tmem_ld16(acc + (uint32_t)c, v);
-        if (m < M) {
-          float* out = V + m * r + n0;
+      for (int c = 0; c < NB; c += 32, ++nbox) {
+        float* box = stg + (nbox & 1) * (BM * 32);
+        if (nbox >= 2) {
+          if (et == 0) bulk_wait_read<1>();
+          epi_bar();
+        }
 #pragma unroll
-          for (int i = 0; i < 16; i += 4)
-            if (n0 + c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        for (int h2 = 0; h2 < 32; h2 += 16) {
+          if (c + h2 < NB) {
+            float v[16];
+            tmem_ld16(acc + (uint32_t)(c + h2), v);
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+              const int chunk = ((h2 + i) >> 2) ^ (row & 7);
+              *reinterpret_cast<float4*>(box + row * 32 + chunk * 4) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+          }
+        }
+        fence_smem_to_async();
+        epi_bar();
+        if (et == 0) {
+          tma_store_2d(&tmV, box, n0 + c, m0);
+          bulk_commit_group();
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->tempty[b]);
     }
+    if (et == 0) bulk_wait_done();
   }
   tc_fence_before();
   __syncthreads();
@@ -711,6 +736,20 @@ bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, ui
 
 // 3D bf16 tensor map of a K-blocked operand (blk_index): dims {64, r, blocks},
 // box {64, box_rows, 1}: one box = box_rows contiguous 128-byte rows.
+// 2D FP32 tensor map with 128-byte swizzle (box_inner * 4 <= 128 bytes).
+bool encode_2d_f32(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+                   uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(g), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_blocked(CUtensorMap* m, const void* g, int64_t L, int r, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -893,17 +932,19 @@ int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float
   const int acc_cols = tmem_cols_for(NB);  // two accumulators: 2 acc_cols <= 256 TMEM columns
   const uint32_t bbytes = (uint32_t)NB * BK * 2;
   const size_t stage = A_BYTES + 3 * (size_t)bbytes;
-  size_t stages = (227 * 1024 - 1024 - sizeof(RCtl)) / stage;
+  size_t stages = (227 * 1024 - 1024 - ROT_STAGING_BYTES - sizeof(RCtl)) / stage;
   if (stages > 4) stages = 4;
+  if (((uintptr_t)V & 15) != 0) return -1;  // TMA stores need a 16-byte aligned base
   const bf16* T3 = reinterpret_cast<const bf16*>(TWT3);
-  CUtensorMap tmX, tmHi, tmMid, tmLo;
+  CUtensorMap tmX, tmHi, tmMid, tmLo, tmV;
   if (!encode_blocked(&tmX, Xblk, M, r, 64)) return -1;
+  if (!encode_2d_f32(&tmV, V, (uint64_t)r, (uint64_t)M, (uint64_t)r * 4, 32, BM)) return -1;
   for (int t = 0; t < 3; ++t) {
     CUtensorMap* mp = t == 0 ? &tmHi : (t == 1 ? &tmMid : &tmLo);
     if (!encode_2d(mp, T3 + (size_t)t * r * r, (uint64_t)r, (uint64_t)r, (uint64_t)r * 2, BK, (uint32_t)NB, true))
       return -1;
   }
-  const size_t smem = 1024 + stages * stage + sizeof(RCtl);
+  const size_t smem = 1024 + stages * stage + ROT_STAGING_BYTES + sizeof(RCtl);
   static bool attr = false;
   static int num_sms = 0;
   if (!attr) {
@@ -917,8 +958,8 @@ int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float
   const int n_halves = (int)ceil_div(nmma, NB);
   const int64_t n_tiles = ceil_div(M, BM) * n_halves;
   const unsigned grid = (unsigned)(n_tiles < num_sms ? n_tiles : num_sms);
-  k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, M, r, NB, acc_cols, (int)stages, n_halves,
-                                           n_tiles, V, (uint64_t)wait_us * 1000ull, status);
+  k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, tmV, M, r, NB, acc_cols, (int)stages, n_halves,
+                                           n_tiles, (uint64_t)wait_us * 1000ull, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
