@@ -288,9 +288,12 @@ namespace {
 //             trailing update A_IJ -= R_KI^T R_KJ run as strip GEMMs on all
 //             threads;
 //   inverse:  block rows from the bottom, T_IJ = -T_II sum_{K=I+1..J} R_IK T_KJ.
-// Upper-triangle blocks are stored packed, each 32 x 33 floats; a partial last
-// block is padded with the identity (the Gram is equilibrated to unit diagonal).
-constexpr int CB = 32, CBP = 33, CBE = CB * CBP;
+// Upper-triangle blocks are stored packed, each 32 x 32 floats (rows of 128
+// bytes: every access either runs along a row across the lanes or is a
+// broadcast, so no padding is needed and the strips load 16-byte vectors); a
+// partial last block is padded with the identity (the Gram is equilibrated to
+// unit diagonal).
+constexpr int CB = 32, CBP = 32, CBE = CB * CBP;
 
 __device__ __forceinline__ int blk_id(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
 
@@ -300,11 +303,32 @@ template <bool LT>
 __device__ __forceinline__ void strip(const float* L, const float* Rm, int i0, int c, float (&acc)[8]) {
 #pragma unroll
   for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+  if (LT) {
+    // L(k, i0 .. i0 + 7) is one 32-byte run of row k: two broadcast float4 loads
 #pragma unroll 8
-  for (int k = 0; k < CB; ++k) {
-    const float x = Rm[k * CBP + c];
+    for (int k = 0; k < CB; ++k) {
+      const float x = Rm[k * CBP + c];
+      const float4 l0 = *reinterpret_cast<const float4*>(L + k * CBP + i0);
+      const float4 l1 = *reinterpret_cast<const float4*>(L + k * CBP + i0 + 4);
+      const float l[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = fmaf(LT ? L[k * CBP + i0 + t] : L[(i0 + t) * CBP + k], x, acc[t]);
+      for (int t = 0; t < 8; ++t) acc[t] = fmaf(l[t], x, acc[t]);
+    }
+  } else {
+    // L[i0 + t][k .. k + 3]: one broadcast float4 per row and 4 values of k
+#pragma unroll 2
+    for (int k = 0; k < CB; k += 4) {
+      const float x0 = Rm[k * CBP + c], x1 = Rm[(k + 1) * CBP + c];
+      const float x2 = Rm[(k + 2) * CBP + c], x3 = Rm[(k + 3) * CBP + c];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float4 l = *reinterpret_cast<const float4*>(L + (i0 + t) * CBP + k);
+        acc[t] = fmaf(l.x, x0, acc[t]);
+        acc[t] = fmaf(l.y, x1, acc[t]);
+        acc[t] = fmaf(l.z, x2, acc[t]);
+        acc[t] = fmaf(l.w, x3, acc[t]);
+      }
+    }
   }
 }
 

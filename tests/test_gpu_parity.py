@@ -241,7 +241,12 @@ def test_step_cutoff_mode(W):
 
 
 @pytest.mark.parametrize("engine", ENGINES_BF16)
-@pytest.mark.parametrize("N,M,r", [(1024, 2048, 32), (1000, 2040, 24), (512, 4096, 128)])
+@pytest.mark.parametrize("N,M,r", [(1024, 2048, 32), (1000, 2040, 24), (512, 4096, 128),
+                                   # ragged tiles of the basis rotation: r = 40 (a 48-column
+                                   # accumulator, its second 32-column store box clipped at r),
+                                   # r = 136 (two column halves, the second clipped at r), and
+                                   # M not a multiple of the 128-parameter tile
+                                   (700, 1992, 40), (1100, 2056, 136)])
 def test_step_bf16(W, engine, N, M, r):
     skip_if_no_tc(W, engine)
     w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.2, noise=1e-4, lam=1e-4, dtype="bf16")
