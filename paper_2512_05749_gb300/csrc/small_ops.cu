@@ -367,22 +367,34 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     const float shift = attempt ? 1e-5f : 0.f;
-    // load the equilibrated upper blocks; identity padding beyond r
-    for (int e = tid; e < nblk * CB * CB; e += 1024) {
-      const int bidx = e / (CB * CB), w = e % (CB * CB), i = w / CB, c = w % CB;
-      int I = 0, rem = bidx;
-      while (rem >= nb - I) rem -= nb - I, ++I;
-      const int J = I + rem;
-      const int gi = I * CB + i, gj = J * CB + c;
-      float v;
-      if (gi < r && gj < r) {
-        const double g = G[(int64_t)gi * r + gj];
-        if (!isfinite(g)) flag = 2;
-        v = (float)g * (float)d[gi] * (float)d[gj] + (gi == gj ? shift : 0.f);
-      } else {
-        v = (gi == gj) ? 1.f : 0.f;
+    // load the equilibrated upper blocks; identity padding beyond r. Thread
+    // tid owns element (tid / 32, tid % 32) of every block; the blocks are
+    // walked in packed order four at a time, their four loads issued together.
+    {
+      const int i = tid / CB, c = tid % CB;
+      int I = 0, J = 0;
+      for (int b0 = 0; b0 < nblk; b0 += 4) {
+        double gv[4];
+        int gi[4], gj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          gi[u] = I * CB + i, gj[u] = J * CB + c;
+          gv[u] = (b0 + u < nblk && gi[u] < r && gj[u] < r) ? G[(int64_t)gi[u] * r + gj[u]] : 0.0;
+          if (++J == nb) J = ++I;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (b0 + u >= nblk) break;
+          float v;
+          if (gi[u] < r && gj[u] < r) {
+            if (!isfinite(gv[u])) flag = 2;
+            v = (float)gv[u] * (float)d[gi[u]] * (float)d[gj[u]] + (gi[u] == gj[u] ? shift : 0.f);
+          } else {
+            v = (gi[u] == gj[u]) ? 1.f : 0.f;
+          }
+          B[(b0 + u) * CBE + i * CBP + c] = v;
+        }
       }
-      B[bidx * CBE + i * CBP + c] = v;
     }
     __syncthreads();
     if (flag == 2) break;
@@ -499,11 +511,17 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
     }
     __syncthreads();
   }
-  // T = D T' (rows scaled by d_i), full r x r with zeros below the diagonal
-  for (int e = tid; e < r * r; e += 1024) {
-    const int i = e / r, j = e % r;
-    const int I = i / CB, J = j / CB;
-    T[e] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + (i % CB) * CBP + (j % CB)] * (float)d[i] : 0.f;
+  // T = D T' (rows scaled by d_i), full r x r with zeros below the diagonal;
+  // rows over warps, columns over lanes (column j of a row sits in block j / 32
+  // at position j % 32 = lane)
+  for (int i = warp; i < r; i += 32) {
+    const float di = (float)d[i];
+    const int I = i / CB, ii = i % CB;
+    float* Trow = T + (int64_t)i * r;
+    for (int j = lane; j < r; j += 32) {
+      const int J = j / CB;
+      Trow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + ii * CBP + lane] * di : 0.f;
+    }
   }
 }
 }  // namespace
