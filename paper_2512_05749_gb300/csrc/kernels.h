@@ -137,13 +137,13 @@ void launch_sum_partials(const float* Gp, int S, int r, double scale, double* G,
 void launch_cast(const float* X, int64_t L, int r, void* out_rowmajor, int to_bf16, void* out_T,
                  int64_t ldT, double* colsum_part, cudaStream_t st);
 // Symmetric eigensolve of H (FP64 r x r) by FP32 cyclic Jacobi on one CTA.
-// Writes the rotation log, the eigenvalues and their ranks; launch_jacobi_vectors
-// builds the sorted W.
+// Writes the rotation log and the eigenvalue ranks; launch_jacobi_vectors
+// builds the sorted W (the Ritz values come from FP64 Rayleigh quotients).
 size_t jacobi_smem(int r);
 int64_t jacobi_ws_floats(int r);  // device workspace of the matrix above WSSR_SMEM_RANK_MAX
 int64_t jacobi_log_elems(int r, int max_sweeps);
-void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
-                   float* evals, int* status, cudaStream_t st, float* ws = nullptr);
+void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps, int* status,
+                   cudaStream_t st, float* ws = nullptr);
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int max_sweeps, float* W,
                            cudaStream_t st);
 // c = V^T g (FP64), M x r V.

@@ -1005,8 +1005,8 @@ __device__ __forceinline__ int skew_at(int u, int v, int n1, int h, int L) {
 // workspace gA (same layout).
 template <bool GWS>
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, int r, int max_sweeps,
-                                                 float2* __restrict__ rot_log, int* nsweeps_out,
-                                                 float* __restrict__ evals, int* status, float* __restrict__ gA) {
+                                                 float2* __restrict__ rot_log, int* nsweeps_out, int* status,
+                                                 float* __restrict__ gA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int h = r / 2, n1 = r - 1, L = jacobi_lds(h);
   float* S = GWS ? gA : reinterpret_cast<float*>(smem_raw);
@@ -1117,12 +1117,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ H, i
   }
 
   if (tid == 0) *nsweeps_out = sweep;
-  // eigenvalues, and their ranks (descending, ties by index) for the replay's column order
+  // ranks of the eigenvalues (descending, ties by index): the replay's column order
   __shared__ float lam[WSSR_RANK_MAX];
-  for (int i = tid; i < r; i += 1024) {
-    lam[i] = i == 0 ? Z[n1] : S[(i - 1) * L];
-    evals[i] = lam[i];
-  }
+  for (int i = tid; i < r; i += 1024) lam[i] = i == 0 ? Z[n1] : S[(i - 1) * L];
   __syncthreads();
   for (int i = tid; i < r; i += 1024) {
     const float li = lam[i];
@@ -1244,18 +1241,18 @@ int64_t jacobi_log_elems(int r, int max_sweeps) {
   return (int64_t)max_sweeps * (r - 1) * (r / 2) + ((int64_t)max_sweeps * (r - 1) + r + 1) / 2;
 }
 
-void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps,
-                   float* evals, int* status, cudaStream_t st, float* ws) {
+void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* nsweeps, int* status,
+                   cudaStream_t st, float* ws) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   if (r <= WSSR_SMEM_RANK_MAX)
-    k_jacobi<false><<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals, status,
+    k_jacobi<false><<<1, 1024, jacobi_smem(r), st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, status,
                                                      nullptr);
   else
-    k_jacobi<true><<<1, 1024, 0, st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, evals, status, ws);
+    k_jacobi<true><<<1, 1024, 0, st>>>(H, r, max_sweeps, (float2*)rot_log, nsweeps, status, ws);
 }
 
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int max_sweeps, float* W,

@@ -63,7 +63,6 @@ struct wssr_ctx {
   float* T = nullptr;
   float* rot_log = nullptr;
   int* nsweeps = nullptr;
-  float* evals = nullptr;
   float* W = nullptr;
   double* Hp = nullptr;
   double* c = nullptr;
@@ -140,7 +139,7 @@ void free_all(wssr_ctx* h) {
   free_feed(h);
   void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
                   h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
-                  h->rot_log, h->nsweeps, h->evals, h->W, h->Hp, h->c, h->e, h->dot_part,
+                  h->rot_log, h->nsweeps, h->W, h->Hp, h->c, h->e, h->dot_part,
                   h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->Vhp, h->gbar, h->wE, h->wE_sum,
                   h->chol_ws, h->jac_ws};
   for (void* p : ptrs)
@@ -392,7 +391,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   right_multiply_Y(h, h->Y, h->TX, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
-  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->evals, h->status, st, h->jac_ws);
+  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->status, st, h->jac_ws);
   launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
@@ -606,7 +605,6 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(T, (size_t)r * r * f);
   ALLOC(rot_log, (size_t)jacobi_log_elems(r, opt.jacobi_sweeps) * 2 * f);
   ALLOC(nsweeps, sizeof(int));
-  ALLOC(evals, (size_t)r * f);
   ALLOC(W, (size_t)r * r * f);
   ALLOC(Hp, (size_t)r * r * d);
   ALLOC(c, (size_t)r * d);
