@@ -275,6 +275,14 @@ wssr_status wssr_woodbury_noalloc(const float* V, const double* sigma, const flo
  * status; also surfaces asynchronous CUDA errors as WSSR_ERR_CUDA. */
 wssr_status wssr_sync(wssr_handle h);
 
+/* Failure-detection self-test (no paper counterpart): enqueue one device wait
+ * on a barrier that nothing completes, bounded by wait_us microseconds of GPU
+ * time (0 <= wait_us <= 10^7), through the same bounded wait every pipeline
+ * kernel uses. When the bound runs out the kernel records
+ * WSSR_ERR_DEVICE_TIMEOUT in the handle's status word and returns, so the
+ * next wssr_sync reports it and the context stays usable. */
+wssr_status wssr_selftest_wait(wssr_handle h, int64_t wait_us, wssr_stream_t stream);
+
 /* Read the sticky device status after the caller synchronised the stream. */
 wssr_status wssr_get_status(wssr_handle h);
 

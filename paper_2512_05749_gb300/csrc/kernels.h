@@ -91,6 +91,9 @@ int tc_gram_launch(const void* XT, int64_t ld, int64_t L, int r, int splits, flo
 
 // V (M x r floats) = Xblk (K-blocked bf16) * TW, with TWT3 = three bf16 terms
 // (hi, mid, lo; each r x r, row n = column n of TW). Persistent, one CTA per SM.
+// One bounded device wait that nothing completes: records WSSR_ERR_DEVICE_TIMEOUT
+// in *status after wait_us microseconds of GPU time.
+int wait_selftest_launch(int64_t wait_us, int* status, cudaStream_t st);
 int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float* V, int64_t wait_us,
                      int* status, cudaStream_t st);
 

@@ -683,6 +683,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Bounded-wait self-test: one thread waits on an mbarrier that nothing
+// arrives at, through the same bounded wait the pipelines use; when the
+// bound runs out it records WSSR_ERR_DEVICE_TIMEOUT and returns. Nothing is
+// in flight, so the kernel always ends and the context stays usable.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(uint64_t limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  abort_flag = 0;
+  fence_barrier_init();
+  if (!mbar_wait(&bar, 0, limit_ns, &abort_flag)) set_status(status, WSSR_ERR_DEVICE_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 int nmma_for(int r) { return (r + 15) / 16 * 16; }
@@ -960,6 +976,11 @@ int tc_rotate_launch(const void* Xblk, int64_t M, int r, const void* TWT3, float
   const unsigned grid = (unsigned)(n_tiles < num_sms ? n_tiles : num_sms);
   k_tc_rotate<<<grid, THREADS, smem, st>>>(tmX, tmHi, tmMid, tmLo, tmV, M, r, NB, acc_cols, (int)stages, n_halves,
                                            n_tiles, (uint64_t)wait_us * 1000ull, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+}
+
+int wait_selftest_launch(int64_t wait_us, int* status, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)wait_us * 1000ull, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -914,6 +914,13 @@ wssr_status wssr_get_status(wssr_handle h) {
   return (wssr_status)s;
 }
 
+wssr_status wssr_selftest_wait(wssr_handle h, int64_t wait_us, wssr_stream_t stream) {
+  if (!h || wait_us < 0 || wait_us > 10000000) return WSSR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return wait_selftest_launch(wait_us, h->status, st) == 0 ? WSSR_OK : WSSR_ERR_CUDA;
+}
+
 wssr_status wssr_sync(wssr_handle h) {
   if (!h) return WSSR_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return WSSR_ERR_CUDA;

@@ -43,7 +43,7 @@ EXPORTED = [
     "wssr_mlp_create", "wssr_mlp_destroy", "wssr_mlp_forward", "wssr_mlp_jacobian", "wssr_mlp_vjp",
     "wssr_mlp_padded_count", "wssr_mlp_pad", "wssr_mlp_unpad", "wssr_step_averaged",
     "wssr_step_local_energy", "wssr_randomized_svd", "wssr_set_rank", "wssr_get_rank", "wssr_rank_next",
-    "wssr_extend_basis", "wssr_get_engine", "wssr_step_host",
+    "wssr_extend_basis", "wssr_get_engine", "wssr_step_host", "wssr_selftest_wait",
 ]
 
 WSSR_MLP_MAX_LAYERS = 8
@@ -137,6 +137,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "wssr_orthonormalize": (i32, [vp, vp, i64, i32, vp]),
         "wssr_woodbury": (i32, [vp, vp, vp, vp, vp, vp]),
         "wssr_sync": (i32, [vp]),
+        "wssr_selftest_wait": (i32, [vp, i64, vp]),
         "wssr_get_status": (i32, [vp]),
         "wssr_last_launch_count": (i64, [vp]),
         "wssr_destroy": (None, [vp]),
@@ -232,6 +233,10 @@ def wssr_step_host(h: int, O_host, ld: int, g_host, O_next_host, g_next_host, V_
     _check(load().wssr_step_host(h, _ptr(O_host), int(ld), _ptr(g_host), _ptr(O_next_host), _ptr(g_next_host),
                                  _ptr(V_prev), _ptr(V_out), _ptr(delta_host), _ptr(sigma_host), _stream(stream)),
            "wssr_step_host")
+
+
+def wssr_selftest_wait(h: int, wait_us: int, stream=None):
+    _check(load().wssr_selftest_wait(h, int(wait_us), _stream(stream)), "wssr_selftest_wait")
 
 
 def wssr_step_averaged(h: int, op: wssr_operator, g, V_prev, sigma_prev, Lbar_prev, weight: float, delta, sigma,

@@ -313,6 +313,29 @@ def test_nonfinite_gradient_sets_status(W):
     s.close()
 
 
+def test_device_wait_timeout_is_reported(W):
+    """A device wait that nothing completes (a barrier no thread arrives at),
+    bounded at 2 ms of GPU time: the kernel records WSSR_ERR_DEVICE_TIMEOUT and
+    returns, the host reads it, and the same context then runs a clean step."""
+    import time
+    w = wl.small_planted(300, 520, 16, K=300)
+    O, Oex = make_O(w, "f32")
+    g = torch.from_numpy(wl.gradient_np(w.M, 0, "to").astype(np.float32)).to(dev())
+    Vp = torch.from_numpy(wl.orthonormal_np(w.M, w.r, "toV").astype(np.float32)).to(dev())
+    s = W.WSSR(w.N, w.M, w.r, w.lam)
+    t0 = time.perf_counter()
+    W.wssr_selftest_wait(s.handle, 2000)
+    assert s.sync() == W.WSSR_ERR_DEVICE_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert s.sync() == W.WSSR_OK  # read once, then cleared
+    s.step(O, g, Vp)
+    assert s.sync() == W.WSSR_OK
+    with pytest.raises(W.WSSRError) as ei:
+        W.wssr_selftest_wait(s.handle, -1)
+    assert ei.value.code == W.WSSR_ERR_INVALID_ARG
+    s.close()
+
+
 def test_rank_deficient_start_is_reported(W):
     w = wl.small_planted(300, 520, 16, K=300)
     O, Oex = make_O(w, "f32")
