@@ -73,7 +73,7 @@ struct wssr_ctx {
   float* TW = nullptr;         // r x r: TX W
   float* tc_gram_part = nullptr;  // tcgen05 Gram partials (splits x r x r)
   float* chol_ws = nullptr;       // r x r factor blocks above the shared-memory rank
-  float* jac_ws = nullptr;        // packed Jacobi matrix above the shared-memory rank
+  float* jac_ws = nullptr;        // Jacobi matrix (ring coordinates) above the shared-memory rank
   void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
   bool c_ready = false;           // h->c already holds V_out^T g
   void* Vhp = nullptr;            // history averaging: bf16 K-blocked copy of V_prev
