@@ -23,11 +23,13 @@
  *
  * Conventions for every entry point:
  *   - All array pointers are DEVICE pointers on the current CUDA device,
- *     owned by the caller; the library never frees them. Matrices are dense
- *     row-major. float = IEEE binary32, double = binary64, bf16 = bfloat16
- *     stored as uint16_t.
+ *     owned by the caller; the library never frees them. The one exception
+ *     is wssr_step_host, whose O, g, delta and sigma are host pointers.
+ *     Matrices are dense row-major. float = IEEE binary32, double =
+ *     binary64, bf16 = bfloat16 stored as uint16_t.
  *   - The library allocates device memory only in wssr_create (its
- *     workspace) and frees it in wssr_destroy.
+ *     workspace) and at the first wssr_step_host (its two input slots), and
+ *     frees it in wssr_destroy.
  *   - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t,
  *     0 = legacy default stream). A returned WSSR_OK only means that the
  *     work was validated and enqueued; device-side failures (Cholesky
