@@ -888,12 +888,19 @@ def main():
                     help="regulariser of the apply (damped, the paper's cutoff, truncated pseudo-inverse)")
     ap.add_argument("--sigma-floor", type=float, default=None,
                     help="cutoff: sigma_floor (default lambda); pinv: eps_tol (default 1e-5)")
+    ap.add_argument("--m", type=int, default=None,
+                    help="subspace iterations per step (default: the workload's, m = 2)")
     ap.add_argument("--materialise", action="store_true",
                     help="MLP workloads: form O with the per-sample Jacobian kernel instead of the "
                          "matrix-free operator")
     args = ap.parse_args()
     from synth import workloads as wl
     w = wl.WORKLOADS[args.workload]
+    if args.m is not None:
+        if args.m < 1:
+            raise SystemExit("--m must be >= 1")
+        import dataclasses
+        w = dataclasses.replace(w, m=args.m)
     if isinstance(w, wl.MLPWorkload):
         if args.path == "rssr" or (args.materialise and (args.path != "step" or args.history > 0)):
             raise SystemExit("the network workloads run --path step or local-energy (matrix-free)")
