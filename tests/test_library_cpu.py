@@ -75,6 +75,9 @@ def test_null_handle_calls_are_rejected():
     assert lib.wssr_sync(None) == W.WSSR_ERR_INVALID_ARG
     assert lib.wssr_step(None, None, None, None, None, None, None, None) == W.WSSR_ERR_INVALID_ARG
     assert lib.wssr_last_launch_count(None) == -1
+    assert lib.wssr_step_host(None, None, 0, None, None, None, None, None, None, None, None) == \
+        W.WSSR_ERR_INVALID_ARG
+    assert lib.wssr_selftest_wait(None, 1000, None) == W.WSSR_ERR_INVALID_ARG
     lib.wssr_destroy(None)
 
 
