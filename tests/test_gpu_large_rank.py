@@ -117,3 +117,41 @@ def test_adaptive_rank_grows_across_256():
             s.set_rank(r)
     assert seen == [(240, 240, 360), (360, 341, 360)], seen
     s.close()
+
+
+def test_step_at_the_maximum_rank_1024():
+    """r = 1024, the largest rank the context takes (SIMT engine; the r x r
+    factor and the eigensolve in the device workspace, 512 rotation pairs per
+    round, four per replay thread). The oracle's one-sided Jacobi SVD is too
+    slow at this rank, so the step is held to properties that fix it: an
+    orthonormal V, descending sigma equal to the FP64 Rayleigh quotients
+    sigma_i^2 = v_i^T S v_i of the returned basis, V^T S V diagonal (the
+    Rayleigh-Ritz finish), and delta equal to the apply of Eq.
+    (updated_sr_1) (damped reading) recomputed in FP64 from the returned V
+    and sigma."""
+    from paper_2512_05749_gb300 import WSSR
+    N, M, r = 1100, 1200, 1024
+    w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.0, noise=1e-4, lam=1e-3)
+    O = wl.planted_O_np(w).astype(np.float32)
+    Oc = O.astype(np.float64) - O.astype(np.float64).mean(axis=0)
+    V0 = wl.orthonormal_np(M, r, "max1024").astype(np.float32)
+    g = wl.gradient_np(M, 0, "max1024").astype(np.float32)
+    # a random start at this rank leaves H far from diagonal: allow more sweeps than the default 12
+    s = WSSR(N, M, r, w.lam, m=2, dtype="f32", engine="simt", jacobi_sweeps=24)
+    assert s.engine == "simt"
+    d, sg, Vo = s.step(t(O), t(g), t(V0))
+    s.check("step at r = 1024")
+    d = d.double().cpu().numpy()
+    sg = sg.cpu().numpy()
+    V = Vo.double().cpu().numpy()
+    assert np.abs(V.T @ V - np.eye(r)).max() <= 1e-4
+    assert np.all(np.diff(sg) <= 1e-12 * sg[0]) and sg[-1] >= 0
+    Y = Oc @ V
+    H = Y.T @ Y / N
+    rq = np.sqrt(np.clip(np.diag(H), 0, None))
+    assert np.max(np.abs(sg - rq)) <= 1e-4 * sg[0]
+    assert np.abs(H - np.diag(np.diag(H))).max() <= 1e-5 * H[0, 0]
+    c = V.T @ g.astype(np.float64)
+    dref = g / w.lam + V @ ((1.0 / (sg ** 2 + w.lam) - 1.0 / w.lam) * c)
+    assert np.linalg.norm(d - dref) / np.linalg.norm(dref) <= 1e-5
+    s.close()
