@@ -661,6 +661,8 @@ wssr_status wssr_step_host(wssr_handle h, const void* O_host, int64_t ld, const 
   if (!h || !O_host || !g_host || !V_prev || !V_out || !delta_host || !sigma_host) return WSSR_ERR_INVALID_ARG;
   if (ld < h->M || (O_next_host && !g_next_host)) return WSSR_ERR_INVALID_ARG;
   const size_t esz = is_bf16(h) ? 2 : 4;
+  // the row pitch the device step will accept (checked before any copy is enqueued)
+  if (h->use_tc && ((size_t)ld * esz) % 16 != 0) return WSSR_ERR_INVALID_ARG;
   const int64_t bytes_O = h->N * ld * (int64_t)esz;
   auto& f = h->feed;
   if (f.ready && f.bytes_O != bytes_O) free_feed(h);  // the row pitch changed
