@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "WSSR step ms & % roofline at N=16k,M=1M,r=256 BF16 vs FP32; rel err vs FP64"
 METRIC_RSSR = "randomized sketching SVD ms & % roofline at N=16k,M=1M,r=256 BF16"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# rated (nominal) GB300 figures, reported beside the measured denominators
+HBM_RATED_GBS = 7900.0
+BF16_RATED_TFLOPS = 2250.0
 # FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -60,6 +63,18 @@ def max_over_ranks(x: float) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_step_ms(elapsed_ms: float, steps: int) -> float:
+    """ms per step of the replicated job: every rank runs the whole step on its
+    own copy, so the job's step takes as long as the slowest replica's (the
+    time is NOT divided by the number of replicas)."""
+    return max_over_ranks(elapsed_ms) / steps
+
+
+def headline_fields(ms_step: float, world: int) -> dict:
+    """The value fields of the JSON line: the job's ms per step and the GPU count."""
+    return {"value": ms_step, "unit": "ms", "n_gpus": world, "ms_per_step": ms_step}
 
 
 class ClockSampler:
@@ -166,6 +181,68 @@ def time_oracle(w, cols: int):
                           f"{w.M} parameter columns ({t1:.1f} s, {t2:.1f} s), extrapolated linearly in M"}
 
 
+def accuracy_on_sample(w, args, dev, cols: int):
+    """The metric's "rel err vs FP64" part: one GPU step (the handle options the
+    bench times: same dtype, engine, m, lambda) and one FP64 oracle step on the
+    same inputs -- all N samples of the workload recipe and its first `cols`
+    parameter columns (the bf16 bytes the GPU consumes, exactly), a gradient
+    g ~ N(0, 1), and the GPU's own warm start (init_subspace, m_init
+    iterations) fed to both sides. Returns the errors and the oracle step's
+    measured wall time."""
+    import numpy as np
+    import torch
+
+    from oracle import wssr_oracle as orc
+    from paper_2512_05749_gb300 import WSSR
+    ws, O64, g64, V0 = cpu_sample(w, cols)
+    dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    O_t = torch.from_numpy(O64.astype(np.float32)).to(dev).to(dt)
+    s = WSSR(ws.N, cols, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine)
+    Vp, _ = s.init_subspace(O_t, torch.from_numpy(V0.astype(np.float32)).to(dev))
+    g_t = torch.from_numpy(g64.astype(np.float32)).to(dev)
+    d, sg, V = s.step(O_t, g_t, Vp)
+    s.check("accuracy sample step")
+    d, sg, V = d.double().cpu().numpy(), sg.cpu().numpy(), V.double().cpu().numpy()
+    Vp64 = Vp.double().cpu().numpy()
+    s.close()
+    t0 = time.perf_counter()
+    dr, sr, Vr = orc.wssr_step(O64, g64, Vp64, w.lam, w.m)
+    t_oracle = time.perf_counter() - t0
+    lr, lrr = d - g64 / w.lam, dr - g64 / w.lam
+    acc = {"delta_rel": float(np.linalg.norm(d - dr) / np.linalg.norm(dr)),
+           "delta_lr_rel": float(np.linalg.norm(lr - lrr) / np.linalg.norm(lrr)),
+           "sigma_max_rel": float(np.max(np.abs(sg - sr) / sr)),
+           "sigma_top16_max_rel": float(np.max(np.abs(sg[:16] - sr[:16]) / sr[:16])),
+           "projector": float(orc.projector_distance(V, Vr)),
+           "orthonormality": float(np.abs(V.T @ V - np.eye(w.r)).max()),
+           "sample": f"N={ws.N}, M={cols} (first {cols} of {w.M} parameter columns, same recipe), r={w.r}, "
+                     f"m={w.m}, lambda={w.lam}; O the {args.dtype} bytes the GPU consumes; GPU warm start "
+                     f"(init_subspace, m_init={args.m_init}) fed to both sides",
+           "delta_lr": "low-rank part delta - g/lambda"}
+    return acc, t_oracle
+
+
+def oracle_small_workload_ms(name="planted-n1024-m2048-r32"):
+    """One full FP64 oracle step, measured (not extrapolated), on the small
+    planted workload (N=1024, M=2048, r=32, m=2) from its converged subspace."""
+    import numpy as np
+
+    from oracle import wssr_oracle as orc
+    from synth import workloads as wl
+    ws = wl.WORKLOADS[name]
+    O = wl.planted_O_np(ws).astype(np.float32).astype(np.float64)
+    g = wl.gradient_np(ws.M, 0, "bench").astype(np.float32).astype(np.float64)
+    Vp = orc.init_subspace(O, wl.start_subspace_np(ws.M, ws.r, "bench"), m_init=10)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        orc.wssr_step(O, g, Vp, ws.lam, ws.m)
+        ts.append(time.perf_counter() - t0)
+    return {"workload": name, "N": ws.N, "M": ws.M, "r": ws.r, "m": ws.m,
+            "ms": 1e3 * sorted(ts)[1], "steps_timed": 3, "kind": "oracle, full step, measured",
+            "cores": os.cpu_count()}
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -229,7 +306,10 @@ def roofline_for(w, args, prof, steps, peaks, engine_name):
         peak = peaks["hbm_gbs"]
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "ms_per_launch": t,
-                "algorithmic_per_launch": bytes_O, "peak_source": "measured copy bandwidth"}
+                "algorithmic_per_launch": bytes_O, "peak_source": "measured copy bandwidth",
+                "headline": "frac (of the measured copy bandwidth)",
+                "peak_rated": HBM_RATED_GBS, "frac_rated": achieved / HBM_RATED_GBS,
+                "peak_rated_source": "GB300 nominal HBM3e bandwidth, 7.9 TB/s"}
     achieved = flops / (t * 1e-3) / 1e12
     peak = FP32_SIMT_PEAK_TFLOPS
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -463,7 +543,7 @@ def run_ours(args, w):
     prof = s.profile_end()
     s.check("timed steps")
     stats = s.stats()
-    ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    ms_step = replica_step_ms(e0.elapsed_time(e1), args.steps)
 
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
@@ -547,18 +627,26 @@ def run_ours(args, w):
         roof["traffic"] = measured_traffic(w, roof["kernel"])
     step_roof = step_roofline_ms(w, args, peaks, engine_name)
     s.close()
+    del O
+
+    accuracy = None
+    plain = args.path == "step" and args.history <= 0 and args.apply == "damped"
+    if rank == 0 and world == 1 and plain and args.accuracy_cols > 0:
+        accuracy, t_or = accuracy_on_sample(w, args, dev, args.accuracy_cols)
+        accuracy["oracle_step_s_measured"] = t_or
 
     if rank != 0:
         return
     cpu = None
-    if world == 1 and args.cpu_cols > 0 and args.path == "step" and args.history <= 0 and args.apply == "damped":
+    if world == 1 and args.cpu_cols > 0 and plain:
         ms, info = time_oracle(w, max(w.r, args.cpu_cols // 4))
         info["value"] = ms
         info["unit"] = "ms"
+        info["measured_full_step_small_workload"] = oracle_small_workload_ms()
         cpu = info
     line = {
-        "metric": METRIC if args.path != "rssr" else METRIC_RSSR, "value": ms_step / world, "unit": "ms", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "metric": METRIC if args.path != "rssr" else METRIC_RSSR, **headline_fields(ms_step, world),
+        "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic", "config": workload_config(w, args, engine_name),
         "clocks": clk, "e2e": e2e, "gpu_launches": launches,
@@ -570,6 +658,7 @@ def run_ours(args, w):
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
         "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
         "bf16_vs_fp32": compare,
+        "accuracy": accuracy,
         "cpu_baseline": cpu,
     }
     if args.path == "adaptive":
@@ -828,6 +917,9 @@ def run_mlp_mf(args, w):
     roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "ms_per_launch": t, "algorithmic_per_launch": flops,
             "peak_source": f"cuBLAS bf16 sustained ({src})",
+            "headline": "frac (of the measured sustained cuBLAS bf16 rate)",
+            "peak_rated": BF16_RATED_TFLOPS, "frac_rated": achieved / BF16_RATED_TFLOPS,
+            "peak_rated_source": "GB300 nominal dense BF16 tensor rate, 2.25 PFLOP/s",
             "other_product": {"ms_per_launch": tb if t == ta else ta,
                               "tflops": flops / ((tb if t == ta else ta) * 1e-3) / 1e12}}
     passes = 2 * w.m + 1
@@ -871,7 +963,10 @@ def main():
     ap.add_argument("--m-init", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-cols", type=int, default=2048)
-    ap.add_argument("--compare-f32", type=int, default=0,
+    ap.add_argument("--accuracy-cols", type=int, default=2048,
+                    help="parameter columns of the sample on which one GPU step is compared with the FP64 "
+                         "oracle (0 = skip)")
+    ap.add_argument("--compare-f32", type=int, default=2,
                     help="also time this many steps of the plain FP32 (SIMT) path on the FP32 master "
                          "of the same planted matrix and report the speedup and the delta difference")
     ap.add_argument("--history", type=float, default=0.0,

@@ -61,8 +61,19 @@ typedef enum {
   WSSR_ERR_NONFINITE = 4,      /* NaN/Inf met in O, g, V_prev or a small factor */
   WSSR_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait ran out (kernel returned early) */
   WSSR_ERR_CUDA = 6,           /* a CUDA runtime call failed */
-  WSSR_ERR_UNSUPPORTED = 7     /* feature not available for these options/shape */
+  WSSR_ERR_UNSUPPORTED = 7,    /* feature not available for these options/shape */
+  WSSR_ERR_BOUNDS = 8          /* bounds-checked build only (compiled with WSSR_CHECK_BOUNDS):
+                                  a kernel index or a tensor map left its buffer; the access
+                                  was skipped (device) or the launch not made (host) */
 } wssr_status;
+
+/* options.debug bits. WSSR_DEBUG_POISON fills the whole workspace with 0xFF
+ * bytes (a NaN in float, double and bf16) at wssr_create and at every
+ * wssr_set_rank, so that a kernel reading a workspace slot that nothing wrote
+ * yields NaN and shows up as WSSR_ERR_NONFINITE or a wrong result instead of
+ * depending on what the allocator handed out. For testing; costs one memset
+ * of the workspace per call of those two. */
+enum { WSSR_DEBUG_POISON = 1 };
 
 enum { WSSR_DTYPE_F32 = 0, WSSR_DTYPE_BF16 = 1 };
 /* DAMPED: [V diag(1/(sigma^2+lambda)) V^T + lambda^-1 (I - V V^T)] g.
@@ -89,7 +100,7 @@ typedef struct {
   int32_t engine;       /* WSSR_ENGINE_* (default AUTO) */
   int32_t jacobi_sweeps;/* max FP32 Jacobi sweeps of the Rayleigh-Ritz eigensolve (default 12) */
   int32_t history;      /* 1: allocate the workspace of wssr_step_averaged (tcgen05 engine) (default 0) */
-  int32_t reserved;     /* 0 */
+  int32_t debug;        /* WSSR_DEBUG_* bits (default 0) */
   double r_reg;         /* truncation ratio of Eq. (ruler) (Section 4.3), 0 <= r_reg <= 1 (default 0 = off):
                            the apply keeps the leading Ritz triplets with r_reg <= sigma_i^2 / sigma_1^2
                            (the paper's s_i are singular values of S = squares of sigma_i); the rest
@@ -256,14 +267,16 @@ wssr_status wssr_woodbury(wssr_handle h, const float* V, const double* sigma, co
  * memory (a caching allocator or a hard memory cap), or in latency-critical
  * loops where cudaMalloc/cudaFree, which can synchronise the whole device,
  * are not acceptable. It needs no handle and allocates nothing: its scratch
- * (FP64 partial sums of V^T g and the r coefficients, 1,052,672 bytes) is a
- * fixed device array inside the library, present on every GPU that loads it
+ * (FP64 partial sums of V^T g over at most 1216 row blocks, and the r values
+ * of V^T g and of the coefficients: 2,494,464 bytes) is a fixed device array
+ * inside the library, present on every GPU that loads it
  * until the process exits.
  *   V (M x r floats, orthonormal), sigma (r doubles), g (M floats), delta
  *   (out, M floats): device pointers; lambda > 0; apply_mode WSSR_APPLY_*;
  *   sigma_floor > 0 for WSSR_APPLY_CUTOFF.
- * Limits: 1 <= r <= 256 and M >= 1 (larger r returns WSSR_ERR_INVALID_ARG,
- * as do null pointers and bad modes). The first call on each device looks up
+ * Limits: 1 <= r <= 256 and any M >= 1 (a larger r returns
+ * WSSR_ERR_INVALID_ARG, as do null pointers, bad modes and a sigma_floor out
+ * of its mode's range). The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress, with that device
  * current); make that first call before any stream capture. All calls share
  * the one array: calls whose kernels overlap on the GPU (other streams, other

@@ -24,6 +24,31 @@ __device__ __forceinline__ void set_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Index guard of the bounds-checked build (compiled with -DWSSR_CHECK_BOUNDS):
+// an index outside [0, n) records WSSR_ERR_BOUNDS and the caller skips the
+// access. In the normal build the guard is the constant true.
+#ifdef WSSR_CHECK_BOUNDS
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int* status) {
+  if (i >= 0 && i < n) return true;
+  set_status(status, WSSR_ERR_BOUNDS);
+  return false;
+}
+#define WSSR_IN_BOUNDS(i, n, status) ::wssr::in_bounds((int64_t)(i), (int64_t)(n), (status))
+#else
+#define WSSR_IN_BOUNDS(i, n, status) true
+#endif
+
+// Host side of the bounds-checked build (wssr.cu): every workspace allocation
+// is registered with its size, and each tensor map is checked against the
+// allocation that contains its base address before it is used. Caller-owned
+// buffers are not registered and pass unchecked. A failed check is remembered
+// until bounds_take_error() reads it. In the normal build no allocation is
+// registered and every check passes.
+void bounds_register(const void* p, size_t bytes);
+void bounds_unregister(const void* p);
+bool bounds_check_extent(const void* base, size_t extent_bytes);
+bool bounds_take_error();
+
 template <typename T>
 __device__ __forceinline__ float to_f32(T v);
 template <>

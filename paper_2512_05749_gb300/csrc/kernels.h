@@ -149,7 +149,9 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
                    cudaStream_t st, float* ws = nullptr);
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int max_sweeps, float* W,
                            cudaStream_t st);
-// c = V^T g (FP64), M x r V.
+// c = V^T g (FP64), M x r V. The partial sums use at most DOT_MAX_BLOCKS row
+// blocks (8 CTAs per SM on 152 SMs), so dot_part_elems(M, r) <= DOT_MAX_BLOCKS * r.
+constexpr int DOT_MAX_BLOCKS = 1216;
 int64_t dot_part_elems(int64_t M, int r);
 void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, double* c,
                 cudaStream_t st);

@@ -28,12 +28,13 @@
 
 namespace {
 
-// Layout (doubles): [0, PART) partial sums of V^T g (up to 512 row blocks x
-// 256 columns), then c (256), then e (256).
+// Layout (doubles): [0, PART) partial sums of V^T g (up to DOT_MAX_BLOCKS =
+// 1216 row blocks x 256 columns: every M at r <= 256), then c (256), then e
+// (256); 2,494,464 bytes in all.
 constexpr int kMaxR = 256;
-constexpr int kMaxBlocks = 512;
-constexpr size_t kPartDoubles = (size_t)kMaxBlocks * kMaxR;
+constexpr size_t kPartDoubles = (size_t)wssr::DOT_MAX_BLOCKS * kMaxR;
 constexpr size_t kScratchDoubles = kPartDoubles + 2 * kMaxR;
+static_assert(kScratchDoubles * sizeof(double) == 2494464, "scratch size stated in include/wssr.h");
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -72,6 +73,7 @@ extern "C" wssr_status wssr_woodbury_noalloc(const float* V, const double* sigma
     return WSSR_ERR_INVALID_ARG;
   if (apply_mode == WSSR_APPLY_CUTOFF && !(sigma_floor > 0.0)) return WSSR_ERR_INVALID_ARG;
   if (apply_mode == WSSR_APPLY_PINV && !(sigma_floor > 0.0 && sigma_floor <= 1.0)) return WSSR_ERR_INVALID_ARG;
+  // holds for every M at r <= kMaxR (the row blocks are capped at DOT_MAX_BLOCKS)
   if (wssr::dot_part_elems(M, r) > (int64_t)kPartDoubles) return WSSR_ERR_INVALID_ARG;
   int dev = -1;
   double* base = scratch_for_current_device(&dev);

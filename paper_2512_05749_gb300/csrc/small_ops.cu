@@ -1292,7 +1292,7 @@ int dot_nb(int64_t M) {
   // enough CTAs (8 per SM on 152 SMs, 256 threads each) and rows in flight per
   // thread to keep HBM busy on the M x r read
   int64_t nb = ceil_div(M, 512);
-  if (nb > 1216) nb = 1216;
+  if (nb > DOT_MAX_BLOCKS) nb = DOT_MAX_BLOCKS;
   if (nb < 1) nb = 1;
   return (int)nb;
 }

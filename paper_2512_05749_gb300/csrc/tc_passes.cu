@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if ((ok || nk == 0) && n < N) {
 #pragma unroll
           for (int i = 0; i < 16; i += 4)
-            if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            if (c + i < r && WSSR_IN_BOUNDS(((int64_t)split * N + n) * r + c + i + 3, (int64_t)splits * N * r, status))
+              *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
       }
     }
@@ -385,13 +386,23 @@ __global__ void __launch_bounds__(THREADS, 1)
             // consecutive parameters (64 contiguous bytes)
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-              if (c + i < r) ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(v[i]);
+              if (c + i < r && WSSR_IN_BOUNDS(blk_index(m, c + i, r), blk_elems(M, r), status))
+                ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(v[i]);
           } else {
             float* out = Z + m * r;
 #pragma unroll
             for (int i = 0; i < 16; i += 4)
-              if (c + i < r) *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+              if (c + i < r && WSSR_IN_BOUNDS(m * r + c + i + 3, M * r, status))
+                *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
           }
+        } else if (ZT && m < ceil_div(M, 64) * 64) {
+          // rows past M inside the last 64-parameter block: the Gram, pass A
+          // and the rotation read whole blocks, so the padding must hold zeros
+          // (on the history path nothing else writes this buffer's padding)
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c + i < r && WSSR_IN_BOUNDS(blk_index(m, c + i, r), blk_elems(M, r), status))
+              ZT[blk_index(m, c + i, r)] = __float2bfloat16_rn(0.f);
         }
       }
     }
@@ -476,7 +487,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (i < r) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4)
-            if (c + j < r)
+            if (c + j < r && WSSR_IN_BOUNDS(((int64_t)split * r + i) * r + c + j + 3,
+                                            ceil_div(k_chunks, kc_per_split) * r * r, status))
               *reinterpret_cast<float4*>(out + c + j) =
                   ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -741,6 +753,9 @@ bool encode_2d(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer, ui
                uint32_t box_inner, uint32_t box_outer, bool swizzle) {
   auto fn = encode_fn();
   if (!fn) return false;
+#ifdef WSSR_CHECK_BOUNDS
+  if (!bounds_check_extent(g, (size_t)((outer - 1) * pitch_bytes + inner * 2))) return false;
+#endif
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {pitch_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
@@ -757,6 +772,9 @@ bool encode_2d_f32(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer
                    uint32_t box_inner, uint32_t box_outer) {
   auto fn = encode_fn();
   if (!fn) return false;
+#ifdef WSSR_CHECK_BOUNDS
+  if (!bounds_check_extent(g, (size_t)((outer - 1) * pitch_bytes + inner * 4))) return false;
+#endif
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {pitch_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
@@ -769,6 +787,9 @@ bool encode_2d_f32(CUtensorMap* m, const void* g, uint64_t inner, uint64_t outer
 bool encode_blocked(CUtensorMap* m, const void* g, int64_t L, int r, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
+#ifdef WSSR_CHECK_BOUNDS
+  if (!bounds_check_extent(g, (size_t)blk_elems(L, r) * 2)) return false;
+#endif
   cuuint64_t dims[3] = {64, (cuuint64_t)r, (cuuint64_t)ceil_div(L, 64)};
   cuuint64_t strides[2] = {128, (cuuint64_t)r * 128};
   cuuint32_t box[3] = {64, box_rows, 1};

@@ -20,6 +20,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -27,6 +29,43 @@
 #include "kernels.h"
 
 using namespace wssr;
+
+namespace wssr {
+namespace {
+std::mutex g_bounds_mu;
+std::map<uintptr_t, size_t> g_regions;  // workspace allocations: base -> bytes
+bool g_bounds_error = false;
+}  // namespace
+
+void bounds_register(const void* p, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_bounds_mu);
+  g_regions[(uintptr_t)p] = bytes;
+}
+
+void bounds_unregister(const void* p) {
+  std::lock_guard<std::mutex> lk(g_bounds_mu);
+  g_regions.erase((uintptr_t)p);
+}
+
+bool bounds_check_extent(const void* base, size_t extent_bytes) {
+  std::lock_guard<std::mutex> lk(g_bounds_mu);
+  const uintptr_t b = (uintptr_t)base;
+  auto it = g_regions.upper_bound(b);
+  if (it == g_regions.begin()) return true;  // not in the workspace: caller memory
+  --it;
+  if (b >= it->first + it->second) return true;
+  if (b + extent_bytes <= it->first + it->second) return true;
+  g_bounds_error = true;
+  return false;
+}
+
+bool bounds_take_error() {
+  std::lock_guard<std::mutex> lk(g_bounds_mu);
+  const bool e = g_bounds_error;
+  g_bounds_error = false;
+  return e;
+}
+}  // namespace wssr
 
 struct wssr_ctx {
   int64_t N = 0, M = 0;
@@ -83,6 +122,7 @@ struct wssr_ctx {
   float* fuse_g = nullptr;
   float* gbar = nullptr;          // history averaging: the averaged gradient (M)
   int gram_splits_tc = 1;
+  std::vector<std::pair<void*, size_t>> regions;  // every workspace allocation (poison, bounds registry)
 
   // wssr_step_host: two device slots for a step's inputs (O, g), the host
   // buffers each slot was filled from, a copy stream and its events
@@ -117,8 +157,14 @@ namespace {
 bool is_bf16(const wssr_ctx* h) { return h->opt.dtype == WSSR_DTYPE_BF16; }
 
 template <typename P>
-cudaError_t dalloc(P** p, size_t bytes) {
-  return cudaMalloc((void**)p, bytes < 256 ? 256 : bytes);
+cudaError_t dalloc(std::vector<std::pair<void*, size_t>>& regions, P** p, size_t bytes) {
+  if (bytes < 256) bytes = 256;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) {
+    regions.push_back({(void*)*p, bytes});
+    bounds_register(*p, bytes);
+  }
+  return e;
 }
 
 void free_feed(wssr_ctx* h) {
@@ -137,17 +183,33 @@ void free_feed(wssr_ctx* h) {
 
 void free_all(wssr_ctx* h) {
   free_feed(h);
-  void* ptrs[] = {h->status, h->Yp, h->Y, h->Y2, h->csum_part, h->mean_r, h->ysum,
-                  h->Z, h->V, h->V2, h->Xhat, h->Yhat, h->mu, h->gram_part, h->G, h->T,
-                  h->rot_log, h->nsweeps, h->W, h->Hp, h->c, h->e, h->dot_part,
-                  h->TX, h->TY, h->TW, h->tc_gram_part, h->TWT3, h->Vhp, h->gbar, h->wE, h->wE_sum,
-                  h->chol_ws, h->jac_ws};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (auto& rg : h->regions) {
+    bounds_unregister(rg.first);
+    cudaFree(rg.first);
+  }
+  h->regions.clear();
 }
+
+// Debug option WSSR_DEBUG_POISON: every workspace byte 0xFF (NaN in float,
+// double and bf16) except the status words, after the device is idle.
+cudaError_t poison_workspace(wssr_ctx* h) {
+  cudaError_t e = cudaDeviceSynchronize();
+  for (auto& rg : h->regions) {
+    if (e != cudaSuccess) break;
+    if (rg.first == (void*)h->status || rg.first == (void*)h->nsweeps) continue;
+    e = cudaMemset(rg.first, 0xFF, rg.second);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e;
+}
+
+// Status of a tensor-core launch that could not be made: a bounds violation
+// found by the checked build's tensor-map check, else an unsupported shape.
+wssr_status tc_fail() { return bounds_take_error() ? WSSR_ERR_BOUNDS : WSSR_ERR_UNSUPPORTED; }
 
 wssr_status check_launch(wssr_ctx* h) {
   cudaError_t e = cudaGetLastError();
+  if (bounds_take_error()) return WSSR_ERR_BOUNDS;  // a launch the checked build refused
   return e == cudaSuccess ? WSSR_OK : WSSR_ERR_CUDA;
 }
 
@@ -206,11 +268,11 @@ wssr_status pass_A(wssr_ctx* h, const wssr_operator* op, const void* Xop, float*
     if (op->kind == WSSR_OP_MLP) {
       const MlpSource src = mlp_source(op->mlp);
       int rc = tc_mf_jvp_launch(src, N, Xop, r, h->splits_mf, h->Yp, h->opt.wait_cap, h->status, st, &nsplit);
-      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      if (rc != 0) return tc_fail();
     } else if (h->use_tc) {
       int rc = tc_passA_launch(op->O, op->ld, N, M, Xop, h->ldx, r, h->splits_tc, h->Yp,
                                h->opt.wait_cap, h->status, st, &nsplit);
-      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      if (rc != 0) return tc_fail();
     } else {
       if (is_bf16(h)) launch_passA_simt<bf16>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
       else launch_passA_simt<float>(op->O, op->ld, N, M, Xop, r, h->splits_simt, h->Yp, st);
@@ -241,7 +303,7 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
       const MlpSource src = mlp_source(op->mlp);
       int rc = tc_mf_vjp_launch(src, N, Yop, h->ldy, r, h->ysum, Zf, ZT, h->mu, h->mu_valid ? 0 : 1,
                                 h->opt.wait_cap, h->status, st, Zadd);
-      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      if (rc != 0) return tc_fail();
       h->mu_valid = true;
     } else if (h->use_tc) {
       void* ZT = Zf ? nullptr : h->Xhat;
@@ -249,7 +311,7 @@ wssr_status pass_B(wssr_ctx* h, const wssr_operator* op, const void* Yop, float*
                                h->mu_valid ? 0 : 1, h->opt.wait_cap, h->status, st, Zadd, h->fuse_w, h->fuse_g,
                                h->wE_sum);
       h->fuse_w = nullptr, h->fuse_g = nullptr;  // formed with this step's column means
-      if (rc != 0) return WSSR_ERR_UNSUPPORTED;
+      if (rc != 0) return tc_fail();
       h->mu_valid = true;
     } else if (is_bf16(h)) {
       launch_passB_simt<bf16>(op->O, op->ld, N, M, Yop, r, h->ysum, Zf ? Zf : h->Z, h->mu, st);
@@ -401,7 +463,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     // more warp shuffles than re-reading V_out)
     launch_split3_T(h->TW, r, h->TWT3, st);
     if (tc_rotate_launch(Xop, M, r, h->TWT3, V_out, h->opt.wait_cap, h->status, st) != 0)
-      return WSSR_ERR_UNSUPPORTED;
+      return tc_fail();
     h->launches += 2;
   } else {
     launch_apply_any(Xop, operand_layout(h), r, M, r, h->TW, V_out, nullptr, 0, nullptr, 0, nullptr,
@@ -546,6 +608,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (opt.wait_cap < 1) return WSSR_ERR_INVALID_ARG;
   if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;
   if (!(opt.r_reg >= 0.0 && opt.r_reg <= 1.0)) return WSSR_ERR_INVALID_ARG;
+  if (opt.debug & ~WSSR_DEBUG_POISON) return WSSR_ERR_INVALID_ARG;
 
   wssr_ctx* h = new (std::nothrow) wssr_ctx();
   if (!h) return WSSR_ERR_OOM;
@@ -581,7 +644,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   const int64_t gpart = std::max(gram_part_elems(N + r, r), gram_part_elems(M, r));
   cudaError_t e = cudaSuccess;
 #define ALLOC(p, bytes) \
-  if (e == cudaSuccess) e = dalloc(&h->p, (bytes))
+  if (e == cudaSuccess) e = dalloc(h->regions, &h->p, (bytes))
   ALLOC(status, 2 * sizeof(int));
   ALLOC(Yp, h->yp_elems * f);
   // sample-side blocks carry r extra rows (history averaging)
@@ -631,7 +694,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
     delete h;
     return e == cudaErrorMemoryAllocation ? WSSR_ERR_OOM : WSSR_ERR_CUDA;
   }
-  if (cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
+  if (((opt.debug & WSSR_DEBUG_POISON) && poison_workspace(h) != cudaSuccess) ||
+      cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(h->nsweeps, 0, sizeof(int)) != cudaSuccess) {
     free_all(h);
     delete h;
@@ -927,6 +991,7 @@ wssr_status wssr_sync(wssr_handle h) {
   if (!h) return WSSR_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return WSSR_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return WSSR_ERR_CUDA;
+  if (bounds_take_error()) return WSSR_ERR_BOUNDS;
   int s = 0;
   if (cudaMemcpy(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WSSR_ERR_CUDA;
   if (s != 0 && cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) return WSSR_ERR_CUDA;
@@ -965,6 +1030,7 @@ wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n) {
 wssr_status wssr_set_rank(wssr_handle h, int32_t r) {
   if (!h || !rank_ok(h, r) || r > h->N - 1 || r > h->M) return WSSR_ERR_INVALID_ARG;
   configure_rank(h, r);
+  if ((h->opt.debug & WSSR_DEBUG_POISON) && poison_workspace(h) != cudaSuccess) return WSSR_ERR_CUDA;
   return WSSR_OK;
 }
 
@@ -1075,6 +1141,7 @@ const char* wssr_status_string(wssr_status s) {
     case WSSR_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
     case WSSR_ERR_CUDA: return "CUDA runtime error";
     case WSSR_ERR_UNSUPPORTED: return "unsupported configuration";
+    case WSSR_ERR_BOUNDS: return "index or tensor map outside its buffer (bounds-checked build)";
   }
   return "unknown status";
 }

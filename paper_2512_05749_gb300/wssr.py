@@ -22,6 +22,8 @@ WSSR_ERR_NONFINITE = 4
 WSSR_ERR_DEVICE_TIMEOUT = 5
 WSSR_ERR_CUDA = 6
 WSSR_ERR_UNSUPPORTED = 7
+WSSR_ERR_BOUNDS = 8
+WSSR_DEBUG_POISON = 1
 
 WSSR_DTYPE_F32 = 0
 WSSR_DTYPE_BF16 = 1
@@ -62,7 +64,7 @@ class wssr_options(ctypes.Structure):
         ("engine", ctypes.c_int32),
         ("jacobi_sweeps", ctypes.c_int32),
         ("history", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("debug", ctypes.c_int32),
         ("r_reg", ctypes.c_double),
     ]
 
@@ -105,19 +107,25 @@ class WSSRError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
+def checked_build_requested() -> bool:
+    """WSSR_CHECK_BOUNDS=1 in the environment selects the bounds-checked library."""
+    return os.environ.get("WSSR_CHECK_BOUNDS", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return os.path.join(HERE, "libwssr.so")
+    return os.path.join(HERE, "libwssr_checked.so" if checked_build_requested() else "libwssr.so")
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libwssr.so (building it in-tree with nvcc if it is missing)."""
+    """Load libwssr.so, or libwssr_checked.so when WSSR_CHECK_BOUNDS=1
+    (building it in-tree with nvcc if it is missing or stale)."""
     global _lib
     if _lib is not None:
         return _lib
     path = library_path()
     if build_if_missing:
         from . import build as _build
-        _build.build()
+        _build.build(checked=checked_build_requested())
     if not os.path.exists(path):
         raise RuntimeError(f"libwssr.so not found at {path}; run paper_2512_05749_gb300.build")
     lib = ctypes.CDLL(path)
@@ -284,11 +292,27 @@ def wssr_woodbury(h: int, V, sigma, g, delta, stream=None):
 def wssr_woodbury_noalloc(V, sigma, g, delta, lam: float, apply_mode: int = WSSR_APPLY_DAMPED,
                           sigma_floor: float = 0.0, stream=None):
     """The Woodbury apply without a handle and without any device allocation
-    (for callers that cannot call cudaMalloc); see include/wssr.h."""
+    (for callers that cannot call cudaMalloc); see include/wssr.h.
+
+    V: contiguous float32 (M, r) CUDA tensor; sigma: float64 (r,); g, delta:
+    float32 (M,); all on one device. The call runs with that device current,
+    so the library's scratch array and default stream are that device's."""
+    import torch
+    if not (isinstance(V, torch.Tensor) and V.is_cuda and V.dim() == 2 and V.dtype == torch.float32
+            and V.is_contiguous()):
+        raise ValueError("V must be a contiguous 2-D float32 CUDA tensor")
     M, r = V.shape
-    _check(load().wssr_woodbury_noalloc(_ptr(V), _ptr(sigma), _ptr(g), _ptr(delta), M, r, lam,
-                                        apply_mode, sigma_floor, _stream(stream)),
-           "wssr_woodbury_noalloc")
+    for name, t, dt, n in (("sigma", sigma, torch.float64, r), ("g", g, torch.float32, M),
+                           ("delta", delta, torch.float32, M)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.dim() == 1 and t.numel() == n
+                and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor of {n} elements")
+        if t.device != V.device:
+            raise ValueError(f"{name} is on {t.device}, V on {V.device}")
+    with torch.cuda.device(V.device):
+        _check(load().wssr_woodbury_noalloc(_ptr(V), _ptr(sigma), _ptr(g), _ptr(delta), M, r, lam,
+                                            apply_mode, sigma_floor, _stream(stream)),
+               "wssr_woodbury_noalloc")
 
 
 def wssr_set_rank(h: int, r: int):
@@ -421,6 +445,9 @@ class WSSR:
         opt.r_reg = r_reg
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
         opt.history = 1 if history else 0
+        # WSSR_DEBUG_POISON=1 in the environment: NaN-fill the workspace (include/wssr.h)
+        if os.environ.get("WSSR_DEBUG_POISON", "0") not in ("", "0"):
+            opt.debug |= WSSR_DEBUG_POISON
         opt.dtype = {"f32": WSSR_DTYPE_F32, "bf16": WSSR_DTYPE_BF16}[dtype]
         opt.apply_mode = {"damped": WSSR_APPLY_DAMPED, "cutoff": WSSR_APPLY_CUTOFF,
                           "pinv": WSSR_APPLY_PINV}[apply_mode]

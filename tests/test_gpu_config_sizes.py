@@ -1,0 +1,56 @@
+"""One-step parity at the stated size of the FP32 centring workload
+(N = 8192 samples, M = 200,000 parameters, r = 128, lambda = 1e-3, m = 2,
+sigma_k = 1/k, noise 1e-4, per-column offsets 0.1 N(0, 1); O stored in FP32
+and multiplied on the plain FP32 engine, 6.55 GB) against the FP64 oracle on
+the same float32 values (13 GB in float64 on the host).
+
+The warm start is an input (float32 subspace iteration with LAPACK QR, not the
+GPU): both sides take the same V_prev. FP32 tolerances: delta 1e-5 (the
+stated FP32 bound), its low-rank part delta - g/lambda and the Ritz values
+1e-4 (the test of the offset-column case at the small size), projector 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import wssr_oracle as orc
+from synth import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def test_centring_workload_full_size_step_fp32_simt():
+    from paper_2512_05749_gb300 import WSSR
+    w = wl.WORKLOADS["planted-n8192-m200k-r128"]
+    free, _ = torch.cuda.mem_get_info()
+    if free < 20e9:
+        pytest.skip("needs about 20 GB of free device memory")
+    O32 = wl.planted_O_np(w).astype(np.float32)
+    # warm start: float32 subspace iteration on the centred matrix (an input)
+    Oc32 = O32 - O32.mean(axis=0, dtype=np.float64).astype(np.float32)[None, :]
+    V = np.linalg.qr(wl.gaussian_np((w.M, w.r), "cfg2warm").astype(np.float32))[0]
+    for _ in range(6):
+        V = np.linalg.qr(Oc32.T @ (Oc32 @ V))[0]
+    del Oc32
+    Vprev = V.astype(np.float32)
+    g = wl.gradient_np(w.M, 0, "cfg2").astype(np.float32)
+    s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, dtype="f32", engine="simt")
+    O = torch.from_numpy(O32).to("cuda:0")
+    d, sg, Vo = s.step(O, torch.from_numpy(g).to("cuda:0"), torch.from_numpy(Vprev).to("cuda:0"))
+    s.check("centring workload step")
+    d, sg, Vo = d.double().cpu().numpy(), sg.cpu().numpy(), Vo.double().cpu().numpy()
+    s.close()
+    del O
+    torch.cuda.empty_cache()
+    g64 = g.astype(np.float64)
+    dr, sr, Vr = orc.wssr_step(O32.astype(np.float64), g64, Vprev.astype(np.float64), w.lam, w.m)
+    err_d = np.linalg.norm(d - dr) / np.linalg.norm(dr)
+    err_lr = np.linalg.norm((d - g64 / w.lam) - (dr - g64 / w.lam)) / np.linalg.norm(dr - g64 / w.lam)
+    err_s = np.max(np.abs(sg - sr) / sr)
+    P = orc.projector_distance(Vo, Vr)
+    print(f"delta {err_d:.2e} delta_lr {err_lr:.2e} sigma {err_s:.2e} projector {P:.2e}")
+    assert err_d <= 1e-5, err_d
+    assert err_lr <= 1e-4, err_lr
+    assert err_s <= 1e-4, err_s
+    assert P <= 1e-3, P
+    assert np.abs(Vo.T @ Vo - np.eye(w.r)).max() <= 1e-5

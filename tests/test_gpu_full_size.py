@@ -1,7 +1,4 @@
-"""(Runs after the other GPU test modules: it allocates and frees about 45 GB of
-device memory.)
-
-Parity at the full sizes the bench times, with the bench's handle options
+"""Parity at the full sizes the bench times, with the bench's handle options
 (BF16 O, tcgen05 engine, m = 2), on outputs the oracle side computes one by one
 on the host in FP64, and on properties that hold at any size.
 

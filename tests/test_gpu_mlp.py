@@ -91,12 +91,14 @@ def test_vjp_and_autograd(widths, ne):
     ans.close()
 
 
-def test_wssr_step_on_mlp_jacobian():
+@pytest.mark.parametrize("N,r", [(1024, 32), (4096, 64)])
+def test_wssr_step_on_mlp_jacobian(N, r):
     """The Jacobian kernel's O fed to the WSSR step matches the oracle step on
-    the oracle's Jacobian (N = 1024 samples, M = 85,505, r = 32)."""
+    the oracle's Jacobian (M = 85,505 parameters of the 75->256->256->1 network;
+    N = 4096, r = 64 is the network workload's own size)."""
     from paper_2512_05749_gb300 import WSSR
     widths = (75, 256, 256, 1)
-    N, r, lam = 1024, 32, 1e-3
+    lam = 1e-3
     ans, th, x, tth, tx = setup(widths, 10, N, "step")
     O = ans.per_sample_jacobian(tth, tx)
     J = mo.per_sample_jacobian(th.astype(np.float64), widths, x.astype(np.float64))

@@ -239,3 +239,43 @@ def test_wssr_step_matrix_free(widths, ne, N, r):
     assert np.all(np.diff(sg) <= 1e-12 * sg[0])
     s.close()
     ans.close()
+
+
+def test_wssr_step_matrix_free_rank256():
+    """The matrix-free step at the network bench's rank r = 256 (both 128 x 256
+    TMEM accumulators of the forward product, the r = 256 Cholesky blocks and
+    Jacobi ring) against the FP64 oracle on the operator the kernels apply.
+    The warm start is an input: float32 subspace iteration with LAPACK QR.
+    Tolerances as in the dense r = 256 step test (bf16 basis, u = 2^-9)."""
+    skip_if_no_tc()
+    widths, ne, N, r, lam = (75, 130, 70, 1), 10, 1024, 256, 1e-3
+    ans, s, th, x, tth, tx = setup(widths, ne, N, r, "step256", lam=lam)
+    Oh = o_hat(th, widths, x)
+    Oc = orc.centre(Oh).astype(np.float32)
+    Vp = np.linalg.qr(wl.gaussian_np((ans.M, r), "mf256").astype(np.float32))[0]
+    for _ in range(6):
+        Vp = np.linalg.qr(Oc.T @ (Oc @ Vp))[0]
+    Vp = Vp.astype(np.float32)
+    g = wl.gradient_np(ans.M, 0, "mfstep256").astype(np.float32)
+    d, sg, V = s.step(ans.operator(tth, tx), ans.pad(torch.from_numpy(g).to(dev())),
+                      ans.pad(torch.from_numpy(Vp).to(dev())))
+    s.check("matrix-free step r = 256")
+    du, Vu = ans.unpad(d).double().cpu().numpy(), ans.unpad(V).double().cpu().numpy()
+    sg = sg.cpu().numpy()
+    dr, sr, Vr = orc.wssr_step(Oh, g.astype(np.float64), Vp.astype(np.float64), lam, 2)
+    g64 = g.astype(np.float64)
+    err_d = np.linalg.norm(du - dr) / np.linalg.norm(dr)
+    err_lr = np.linalg.norm((du - g64 / lam) - (dr - g64 / lam)) / np.linalg.norm(dr - g64 / lam)
+    err_top = np.max(np.abs(sg[:32] - sr[:32]) / sr[:32])
+    err_s = np.max(np.abs(sg - sr) / sr)
+    P = orc.projector_distance(Vu, Vr)
+    print(f"delta {err_d:.2e} delta_lr {err_lr:.2e} sigma_top {err_top:.2e} sigma {err_s:.2e} proj {P:.2e}")
+    assert err_d <= 1e-3, err_d
+    assert err_lr <= 1e-2, err_lr
+    assert err_top <= 2e-3, err_top
+    assert err_s <= 2e-2, err_s
+    assert P <= 5e-2, P
+    assert np.abs(Vu.T @ Vu - np.eye(r)).max() <= 1e-5
+    assert np.all(np.diff(sg) <= 1e-12 * sg[0])
+    s.close()
+    ans.close()

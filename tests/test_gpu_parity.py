@@ -182,6 +182,7 @@ def run_step(W, w, dtype, engine="auto", m=2, mode="damped", floor=0.0, ld_pad=0
     ref = orc.wssr_step(Oex, g.astype(np.float64), Vprev.astype(np.float64), w.lam, m, mode,
                         floor if mode in ("cutoff", "pinv") else None)
     s.close()
+    run_step.last_g = g.astype(np.float64)
     return out, ref, Vprev
 
 
@@ -252,6 +253,11 @@ def test_step_bf16(W, engine, N, M, r):
     w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.2, noise=1e-4, lam=1e-4, dtype="bf16")
     out, ref, _ = run_step(W, w, "bf16", engine=engine)
     compare_step(out, ref, 1e-3, 1e-2, 5e-2)
+    # the low-rank part delta - g/lambda, which carries V and sigma (the bf16 basis
+    # moves it by about 2 u / sqrt(3) = 2.3e-3 relative, u = 2^-9)
+    g = run_step.last_g
+    e = step_errors(*out, *ref, g, w.lam)
+    assert e["delta_lr"] <= 1e-2, e
 
 
 def test_init_subspace_f32(W):
@@ -361,4 +367,74 @@ def test_bad_arguments_are_rejected(W):
     V = torch.zeros(520, 16, device=dev())
     with pytest.raises(W.WSSRError):
         W.wssr_step(s.handle, op, g, V, g, torch.zeros(16, device=dev(), dtype=torch.float64), V)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# The tensor-core step at the bench's rank r = 256
+# ---------------------------------------------------------------------------
+
+def warm_start_np(Oex, r, tag, iters=6):
+    """A warm start close to the dominant subspace (an input, not an expected
+    value): float32 subspace iteration with LAPACK QR, from a seeded block."""
+    Oc = orc.centre(Oex).astype(np.float32)
+    V = np.linalg.qr(wl.gaussian_np((Oex.shape[1], r), "warm", tag).astype(np.float32))[0]
+    for _ in range(iters):
+        V = np.linalg.qr(Oc.T @ (Oc @ V))[0]
+    return V.astype(np.float32)
+
+
+def step_errors(d, s, V, dr, sr, Vr, g, lam):
+    """delta, its low-rank part delta - g/lambda, sigma (all and the leading 32),
+    the projector distance and the orthonormality of V."""
+    lr, lrr = d - g / lam, dr - g / lam
+    return {"delta": np.linalg.norm(d - dr) / np.linalg.norm(dr),
+            "delta_lr": np.linalg.norm(lr - lrr) / np.linalg.norm(lrr),
+            "sigma": np.max(np.abs(s - sr) / sr),
+            "sigma_top": np.max(np.abs(s[:32] - sr[:32]) / sr[:32]),
+            "projector": orc.projector_distance(V, Vr),
+            "orth": np.abs(V.T @ V - np.eye(V.shape[1])).max()}
+
+
+# (N, M): split-K 38 and 28 in pass A, two 128 x 256 TMEM accumulators in every
+# product, the r = 256 shared-memory Cholesky blocks and Jacobi ring, the
+# 3-term rotation with r-wide staging; M = 20000 leaves a ragged 64-parameter
+# block (20000 % 64 = 32) and a ragged 256-parameter pass B tile.
+@pytest.mark.parametrize("N,M", [(2048, 32768), (1536, 20000)])
+def test_step_bf16_rank256_tcgen05(W, N, M):
+    """One tensor-core step at r = 256 against the FP64 oracle on the same bf16
+    bytes, from a warm start; a Gaussian g and a g inside span(V_prev), for
+    which delta is all low-rank part.
+
+    Tolerances. The basis is carried in bf16 (unit roundoff u = 2^-9): each
+    basis column is perturbed by about u / sqrt(3) relative, so the projector
+    moves by about u sqrt(2 r / 3) = 0.026 at r = 256 and the low-rank part of
+    delta, which weights the leading directions by up to 1 / lambda, by about
+    2 u / sqrt(3) relative per direction (2.3e-3); bounds 5e-2 and 1e-2. The
+    Ritz values are Rayleigh quotients, second order in the basis error for the
+    leading ones (bound 2e-3 on the leading 32) but not for the tail, whose
+    values sit near the noise edge (bound 2e-2)."""
+    skip_if_no_tc(W, "tcgen05")
+    r, lam = 256, 1e-4
+    w = wl.small_planted(N, M, r, K=min(N, 4 * r), sigma_power=1.2, noise=1e-4, lam=lam, dtype="bf16")
+    O, Oex = make_O(w, "bf16", ld_pad=(-M) % 8)
+    Vprev = warm_start_np(Oex, r, f"{N}-{M}")
+    s = W.WSSR(N, M, r, lam, m=2, dtype="bf16", engine="tcgen05")
+    g1 = wl.gradient_np(M, 0, "r256").astype(np.float32)
+    g2 = (Vprev.astype(np.float64) @ wl.gaussian_np((r,), "r256c")).astype(np.float32)
+    tV = torch.from_numpy(Vprev).to(dev())
+    for tag, g in (("gaussian g", g1), ("g in span(V_prev)", g2)):
+        d, sg, V = s.step(O, torch.from_numpy(g).to(dev()), tV)
+        s.check("r = 256 step")
+        d, sg, V = d.double().cpu().numpy(), sg.cpu().numpy(), V.double().cpu().numpy()
+        dr, sr, Vr = orc.wssr_step(Oex, g.astype(np.float64), Vprev.astype(np.float64), lam, 2)
+        e = step_errors(d, sg, V, dr, sr, Vr, g.astype(np.float64), lam)
+        print(tag, {k: f"{v:.2e}" for k, v in e.items()})
+        assert e["delta"] <= 1e-3, (tag, e)
+        assert e["delta_lr"] <= 1e-2, (tag, e)
+        assert e["sigma_top"] <= 2e-3, (tag, e)
+        assert e["sigma"] <= 2e-2, (tag, e)
+        assert e["projector"] <= 5e-2, (tag, e)
+        assert e["orth"] <= 1e-5, (tag, e)
+        assert np.all(np.diff(sg) <= 1e-12 * sg[0])
     s.close()

@@ -29,8 +29,11 @@ def _replica(rank: int, world: int, port: int, out):
     try:
         # each replica "times" a different step; all must report the slowest
         v = bench.max_over_ranks(10.0 + 3.0 * rank)
+        # the line's value: the slowest replica's ms per step, not divided by the replica count
+        ms = bench.replica_step_ms(100.0 + 30.0 * rank, 10)
+        head = bench.headline_fields(ms, world)
         dist.barrier()
-        out.put((rank, v, bench.dist_env()))
+        out.put((rank, v, bench.dist_env(), head))
     finally:
         dist.destroy_process_group()
 
@@ -47,8 +50,10 @@ def test_max_over_ranks_on_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    assert [(r, v) for r, v, _ in got] == [(0, 13.0), (1, 13.0)]
-    assert [env for _, _, env in got] == [(0, 2, 0), (1, 2, 1)]
+    assert [(r, v) for r, v, _, _ in got] == [(0, 13.0), (1, 13.0)]
+    assert [env for _, _, env, _ in got] == [(0, 2, 0), (1, 2, 1)]
+    for _, _, _, head in got:
+        assert head["value"] == 13.0 and head["ms_per_step"] == 13.0 and head["n_gpus"] == 2
 
 
 def test_max_over_ranks_without_a_group_is_the_value():
