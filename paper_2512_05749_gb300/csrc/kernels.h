@@ -116,6 +116,8 @@ void launch_gram(const float* X, int64_t L, int r, double* part, double* G, doub
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
                      cudaStream_t st, float* ws = nullptr);
 size_t chol_inv_smem(int r);
+// The factor itself: R (FP32 r x r, upper, zeros below) with G = R^T R (r <= WSSR_SMEM_RANK_MAX).
+void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st);
 int64_t chol_ws_floats(int r);
 // Xo = X T (L x r times r x r), optional bf16 copies (row-major L x r, transposed r x ldT)
 // and FP64 column-sum partials of the bf16/f32 operand values written.
@@ -149,6 +151,15 @@ void launch_jacobi(const double* H, int r, int max_sweeps, float* rot_log, int* 
                    cudaStream_t st, float* ws = nullptr);
 void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int max_sweeps, float* W,
                            cudaStream_t st);
+// Rayleigh-Ritz eigensolve on an 8-CTA thread-block cluster (eig_cluster.cu):
+// one-sided Jacobi on R (H = R^T R), W (r x r, row-major, unsorted columns);
+// then q_j = w_j^T H w_j (FP64), sigma (descending) = sqrt(q) and W_sorted.
+bool eig_cluster_supported(int r);
+size_t eig_cluster_smem();
+int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
+                       int* round_cnt, cudaStream_t st);
+void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
+                              float* W_sorted, cudaStream_t st);
 // c = V^T g (FP64), M x r V. The partial sums use at most DOT_MAX_BLOCKS row
 // blocks (8 CTAs per SM on 152 SMs), so dot_part_elems(M, r) <= DOT_MAX_BLOCKS * r.
 constexpr int DOT_MAX_BLOCKS = 1216;

@@ -338,7 +338,8 @@ __device__ __forceinline__ void strip(const float* L, const float* Rm, int i0, i
 // GWS: the blocks live in gws; otherwise in shared memory, where the pointer's
 // address space is known at compile time (shared-memory loads and stores
 // instead of generic ones).
-template <bool GWS>
+// OUT_R: write the factor R itself (G = R^T R, R = R' D^-1) instead of T = R^-1.
+template <bool GWS, bool OUT_R = false>
 __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G, int r,
                                                    float* __restrict__ T, int* status,
                                                    int* shift_count, float* __restrict__ gws) {
@@ -478,6 +479,18 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
     if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
     return;
   }
+  if (OUT_R) {
+    // R = R' D^-1: column j scaled by 1 / d_j = sqrt(G_jj); zeros below the diagonal
+    for (int i = warp; i < r; i += 32) {
+      const int I = i / CB, ii = i % CB;
+      float* Rrow = T + (int64_t)i * r;
+      for (int j = lane; j < r; j += 32) {
+        const int J = j / CB;
+        Rrow[j] = (I <= J && i <= j) ? (float)((double)B[blk_id(I, J, nb) * CBE + ii * CBP + lane] / d[j]) : 0.f;
+      }
+    }
+    return;
+  }
   // inverse, block rows from the bottom: T_II = TKK[I]; T_IJ = -T_II S_IJ,
   // S_IJ = sum_{K=I+1..J} R_IK T_KJ (rows K > I already hold T)
   for (int I = nb - 1; I >= 0; --I) {
@@ -558,6 +571,17 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
     k_chol_inv<false><<<1, 1024, sm, st>>>(G, r, T, status, shift_count, nullptr);
   else
     k_chol_inv<true><<<1, 1024, sm, st>>>(G, r, T, status, shift_count, ws);
+}
+
+void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_chol_inv<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess)
+      return;
+    attr_set = true;
+  }
+  k_chol_inv<false, true><<<1, 1024, chol_inv_smem(r), st>>>(G, r, R, status, shift_count, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -103,6 +103,8 @@ struct wssr_ctx {
   float* rot_log = nullptr;
   int* nsweeps = nullptr;
   float* W = nullptr;
+  float* Wu = nullptr;         // eigenvectors of the cluster eigensolve before sorting
+  double* rq = nullptr;        // their FP64 Rayleigh quotients
   double* Hp = nullptr;
   double* c = nullptr;
   double* e = nullptr;
@@ -439,6 +441,17 @@ wssr_status iterate(wssr_ctx* h, const wssr_operator* op, const void** Xop, bool
   return WSSR_OK;
 }
 
+// The eigensolve of the Rayleigh-Ritz step runs on a thread-block cluster up to
+// r = 256 (one-sided Jacobi, rows split over the CTAs), on one CTA above.
+// WSSR_TUNE_EIG=onecta keeps the one-CTA two-sided Jacobi at every rank (for comparisons).
+bool use_cluster_eig(int r) {
+  static const bool onecta = [] {
+    const char* e = getenv("WSSR_TUNE_EIG");
+    return e && strcmp(e, "onecta") == 0;
+  }();
+  return !onecta && eig_cluster_supported(r);
+}
+
 // Rayleigh-Ritz on span(Xh) = span(Xh TX): Y = (O_c Xh) TX, H = Y^T Y scaled,
 // H = W L W^T (Jacobi), V_out = Xh (TX W), sigma from FP64 Rayleigh quotients.
 wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, float* V_out, double* sigma,
@@ -453,8 +466,24 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   right_multiply_Y(h, h->Y, h->TX, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
-  launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->status, st, h->jac_ws);
-  launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
+  double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
+  const bool on_cluster = use_cluster_eig(r);
+  if (on_cluster) {
+    // H = R^T R (FP32 factor of the FP64 Gram), one-sided Jacobi on R over a cluster,
+    // Ritz values from FP64 Rayleigh quotients of H, columns sorted by them
+    const int ms = h->opt.jacobi_sweeps;
+    int* cnt = reinterpret_cast<int*>(h->rot_log + (size_t)ms * (r - 1) * (r / 2) * 2);
+    launch_chol_R(h->G, r, h->T, h->status, h->status + 1, st);
+    // rotation threshold: above the rounding of the FP32 dot products (about u sqrt(r) relative)
+    const float tol = 4.f * 5.96e-8f * sqrtf((float)r);
+    if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, st) != 0) return WSSR_ERR_CUDA;
+    launch_rr_quotients_sort(h->G, h->Wu, r, h->rq, sig, h->W, st);
+    h->launches += 4;
+  } else {
+    launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->status, st, h->jac_ws);
+    launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
+    h->launches += 2;
+  }
   launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
   if (h->use_tc) {
@@ -470,13 +499,15 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
                      nullptr, st);
     h->launches += 1;
   }
-  launch_apply(h->Y, L, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
-  launch_gram(h->Y2, L, r, h->gram_part, h->Hp, gscale, st);
-  // Gram (2), Jacobi and its eigenvector replay (2), T W (1), Y W (1), Gram (2)
-  h->launches += 2 + 2 + 1 + 1 + 2;
-  double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
-  launch_finalize_sigma(h->Hp, r, sig, st);
-  h->launches++;
+  // Gram (2), T W (1)
+  h->launches += 2 + 1;
+  if (!on_cluster) {
+    // Ritz values: FP64 Rayleigh quotients of the rotated block Y W
+    launch_apply(h->Y, L, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+    launch_gram(h->Y2, L, r, h->gram_part, h->Hp, gscale, st);
+    launch_finalize_sigma(h->Hp, r, sig, st);
+    h->launches += 4;
+  }
   return check_launch(h);
 }
 
@@ -669,6 +700,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(rot_log, (size_t)jacobi_log_elems(r, opt.jacobi_sweeps) * 2 * f);
   ALLOC(nsweeps, sizeof(int));
   ALLOC(W, (size_t)r * r * f);
+  ALLOC(Wu, (size_t)r * r * f);
+  ALLOC(rq, (size_t)r * d);
   ALLOC(Hp, (size_t)r * r * d);
   ALLOC(c, (size_t)r * d);
   ALLOC(e, (size_t)r * d);
