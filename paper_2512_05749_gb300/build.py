@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libwssr.so")
 # tensor map against the workspace allocation it addresses
 LIB_CHECKED = os.path.join(HERE, "libwssr_checked.so")
 SOURCES = ["wssr.cu", "simt_passes.cu", "small_ops.cu", "tc_passes.cu", "tc_mlp.cu", "noalloc.cu", "mlp.cu",
-           "eig_cluster.cu"]
+           "eig_cluster.cu", "r64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

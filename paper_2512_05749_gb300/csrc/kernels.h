@@ -160,6 +160,14 @@ int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* 
                        int* round_cnt, cudaStream_t st);
 void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
                               float* W_sorted, cudaStream_t st);
+// FP64 refinements (r64.cu). Factor: T_out = T (I - E / 2), E = T^T G T - I (P, E:
+// r x r FP64 scratch). Eigenvectors of H (one Ogita-Aishima sweep from the FP32 X):
+// sigma (descending) = sqrt of the refined Ritz values, W_sorted their FP32 vectors
+// (P, S, G, E, Xn: r x r FP64 scratch; lam: r). W_sorted may alias X.
+void launch_refine_factor(const double* G, const float* T, int r, double* P, double* E, float* T_out,
+                          cudaStream_t st);
+void launch_refine_eigenvectors(const double* H, const float* X, int r, double* P, double* S, double* G, double* E,
+                                double* Xn, double* lam, double* sigma, float* W_sorted, cudaStream_t st);
 // c = V^T g (FP64), M x r V. The partial sums use at most DOT_MAX_BLOCKS row
 // blocks (8 CTAs per SM on 152 SMs), so dot_part_elems(M, r) <= DOT_MAX_BLOCKS * r.
 constexpr int DOT_MAX_BLOCKS = 1216;

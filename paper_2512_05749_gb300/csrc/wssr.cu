@@ -99,6 +99,9 @@ struct wssr_ctx {
   float* mu = nullptr;
   double* gram_part = nullptr;
   double* G = nullptr;
+  double* Gx = nullptr;        // FP64 Gram of the basis operand (its factor is T_X)
+  float* Tref = nullptr;       // T_X refined in FP64 (Rayleigh-Ritz)
+  double* r64 = nullptr;       // FP64 refinement scratch: 5 r x r + r
   float* T = nullptr;
   float* rot_log = nullptr;
   int* nsweeps = nullptr;
@@ -345,11 +348,11 @@ void factor_operand(wssr_ctx* h, const void* Xop, float* T_out, cudaStream_t st)
     int used = 0;
     tc_gram_launch(Xop, h->ldx, h->M, r, h->gram_splits_tc, h->tc_gram_part, h->opt.wait_cap, h->status,
                    st, &used);
-    launch_sum_partials(h->tc_gram_part, used, r, 1.0, h->G, st);
+    launch_sum_partials(h->tc_gram_part, used, r, 1.0, h->Gx, st);
   } else {
-    launch_gram_any(Xop, is_bf16(h) ? 1 : 0, h->M, r, h->gram_part, h->G, 1.0, st);
+    launch_gram_any(Xop, is_bf16(h) ? 1 : 0, h->M, r, h->gram_part, h->Gx, 1.0, st);
   }
-  launch_chol_inv(h->G, r, T_out, h->status, h->status + 1, st, h->chol_ws);
+  launch_chol_inv(h->Gx, r, T_out, h->status, h->status + 1, st, h->chol_ws);
   h->launches += 3;
 }
 
@@ -463,7 +466,22 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   wssr_status s;
   if ((s = pass_A(h, op, Xop, h->Y, st)) != WSSR_OK) return s;
   if (hist) history_rows(h, hist, Xop, h->Y, st);
-  right_multiply_Y(h, h->Y, h->TX, L, st);
+  const bool refine = h->opt.fp64_refine != 0;
+  double* P = h->r64;
+  double* rS = P + (size_t)r * r;
+  double* rG = rS + (size_t)r * r;
+  double* rE = rG + (size_t)r * r;
+  double* rX = rE + (size_t)r * r;
+  double* rlam = rX + (size_t)r * r;
+  const float* TXu = h->TX;
+  if (refine) {
+    // the basis factor to FP64 orthonormality: X_h T' with T'^T G_x T' = I + O(E^2)
+    Timed tr(h, WSSR_KCAT_RR, st);
+    launch_refine_factor(h->Gx, h->TX, r, P, rE, h->Tref, st);
+    h->launches += 3;
+    TXu = h->Tref;
+  }
+  right_multiply_Y(h, h->Y, TXu, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
   launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
   double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
@@ -477,14 +495,22 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     // rotation threshold: above the rounding of the FP32 dot products (about u sqrt(r) relative)
     const float tol = 4.f * 5.96e-8f * sqrtf((float)r);
     if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, st) != 0) return WSSR_ERR_CUDA;
-    launch_rr_quotients_sort(h->G, h->Wu, r, h->rq, sig, h->W, st);
-    h->launches += 4;
+    h->launches += 2;
+    if (!refine) {
+      launch_rr_quotients_sort(h->G, h->Wu, r, h->rq, sig, h->W, st);
+      h->launches += 2;
+    }
   } else {
     launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->status, st, h->jac_ws);
     launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
     h->launches += 2;
   }
-  launch_apply(h->TX, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  if (refine) {
+    // one FP64 refinement sweep of the eigenvectors; Ritz values and order from it
+    launch_refine_eigenvectors(h->G, on_cluster ? h->Wu : h->W, r, P, rS, rG, rE, rX, rlam, sig, h->W, st);
+    h->launches += 6;
+  }
+  launch_apply(TXu, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
   if (h->use_tc) {
     // V_out = Xh (T W) on the tensor cores (c = V_out^T g is a separate,
@@ -501,7 +527,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   }
   // Gram (2), T W (1)
   h->launches += 2 + 1;
-  if (!on_cluster) {
+  if (!on_cluster && !refine) {
     // Ritz values: FP64 Rayleigh quotients of the rotated block Y W
     launch_apply(h->Y, L, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
     launch_gram(h->Y2, L, r, h->gram_part, h->Hp, gscale, st);
@@ -616,6 +642,7 @@ void wssr_default_options(wssr_options* opt) {
   opt->engine = WSSR_ENGINE_AUTO;
   opt->jacobi_sweeps = 12;
   opt->history = 0;
+  opt->fp64_refine = 1;
 }
 
 wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const wssr_options* opt_in,
@@ -640,6 +667,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;
   if (!(opt.r_reg >= 0.0 && opt.r_reg <= 1.0)) return WSSR_ERR_INVALID_ARG;
   if (opt.debug & ~WSSR_DEBUG_POISON) return WSSR_ERR_INVALID_ARG;
+  if (opt.fp64_refine != 0 && opt.fp64_refine != 1) return WSSR_ERR_INVALID_ARG;
 
   wssr_ctx* h = new (std::nothrow) wssr_ctx();
   if (!h) return WSSR_ERR_OOM;
@@ -696,6 +724,9 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(mu, (size_t)M * f);
   ALLOC(gram_part, (size_t)gpart * d);
   ALLOC(G, (size_t)r * r * d);
+  ALLOC(Gx, (size_t)r * r * d);
+  ALLOC(Tref, (size_t)r * r * f);
+  if (opt.fp64_refine) ALLOC(r64, ((size_t)5 * r * r + r) * d);
   ALLOC(T, (size_t)r * r * f);
   ALLOC(rot_log, (size_t)jacobi_log_elems(r, opt.jacobi_sweeps) * 2 * f);
   ALLOC(nsweeps, sizeof(int));

@@ -30,7 +30,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 
 def test_options_layout_and_defaults():
-    assert ctypes.sizeof(W.wssr_options) == 56
+    assert ctypes.sizeof(W.wssr_options) == 64
     assert ctypes.sizeof(W.wssr_operator) == 48
     opt = W.wssr_default_options()
     assert (opt.m, opt.m_init, opt.dtype, opt.apply_mode, opt.engine, opt.jacobi_sweeps) == \
