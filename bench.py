@@ -968,7 +968,7 @@ def main():
     ap.add_argument("--accuracy-cols", type=int, default=2048,
                     help="parameter columns of the sample on which one GPU step is compared with the FP64 "
                          "oracle (0 = skip)")
-    ap.add_argument("--fp64-refine", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--fp64-refine", type=int, default=0, choices=[0, 1],
                     help="FP64 refinement of the basis factor and of the eigenvectors in the Rayleigh-Ritz "
                          "step (options.fp64_refine)")
     ap.add_argument("--compare-f32", type=int, default=2,

@@ -105,10 +105,10 @@ typedef struct {
                            the apply keeps the leading Ritz triplets with r_reg <= sigma_i^2 / sigma_1^2
                            (the paper's s_i are singular values of S = squares of sigma_i); the rest
                            of span(V) joins the complement term */
-  int32_t fp64_refine;  /* 1 (default): the Rayleigh-Ritz step refines, in FP64, the basis factor (to an
+  int32_t fp64_refine;  /* 1: the Rayleigh-Ritz step refines, in FP64, the basis factor (to an
                            FP64-orthonormal basis) and the FP32 Jacobi eigenvectors of the projected matrix
-                           (one Ogita-Aishima sweep); 0: FP32 factor and eigenvectors, Ritz values from FP64
-                           Rayleigh quotients */
+                           (one Ogita-Aishima sweep); 0 (default): FP32 factor and eigenvectors, Ritz values
+                           from FP64 Rayleigh quotients */
   int32_t reserved2;    /* 0 */
 } wssr_options;
 

@@ -51,6 +51,7 @@ struct EcSmem {
   float4 recv[2][EC_CLUSTER][EC_MAXR / 2];  // per buffer, source rank and pair: {app, aqq, apq, 0}
   int rotated;                              // rank 0: rotations of the last sweep (read by every CTA)
   int go;                                   // this CTA's copy of rank 0's decision
+  unsigned tmax;                            // largest |tan| of the sweep's rotations (float bits)
 };
 
 __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
@@ -62,12 +63,13 @@ __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
 // [[app, apq], [apq, aqq]]; applied when the pair is not yet orthogonal to
 // `tol` relative to its norms and apq is above the rounding of the FP32 dot
 // products (about u sqrt(rows) of |b_p| |b_q|).
-__device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, float tol, float& c, float& s) {
-  c = 1.f, s = 0.f;
+__device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, float tol, float& c, float& s,
+                                            float& t) {
+  c = 1.f, s = 0.f, t = 0.f;
   const float nrm = sqrtf(app * aqq);
   if (!(fabsf(apq) > tol * nrm)) return false;
   const float tau = (aqq - app) / (2.f * apq);
-  const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
   c = __frsqrt_rn(1.f + t * t);
   s = t * c;
   return true;
@@ -99,9 +101,14 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
   const int i = tid >> 2, sub = tid & 3;
   const bool owner = i < h;
   const int l0 = sub * EC_SEG;
+  // A sweep whose largest rotation has |tan| below t_stop leaves off-diagonal
+  // products of order t_stop^2 = tol / 16 relative: the next sweep would rotate
+  // nothing, so it is not run
+  const float t_stop = 0.25f * sqrtf(tol);
   int buf = 0, sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
+    if (tid == 0) S.tmax = 0u;
     for (int k = 0; k < n1; ++k) {
       int p = 0, q = 0;
       float app = 0.f, aqq = 0.f, apq = 0.f;
@@ -140,8 +147,9 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
           const float4 v = S.recv[buf][d][i];
           tpp += v.x, tqq += v.y, tpq += v.z;
         }
-        float c, s;
-        act = ec_rotation(tpp, tqq, tpq, tol, c, s);
+        float c, s, t;
+        act = ec_rotation(tpp, tqq, tpq, tol, c, s, t);
+        if (act && sub == 0) atomicMax(&S.tmax, __float_as_uint(fabsf(t)));
         if (act) {
 #pragma unroll
           for (int jj = 0; jj < EC_SEG; ++jj) {
@@ -166,12 +174,12 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
     }
     // Every CTA counted the same rotations (identical inputs, identical arithmetic), but the
     // loop exit is taken from rank 0's count so that all CTAs meet the same cluster barriers
-    if (crank == 0 && tid == 0) S.rotated = rotated;
+    if (crank == 0 && tid == 0) S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop) ? 1 : 0;
     cluster.sync();
     if (tid == 0) S.go = *cluster.map_shared_rank(&S.rotated, 0);
     __syncthreads();
     if (!S.go) {
-      ++sweep;  // a sweep without rotations
+      ++sweep;  // the last sweep: no rotation, or none above t_stop
       break;
     }
   }

@@ -164,8 +164,10 @@ void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, d
 // r x r FP64 scratch). Eigenvectors of H (one Ogita-Aishima sweep from the FP32 X):
 // sigma (descending) = sqrt of the refined Ritz values, W_sorted their FP32 vectors
 // (P, S, G, E, Xn: r x r FP64 scratch; lam: r). W_sorted may alias X.
-void launch_refine_factor(const double* G, const float* T, int r, double* P, double* E, float* T_out,
-                          cudaStream_t st);
+void launch_refine_factor(const double* G, const float* T, int r, double* P, double* E, double* T64,
+                          float* T_out, cudaStream_t st);
+// C (FP32) = A (FP64) B (FP32), r x r, products and sums in FP64.
+void launch_dgemm_rr(const double* A, const float* B, int r, float* C, cudaStream_t st);
 void launch_refine_eigenvectors(const double* H, const float* X, int r, double* P, double* S, double* G, double* E,
                                 double* Xn, double* lam, double* sigma, float* W_sorted, cudaStream_t st);
 // c = V^T g (FP64), M x r V. The partial sums use at most DOT_MAX_BLOCKS row

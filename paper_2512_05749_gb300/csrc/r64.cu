@@ -70,6 +70,11 @@ __global__ void __launch_bounds__(256) k_dgemm_r(const TA* __restrict__ A, const
   }
 }
 
+__global__ void k_round_f32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
 template <typename TA, typename TB, typename TD, typename TC, bool TRANS_A>
 void dgemm_r(const TA* A, const TB* B, const TD* D, TC* C, int r, double alpha, double beta, double gamma,
              cudaStream_t st) {
@@ -77,91 +82,115 @@ void dgemm_r(const TA* A, const TB* B, const TD* D, TC* C, int r, double alpha, 
   k_dgemm_r<TA, TB, TD, TC, TRANS_A><<<grid, DG_T * DG_T, 0, st>>>(A, B, D, C, r, alpha, beta, gamma);
 }
 
-// One CTA: lambda_i = s_ii / g_ii (g = X^T X, r_ij = delta_ij - g_ij), the
-// clustering threshold delta and the correction E (see the file comment).
-// Frobenius norms bound the 2-norms of S - diag(lambda) and R; ||H|| is taken
-// as max |lambda_i| (1 + ||R||), the norm of X diag(lambda) X^T.
-__global__ void __launch_bounds__(1024) k_oa_update(const double* __restrict__ S, const double* __restrict__ G, int r,
-                                                    double* __restrict__ E, double* __restrict__ lam) {
-  __shared__ double lam_s[1024];
-  __shared__ double red[3][32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int a = tid; a < r; a += 1024) {
-    const double l = S[(int64_t)a * r + a] / G[(int64_t)a * r + a];
-    lam_s[a] = l;
-    lam[a] = l;
-  }
-  __syncthreads();
-  double off = 0.0, rr = 0.0, lmax = 0.0;
-  for (int e = tid; e < r * r; e += 1024) {
-    const int a = e / r, b = e % r;
-    const double sab = S[e] - (a == b ? lam_s[a] : 0.0);
-    const double rab = (a == b ? 1.0 : 0.0) - G[e];
+// Per row a (one CTA each): lambda_a = s_aa / g_aa (g = X^T X, r_ab = delta_ab - g_ab)
+// and the row's share of ||S - diag(lambda)||_F^2 and ||R||_F^2.
+__global__ void __launch_bounds__(256) k_oa_rows(const double* __restrict__ S, const double* __restrict__ G, int r,
+                                                 double* __restrict__ lam, double* __restrict__ part) {
+  __shared__ double red[2][8];
+  const int a = blockIdx.x, tid = threadIdx.x;
+  const double la = S[(int64_t)a * r + a] / G[(int64_t)a * r + a];
+  double off = 0.0, rr = 0.0;
+  for (int b = tid; b < r; b += 256) {
+    const double sab = S[(int64_t)a * r + b] - (a == b ? la : 0.0);
+    const double rab = (a == b ? 1.0 : 0.0) - G[(int64_t)a * r + b];
     off = fma(sab, sab, off);
     rr = fma(rab, rab, rr);
-    if (a == b) lmax = fmax(lmax, fabs(lam_s[a]));
+  }
+  off = warp_sum(off);
+  rr = warp_sum(rr);
+  if ((tid & 31) == 0) red[0][tid >> 5] = off, red[1][tid >> 5] = rr;
+  __syncthreads();
+  if (tid == 0) {
+    double o = 0.0, q = 0.0;
+    for (int w = 0; w < 8; ++w) o += red[0][w], q += red[1][w];
+    lam[a] = la;
+    part[2 * a] = o;
+    part[2 * a + 1] = q;
+  }
+}
+
+// Per row a (one CTA each): the clustering threshold delta (the row sums
+// reduced again in every CTA, fixed order) and row a of the correction E.
+// Frobenius norms bound the 2-norms of S - diag(lambda) and R; ||H|| is taken
+// as max |lambda_i| (1 + ||R||), the norm of X diag(lambda) X^T.
+__global__ void __launch_bounds__(256) k_oa_correction(const double* __restrict__ S, const double* __restrict__ G,
+                                                       const double* __restrict__ lam, const double* __restrict__ part,
+                                                       int r, double* __restrict__ E) {
+  __shared__ double red[3][8];
+  __shared__ double delta_s;
+  const int a = blockIdx.x, tid = threadIdx.x;
+  double off = 0.0, rr = 0.0, lmax = 0.0;
+  for (int b = tid; b < r; b += 256) {
+    off += part[2 * b];
+    rr += part[2 * b + 1];
+    lmax = fmax(lmax, fabs(lam[b]));
   }
   off = warp_sum(off);
   rr = warp_sum(rr);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  if (lane == 0) red[0][warp] = off, red[1][warp] = rr, red[2][warp] = lmax;
+  if ((tid & 31) == 0) red[0][tid >> 5] = off, red[1][tid >> 5] = rr, red[2][tid >> 5] = lmax;
   __syncthreads();
-  if (warp == 0) {
-    off = red[0][lane], rr = red[1][lane], lmax = red[2][lane];
-    off = warp_sum(off);
-    rr = warp_sum(rr);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if (lane == 0) red[0][0] = off, red[1][0] = rr, red[2][0] = lmax;
+  if (tid == 0) {
+    double o = 0.0, q = 0.0, m = 0.0;
+    for (int w = 0; w < 8; ++w) o += red[0][w], q += red[1][w], m = fmax(m, red[2][w]);
+    const double nR = sqrt(q);
+    delta_s = 2.0 * (sqrt(o) + m * (1.0 + nR) * nR);
   }
   __syncthreads();
-  const double nR = sqrt(red[1][0]);
-  const double delta = 2.0 * (sqrt(red[0][0]) + red[2][0] * (1.0 + nR) * nR);
-  for (int e = tid; e < r * r; e += 1024) {
-    const int a = e / r, b = e % r;
+  const double delta = delta_s, la = lam[a];
+  for (int b = tid; b < r; b += 256) {
+    const int64_t e = (int64_t)a * r + b;
     const double rab = (a == b ? 1.0 : 0.0) - G[e];
     double v;
     if (a == b) {
       v = 0.5 * rab;
     } else {
-      const double gap = lam_s[b] - lam_s[a];
-      v = fabs(gap) > delta ? (S[e] + lam_s[b] * rab) / gap : 0.5 * rab;
+      const double gap = lam[b] - la;
+      v = fabs(gap) > delta ? (S[e] + lam[b] * rab) / gap : 0.5 * rab;
     }
     E[e] = v;
   }
 }
 
 // Descending order of lam (ties by index): sigma[rank] = sqrt(lam), column j
-// of X (FP64) to column rank(j) of Ws (FP32).
-__global__ void __launch_bounds__(1024) k_sort_refined(const double* __restrict__ lam, const double* __restrict__ X,
-                                                       int r, double* __restrict__ sigma, float* __restrict__ Ws) {
+// of X (FP64) to column rank(j) of Ws (FP32). Every CTA ranks all r values
+// (in shared memory) and moves rows [16 blockIdx.x, 16 blockIdx.x + 16).
+__global__ void __launch_bounds__(256) k_sort_refined(const double* __restrict__ lam, const double* __restrict__ X,
+                                                      int r, double* __restrict__ sigma, float* __restrict__ Ws) {
+  __shared__ double lam_s[1024];
   __shared__ int rank_of[1024];
   const int tid = threadIdx.x;
-  for (int j = tid; j < r; j += 1024) {
-    const double lj = lam[j];
+  for (int j = tid; j < r; j += 256) lam_s[j] = lam[j];
+  __syncthreads();
+  for (int j = tid; j < r; j += 256) {
+    const double lj = lam_s[j];
     int rk = 0;
     for (int b = 0; b < r; ++b) {
-      const double lb = lam[b];
+      const double lb = lam_s[b];
       rk += (lb > lj) || (lb == lj && b < j);
     }
     rank_of[j] = rk;
-    sigma[rk] = lj > 0.0 ? sqrt(lj) : 0.0;
+    if (blockIdx.x == 0) sigma[rk] = lj > 0.0 ? sqrt(lj) : 0.0;
   }
   __syncthreads();
-  for (int e = tid; e < r * r; e += 1024) {
-    const int a = e / r, j = e % r;
-    Ws[(int64_t)a * r + rank_of[j]] = (float)X[e];
-  }
+  const int a1 = min(r, 16 * (int)blockIdx.x + 16);
+  for (int a = 16 * blockIdx.x; a < a1; ++a)
+    for (int j = tid; j < r; j += 256) Ws[(int64_t)a * r + rank_of[j]] = (float)X[(int64_t)a * r + j];
 }
 
 }  // namespace
 
-void launch_refine_factor(const double* G, const float* T, int r, double* P, double* E, float* T_out,
-                          cudaStream_t st) {
+void launch_refine_factor(const double* G, const float* T, int r, double* P, double* E, double* T64,
+                          float* T_out, cudaStream_t st) {
   dgemm_r<double, float, double, double, false>(G, T, nullptr, P, r, 1.0, 0.0, 0.0, st);     // P = G T
   dgemm_r<float, double, double, double, true>(T, P, nullptr, E, r, 1.0, 0.0, -1.0, st);     // E = T^T P - I
-  dgemm_r<float, double, float, float, false>(T, E, T, T_out, r, -0.5, 1.0, 0.0, st);        // T - T E / 2
+  dgemm_r<float, double, float, double, false>(T, E, T, T64, r, -0.5, 1.0, 0.0, st);         // T - T E / 2
+  k_round_f32<<<(unsigned)ceil_div((int64_t)r * r, 256), 256, 0, st>>>(T64, (int64_t)r * r, T_out);
+}
+
+void launch_dgemm_rr(const double* A, const float* B, int r, float* C, cudaStream_t st) {
+  dgemm_r<double, float, double, float, false>(A, B, nullptr, C, r, 1.0, 0.0, 0.0, st);
 }
 
 void launch_refine_eigenvectors(const double* H, const float* X, int r, double* P, double* S, double* G, double* E,
@@ -169,9 +198,11 @@ void launch_refine_eigenvectors(const double* H, const float* X, int r, double* 
   dgemm_r<double, float, double, double, false>(H, X, nullptr, P, r, 1.0, 0.0, 0.0, st);     // P = H X
   dgemm_r<float, double, double, double, true>(X, P, nullptr, S, r, 1.0, 0.0, 0.0, st);      // S = X^T H X
   dgemm_r<float, float, double, double, true>(X, X, nullptr, G, r, 1.0, 0.0, 0.0, st);       // G = X^T X
-  k_oa_update<<<1, 1024, 0, st>>>(S, G, r, E, lam);
-  dgemm_r<float, double, float, double, false>(X, E, X, Xn, r, 1.0, 1.0, 0.0, st);          // X + X E
-  k_sort_refined<<<1, 1024, 0, st>>>(lam, Xn, r, sigma, W_sorted);
+  double* part = Xn;  // 2 r doubles of row sums, consumed before Xn is written
+  k_oa_rows<<<r, 256, 0, st>>>(S, G, r, lam, part);
+  k_oa_correction<<<r, 256, 0, st>>>(S, G, lam, part, r, P);                                  // E into P
+  dgemm_r<float, double, float, double, false>(X, P, X, Xn, r, 1.0, 1.0, 0.0, st);          // X + X E
+  k_sort_refined<<<(unsigned)ceil_div(r, 16), 256, 0, st>>>(lam, Xn, r, sigma, W_sorted);
 }
 
 }  // namespace wssr

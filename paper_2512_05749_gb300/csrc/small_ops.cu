@@ -480,13 +480,17 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
     return;
   }
   if (OUT_R) {
-    // R = R' D^-1: column j scaled by 1 / d_j = sqrt(G_jj); zeros below the diagonal
+    // R = R' D^-1: column j scaled by 1 / d_j = sqrt(G_jj) (one division per column, in
+    // place of d); zeros below the diagonal
+    __syncthreads();
+    if (tid < r) d[tid] = 1.0 / d[tid];
+    __syncthreads();
     for (int i = warp; i < r; i += 32) {
       const int I = i / CB, ii = i % CB;
       float* Rrow = T + (int64_t)i * r;
       for (int j = lane; j < r; j += 32) {
         const int J = j / CB;
-        Rrow[j] = (I <= J && i <= j) ? (float)((double)B[blk_id(I, J, nb) * CBE + ii * CBP + lane] / d[j]) : 0.f;
+        Rrow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + ii * CBP + lane] * (float)d[j] : 0.f;
       }
     }
     return;

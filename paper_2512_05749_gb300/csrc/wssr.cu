@@ -101,7 +101,7 @@ struct wssr_ctx {
   double* G = nullptr;
   double* Gx = nullptr;        // FP64 Gram of the basis operand (its factor is T_X)
   float* Tref = nullptr;       // T_X refined in FP64 (Rayleigh-Ritz)
-  double* r64 = nullptr;       // FP64 refinement scratch: 5 r x r + r
+  double* r64 = nullptr;       // FP64 refinement scratch: 6 r x r + r
   float* T = nullptr;
   float* rot_log = nullptr;
   int* nsweeps = nullptr;
@@ -472,13 +472,14 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   double* rG = rS + (size_t)r * r;
   double* rE = rG + (size_t)r * r;
   double* rX = rE + (size_t)r * r;
-  double* rlam = rX + (size_t)r * r;
+  double* T64 = rX + (size_t)r * r;
+  double* rlam = T64 + (size_t)r * r;
   const float* TXu = h->TX;
   if (refine) {
     // the basis factor to FP64 orthonormality: X_h T' with T'^T G_x T' = I + O(E^2)
     Timed tr(h, WSSR_KCAT_RR, st);
-    launch_refine_factor(h->Gx, h->TX, r, P, rE, h->Tref, st);
-    h->launches += 3;
+    launch_refine_factor(h->Gx, h->TX, r, P, rE, T64, h->Tref, st);
+    h->launches += 4;
     TXu = h->Tref;
   }
   right_multiply_Y(h, h->Y, TXu, L, st);
@@ -508,9 +509,10 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   if (refine) {
     // one FP64 refinement sweep of the eigenvectors; Ritz values and order from it
     launch_refine_eigenvectors(h->G, on_cluster ? h->Wu : h->W, r, P, rS, rG, rE, rX, rlam, sig, h->W, st);
-    h->launches += 6;
+    h->launches += 7;
   }
-  launch_apply(TXu, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
+  if (refine) launch_dgemm_rr(T64, h->W, r, h->TW, st);  // T' W with T' in FP64
+  else launch_apply(TXu, r, r, h->W, h->TW, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
   h->c_ready = false;
   if (h->use_tc) {
     // V_out = Xh (T W) on the tensor cores (c = V_out^T g is a separate,
@@ -642,7 +644,7 @@ void wssr_default_options(wssr_options* opt) {
   opt->engine = WSSR_ENGINE_AUTO;
   opt->jacobi_sweeps = 12;
   opt->history = 0;
-  opt->fp64_refine = 1;
+  opt->fp64_refine = 0;
 }
 
 wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const wssr_options* opt_in,
@@ -726,7 +728,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(G, (size_t)r * r * d);
   ALLOC(Gx, (size_t)r * r * d);
   ALLOC(Tref, (size_t)r * r * f);
-  if (opt.fp64_refine) ALLOC(r64, ((size_t)5 * r * r + r) * d);
+  if (opt.fp64_refine) ALLOC(r64, ((size_t)6 * r * r + r) * d);
   ALLOC(T, (size_t)r * r * f);
   ALLOC(rot_log, (size_t)jacobi_log_elems(r, opt.jacobi_sweeps) * 2 * f);
   ALLOC(nsweeps, sizeof(int));

@@ -442,7 +442,7 @@ class WSSR:
     def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
                  dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
                  engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000, history: bool = False,
-                 r_reg: float = 0.0, fp64_refine: bool = True):
+                 r_reg: float = 0.0, fp64_refine: bool = False):
         opt = wssr_default_options()
         opt.fp64_refine = 1 if fp64_refine else 0
         opt.r_reg = r_reg

@@ -169,13 +169,13 @@ def test_woodbury_apply(W, mode, M, r):
 # The whole step
 # ---------------------------------------------------------------------------
 
-def run_step(W, w, dtype, engine="auto", m=2, mode="damped", floor=0.0, ld_pad=0, seed="step"):
+def run_step(W, w, dtype, engine="auto", m=2, mode="damped", floor=0.0, ld_pad=0, seed="step", refine=False):
     O, Oex = make_O(w, dtype, ld_pad=ld_pad)
     g = wl.gradient_np(w.M, 0, seed).astype(np.float32)
     V0 = wl.start_subspace_np(w.M, w.r, seed)
     Vprev = orc.init_subspace(Oex, V0, m_init=30).astype(np.float32)
     s = W.WSSR(w.N, w.M, w.r, w.lam, m=m, dtype=dtype, engine=engine, apply_mode=mode,
-               sigma_floor=floor)
+               sigma_floor=floor, fp64_refine=refine)
     delta, sigma, V = s.step(O, torch.from_numpy(g).to(dev()), torch.from_numpy(Vprev).to(dev()))
     s.check("step")
     out = delta.double().cpu().numpy(), sigma.cpu().numpy(), V.double().cpu().numpy()
@@ -200,10 +200,15 @@ def compare_step(out, ref, tol_delta, tol_sigma, tol_proj):
     return err_d, err_s, P
 
 
-@pytest.mark.parametrize("N,M,r", [(1024, 2048, 32), (1000, 2047, 24), (600, 3000, 64)])
-def test_step_f32(W, N, M, r):
+@pytest.mark.parametrize("refine", [False, True])
+@pytest.mark.parametrize("N,M,r", [(1024, 2048, 32), (1000, 2047, 24), (600, 3000, 64), (1200, 4000, 256)])
+def test_step_f32(W, N, M, r, refine):
+    """FP32 step against the oracle, with and without the FP64 refinement of
+    the Rayleigh-Ritz factor and eigenvectors (options.fp64_refine)."""
     w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.5, noise=1e-4, lam=1e-3)
-    out, ref, _ = run_step(W, w, "f32")
+    out, ref, _ = run_step(W, w, "f32", refine=refine)
+    e = step_errors(*out, *ref, run_step.last_g, w.lam)
+    print("refine" if refine else "fp32", (N, M, r), {k: f"{v:.2e}" for k, v in e.items()})
     compare_step(out, ref, 1e-5, 1e-4, 1e-3)
 
 
@@ -400,8 +405,8 @@ def step_errors(d, s, V, dr, sr, Vr, g, lam):
 # product, the r = 256 shared-memory Cholesky blocks and Jacobi ring, the
 # 3-term rotation with r-wide staging; M = 20000 leaves a ragged 64-parameter
 # block (20000 % 64 = 32) and a ragged 256-parameter pass B tile.
-@pytest.mark.parametrize("N,M", [(2048, 32768), (1536, 20000)])
-def test_step_bf16_rank256_tcgen05(W, N, M):
+@pytest.mark.parametrize("N,M,refine", [(2048, 32768, False), (1536, 20000, False), (2048, 32768, True)])
+def test_step_bf16_rank256_tcgen05(W, N, M, refine):
     """One tensor-core step at r = 256 against the FP64 oracle on the same bf16
     bytes, from a warm start; a Gaussian g and a g inside span(V_prev), for
     which delta is all low-rank part.
@@ -423,7 +428,7 @@ def test_step_bf16_rank256_tcgen05(W, N, M):
     w = wl.small_planted(N, M, r, K=min(N, 4 * r), sigma_power=1.2, noise=1e-4, lam=lam, dtype="bf16")
     O, Oex = make_O(w, "bf16", ld_pad=(-M) % 8)
     Vprev = warm_start_np(Oex, r, f"{N}-{M}")
-    s = W.WSSR(N, M, r, lam, m=2, dtype="bf16", engine="tcgen05")
+    s = W.WSSR(N, M, r, lam, m=2, dtype="bf16", engine="tcgen05", fp64_refine=refine)
     g1 = wl.gradient_np(M, 0, "r256").astype(np.float32)
     g2 = (Vprev.astype(np.float64) @ wl.gaussian_np((r,), "r256c")).astype(np.float32)
     tV = torch.from_numpy(Vprev).to(dev())
