@@ -198,7 +198,7 @@ def accuracy_on_sample(w, args, dev, cols: int):
     dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
     O_t = torch.from_numpy(O64.astype(np.float32)).to(dev).to(dt)
     s = WSSR(ws.N, cols, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine,
-             fp64_refine=bool(args.fp64_refine))
+             fp64_refine=None if args.fp64_refine < 0 else bool(args.fp64_refine))
     Vp, _ = s.init_subspace(O_t, torch.from_numpy(V0.astype(np.float32)).to(dev))
     g_t = torch.from_numpy(g64.astype(np.float32)).to(dev)
     d, sg, V = s.step(O_t, g_t, Vp)
@@ -503,7 +503,7 @@ def run_ours(args, w):
     V0 = wl.start_subspace_torch(w.M, w.r, dev, "bench")
     s = WSSR(w.N, w.M, w.r, w.lam, m=w.m, m_init=args.m_init, dtype=args.dtype, engine=args.engine,
              history=args.history > 0, apply_mode=args.apply, sigma_floor=resolve_sigma_floor(args, w),
-             r_reg=args.r_reg if args.path == "adaptive" else 0.0, fp64_refine=bool(args.fp64_refine))
+             r_reg=args.r_reg if args.path == "adaptive" else 0.0, fp64_refine=None if args.fp64_refine < 0 else bool(args.fp64_refine))
     step = AdaptiveStepper(s, w, dev, args) if args.path == "adaptive" else Stepper(s, w, dev, args)
     gs = step.inputs(max(1, args.steps))
     torch.cuda.synchronize()
@@ -968,7 +968,7 @@ def main():
     ap.add_argument("--accuracy-cols", type=int, default=2048,
                     help="parameter columns of the sample on which one GPU step is compared with the FP64 "
                          "oracle (0 = skip)")
-    ap.add_argument("--fp64-refine", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--fp64-refine", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP64 refinement of the basis factor and of the eigenvectors in the Rayleigh-Ritz "
                          "step (options.fp64_refine)")
     ap.add_argument("--compare-f32", type=int, default=2,

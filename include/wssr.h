@@ -107,8 +107,9 @@ typedef struct {
                            of span(V) joins the complement term */
   int32_t fp64_refine;  /* 1: the Rayleigh-Ritz step refines, in FP64, the basis factor (to an
                            FP64-orthonormal basis) and the FP32 Jacobi eigenvectors of the projected matrix
-                           (one Ogita-Aishima sweep); 0 (default): FP32 factor and eigenvectors, Ritz values
-                           from FP64 Rayleigh quotients */
+                           (one Ogita-Aishima sweep); 0: FP32 factor and eigenvectors, Ritz values from FP64
+                           Rayleigh quotients; -1 (default): 1 when O is FP32, 0 when O is BF16 (whose
+                           rounding of the basis sets the accuracy; the refinement then gains nothing) */
   int32_t reserved2;    /* 0 */
 } wssr_options;
 

@@ -102,9 +102,9 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
   const bool owner = i < h;
   const int l0 = sub * EC_SEG;
   // A sweep whose largest rotation has |tan| below t_stop leaves off-diagonal
-  // products of order t_stop^2 = tol / 16 relative: the next sweep would rotate
-  // nothing, so it is not run
-  const float t_stop = 0.25f * sqrtf(tol);
+  // products of order t_stop^2 = tol relative: the next sweep would rotate at
+  // most pairs at the threshold, so it is not run
+  const float t_stop = sqrtf(tol);
   int buf = 0, sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;

@@ -644,7 +644,7 @@ void wssr_default_options(wssr_options* opt) {
   opt->engine = WSSR_ENGINE_AUTO;
   opt->jacobi_sweeps = 12;
   opt->history = 0;
-  opt->fp64_refine = 0;
+  opt->fp64_refine = -1;
 }
 
 wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const wssr_options* opt_in,
@@ -669,7 +669,8 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   if (opt.history != 0 && opt.history != 1) return WSSR_ERR_INVALID_ARG;
   if (!(opt.r_reg >= 0.0 && opt.r_reg <= 1.0)) return WSSR_ERR_INVALID_ARG;
   if (opt.debug & ~WSSR_DEBUG_POISON) return WSSR_ERR_INVALID_ARG;
-  if (opt.fp64_refine != 0 && opt.fp64_refine != 1) return WSSR_ERR_INVALID_ARG;
+  if (opt.fp64_refine < -1 || opt.fp64_refine > 1) return WSSR_ERR_INVALID_ARG;
+  if (opt.fp64_refine == -1) opt.fp64_refine = opt.dtype == WSSR_DTYPE_F32 ? 1 : 0;
 
   wssr_ctx* h = new (std::nothrow) wssr_ctx();
   if (!h) return WSSR_ERR_OOM;

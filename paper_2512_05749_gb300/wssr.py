@@ -442,9 +442,11 @@ class WSSR:
     def __init__(self, N: int, M: int, r: int, lam: float, *, m: int = 2, m_init: int = 20,
                  dtype: str = "f32", apply_mode: str = "damped", sigma_floor: float = 0.0,
                  engine: str = "auto", jacobi_sweeps: int = 12, wait_cap: int = 2_000_000, history: bool = False,
-                 r_reg: float = 0.0, fp64_refine: bool = False):
+                 r_reg: float = 0.0, fp64_refine: Optional[bool] = None):
         opt = wssr_default_options()
-        opt.fp64_refine = 1 if fp64_refine else 0
+        # None: the library's default (refine when O is FP32)
+        if fp64_refine is not None:
+            opt.fp64_refine = 1 if fp64_refine else 0
         opt.r_reg = r_reg
         opt.m, opt.m_init, opt.jacobi_sweeps, opt.wait_cap = m, m_init, jacobi_sweeps, wait_cap
         opt.history = 1 if history else 0

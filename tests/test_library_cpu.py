@@ -36,10 +36,11 @@ def test_options_layout_and_defaults():
     assert (opt.m, opt.m_init, opt.dtype, opt.apply_mode, opt.engine, opt.jacobi_sweeps) == \
         (2, 20, W.WSSR_DTYPE_F32, W.WSSR_APPLY_DAMPED, W.WSSR_ENGINE_AUTO, 12)
     assert opt.wait_cap == 2_000_000
+    assert (opt.debug, opt.fp64_refine) == (0, -1)
 
 
 def test_status_strings():
-    for code in range(8):
+    for code in range(9):
         assert W.status_string(code) and W.status_string(code) != "unknown status"
 
 
