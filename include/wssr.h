@@ -143,9 +143,10 @@ void wssr_default_options(wssr_options* opt);
 
 /* Create a context for N samples, M parameters, rank r, damping lambda > 0.
  * Constraints: 2 <= N, 8 <= r <= 1024, r % 8 == 0, r <= N - 1, r <= M.
- * The tensor-core engine (and with it history averaging and the matrix-free
- * operator) takes r <= 256: WSSR_ENGINE_TCGEN05 with a larger r returns
- * WSSR_ERR_UNSUPPORTED, WSSR_ENGINE_AUTO selects the SIMT engine. Above
+ * The tensor-core engine (and with it history averaging) takes r <= 512, its
+ * matrix-free network operator r <= 256: WSSR_ENGINE_TCGEN05 with a larger r
+ * returns WSSR_ERR_UNSUPPORTED (a step through the network operator at a
+ * working rank above 256 too), WSSR_ENGINE_AUTO selects the SIMT engine. Above
  * r = 256 the r x r Cholesky factor and the Rayleigh-Ritz eigensolve keep
  * their matrix in the workspace instead of shared memory (slower).
  * Allocates the whole workspace (about 3 M r floats + small terms).

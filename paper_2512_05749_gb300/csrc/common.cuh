@@ -12,11 +12,14 @@ namespace wssr {
 typedef __nv_bfloat16 bf16;
 
 // Largest rank of a handle (the SIMT engine and the r-dimensional kernels),
-// largest rank of the tensor-core engine (one 128 x r FP32 accumulator per
-// 256 TMEM columns), and largest rank whose r x r factor and eigensolve keep
-// their matrix in one CTA's shared memory (above it they use a device workspace).
+// largest rank of the tensor-core engine (a 128 x r FP32 accumulator fills at
+// most the 512 TMEM columns: two per CTA up to r = 256, one above), of its
+// matrix-free network operator, and largest rank whose r x r factor and
+// eigensolve keep their matrix in one CTA's shared memory (above it they use a
+// device workspace).
 constexpr int WSSR_RANK_MAX = 1024;
-constexpr int WSSR_TC_RANK_MAX = 256;
+constexpr int WSSR_TC_RANK_MAX = 512;
+constexpr int WSSR_MF_RANK_MAX = 256;
 constexpr int WSSR_SMEM_RANK_MAX = 256;
 
 // Sticky device status: the first error code written wins.

@@ -47,7 +47,7 @@ struct Ctl {
   uint32_t tmem;
   int abort;
   float mu[2 * BM];
-  float ysum[256];
+  float ysum[512];
   double red[8][BM];
 };
 
@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* base = align1024(smem_raw);
   const uint32_t a_blk = A_BYTES * MT;  // one 64-parameter block of MT x 128 rows
   const uint32_t a_bytes = a_blk * KB;
-  const uint32_t xbox = (uint32_t)nmma * BK * 2;
+  // operand rows per box (a TMA box has at most 256 rows): above r = 256 two boxes,
+  // two MMAs of N <= 256 into TMEM columns 0 and 256 (then MT = 1)
+  const int n0 = nmma > 256 ? 256 : nmma, nh = nmma > 256 ? 2 : 1;
+  const uint32_t xbox = (uint32_t)(nh * n0) * BK * 2;
   const uint32_t stage_bytes = a_bytes + xbox * KB;
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -161,21 +164,27 @@ __global__ void __launch_bounds__(THREADS, 1)
                  for (int b = 0; b < KB; ++b)
                    tma_load_2d_hint(st + b * a_blk, &tmO, bar, k + b * BK, n_tile * BM * MT, pol_o);
                  for (int b = 0; b < KB; ++b)
-                   tma_load_3d_hint(st + a_bytes + b * xbox, &tmX, bar, 0, 0, (k + b * BK) / BK, pol_x);
+                   for (int hh = 0; hh < nh; ++hh)
+                     tma_load_3d_hint(st + a_bytes + b * xbox + hh * n0 * BK * 2, &tmX, bar, 0, 256 * hh,
+                                      (k + b * BK) / BK, pol_x);
                });
     }
   } else if (warp == 1) {
     if (lane == 0 && nk > 0) {
-      const uint32_t idesc = make_idesc(BM, nmma, 0, 0);
+      const uint32_t idesc0 = make_idesc(BM, n0, 0, 0);
+      const uint32_t idesc1 = make_idesc(BM, nh > 1 ? nmma - 256 : n0, 0, 0);
       mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
         for (int b = 0; b < KB; ++b)
 #pragma unroll
           for (int kk = 0; kk < BK / UK; ++kk) {
-            const uint64_t db = smem_desc(sa + a_bytes + b * xbox + kk * 32, 16, 1024);
+            for (int hh = 0; hh < nh; ++hh) {
+              const uint64_t db = smem_desc(sa + a_bytes + b * xbox + hh * n0 * BK * 2 + kk * 32, 16, 1024);
 #pragma unroll
-            for (int a = 0; a < MT; ++a)
-              mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + b * a_blk + a * A_BYTES + kk * 32, 16, 1024),
-                       db, idesc, (!first || b > 0 || kk > 0) ? 1u : 0u);
+              for (int a = 0; a < MT; ++a)
+                mma_bf16(tmem + (uint32_t)((a + hh) * 256),
+                         smem_desc(sa + b * a_blk + a * A_BYTES + kk * 32, 16, 1024), db, hh ? idesc1 : idesc0,
+                         (!first || b > 0 || kk > 0) ? 1u : 0u);
+            }
           }
       });
     }
@@ -230,7 +239,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   const uint32_t a_bytes = A_BYTES * MT;
-  const uint32_t stage_bytes = a_bytes + (uint32_t)nmma * BK * 2;
+  // operand rows per box (at most 256): above r = 256 two boxes and two MMAs of
+  // N <= 256 into TMEM columns 0 and 256 (then MT = 1)
+  const int n0 = nmma > 256 ? 256 : nmma, nh = nmma > 256 ? 2 : 1;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)(nh * n0) * BK * 2;
   Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * BM * MT;
@@ -259,22 +271,26 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                  for (int b = 0; b < 2 * MT; ++b)
                    tma_load_2d_hint(st + b * 8192, &tmO, bar, (int)m0 + 64 * b, n, pol_o);
-                 tma_load_2d_hint(st + a_bytes, &tmY, bar, n, 0, pol_y);
+                 for (int hh = 0; hh < nh; ++hh)
+                   tma_load_2d_hint(st + a_bytes + hh * n0 * BK * 2, &tmY, bar, n, 256 * hh, pol_y);
                });
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(BM, nmma, 1, 0);
+      const uint32_t idesc0 = make_idesc(BM, n0, 1, 0);
+      const uint32_t idesc1 = make_idesc(BM, nh > 1 ? nmma - 256 : n0, 1, 0);
       mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
         // A is MN-major: 16 samples = two 8-row groups (SBO 1024), 64-parameter
         // boxes 8 KB apart (LBO)
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk) {
-          const uint64_t db = smem_desc(sa + a_bytes + kk * 32, 16, 1024);
+          for (int hh = 0; hh < nh; ++hh) {
+            const uint64_t db = smem_desc(sa + a_bytes + hh * n0 * BK * 2 + kk * 32, 16, 1024);
 #pragma unroll
-          for (int a = 0; a < MT; ++a)
-            mma_bf16(tmem + (uint32_t)(a * 256), smem_desc(sa + a * A_BYTES + kk * 2048, 8192, 1024), db,
-                     idesc, (!first || kk > 0) ? 1u : 0u);
+            for (int a = 0; a < MT; ++a)
+              mma_bf16(tmem + (uint32_t)((a + hh) * 256), smem_desc(sa + a * A_BYTES + kk * 2048, 8192, 1024), db,
+                       hh ? idesc1 : idesc0, (!first || kk > 0) ? 1u : 0u);
+          }
         }
       });
     }
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_ld16(tmem + (uint32_t)(a * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
         if (ok && m < M) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 256 ? c + i : 255];
+          for (int i = 0; i < 16; ++i) v[i] -= mu * ctl->ysum[c + i < 512 ? c + i : 511];
           if (Zadd) {
 #pragma unroll
             for (int i = 0; i < 16; ++i)
@@ -500,6 +516,91 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, (uint32_t)tmem_cols);
+  }
+}
+
+// Gram above r = 256 (r <= 512): CTA (split, rb) computes rows [128 rb, 128 rb + 128)
+// of the split's partial Gram, all r columns, in one 128 x r accumulator (two
+// MMAs of N <= 256 into TMEM columns 0 and 256). The B tile (all r rows of
+// XB, two 256-row boxes) is loaded per stage; the A tile is rows 128 rb.. of
+// the same tile (XA = XB) or a 128-row box of XA (CROSS).
+template <bool CROSS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gram_big(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int r, int nmma,
+                  int stages, int k_chunks, int kc_per_split, float* __restrict__ Gp, uint64_t limit_ns,
+                  int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  const uint32_t a_bytes = CROSS ? A_BYTES : 0u;
+  const uint32_t b_half = 256 * BK * 2;  // one 256-row box
+  const uint32_t stage_bytes = a_bytes + 2 * b_half;
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int split = blockIdx.x, rb = blockIdx.y;
+  const int kc0 = split * kc_per_split;
+  const int kc1 = kc0 + kc_per_split < k_chunks ? kc0 + kc_per_split : k_chunks;
+  const int nk = kc1 - kc0;
+  if (threadIdx.x == 0) {
+    for (int s2 = 0; s2 < stages; ++s2) {
+      mbar_init(&ctl->full[s2], 1);
+      mbar_init(&ctl->empty[s2], 1);
+    }
+    mbar_init(&ctl->accum, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem, 512u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem;
+  if (warp == 0) {
+    if (lane == 0 && nk > 0)
+      producer(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](int i, uint8_t* st, uint64_t* bar) {
+        if (CROSS) tma_load_3d(st, &tmA, bar, 0, 128 * rb, kc0 + i);
+        tma_load_3d(st + a_bytes, &tmB, bar, 0, 0, kc0 + i);
+        tma_load_3d(st + a_bytes + b_half, &tmB, bar, 0, 256, kc0 + i);
+      });
+  } else if (warp == 1) {
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc0 = make_idesc(BM, 256, 0, 0);
+      const uint32_t idesc1 = make_idesc(BM, nmma - 256, 0, 0);
+      mma_loop(ctl, base, stage_bytes, stages, nk, limit_ns, status, [&](uint32_t sa, bool first) {
+        const uint32_t sa_a = CROSS ? sa : sa + (uint32_t)(128 * rb) * BK * 2;
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          const uint64_t da = smem_desc(sa_a + kk * 32, 16, 1024);
+          for (int hh = 0; hh < 2; ++hh)
+            mma_bf16(tmem + (uint32_t)(hh * 256), da, smem_desc(sa + a_bytes + hh * b_half + kk * 32, 16, 1024),
+                     hh ? idesc1 : idesc0, (!first || kk > 0) ? 1u : 0u);
+        }
+      });
+    }
+  } else {
+    const int q = warp & 3;
+    const bool ok = nk > 0 && mbar_wait(&ctl->accum, 0, limit_ns, &ctl->abort);
+    if (!ok && nk > 0) timeout(ctl, status);
+    tc_fence_after();
+    const int i = 128 * rb + q * 32 + lane;
+    float* out = Gp + ((int64_t)split * r + i) * r;
+    for (int c = 0; c < nmma; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+      if (i < r) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          if (c + j < r && WSSR_IN_BOUNDS(((int64_t)split * r + i) * r + c + j + 3,
+                                          ceil_div(k_chunks, kc_per_split) * r * r, status))
+            *reinterpret_cast<float4*>(out + c + j) =
+                ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512u);
   }
 }
 
@@ -810,7 +911,7 @@ bool tc_supported(int dev) {
 }
 
 int tc_passA_splits(int64_t N, int64_t M, int r, int num_sms) {
-  const int64_t n_tiles = ceil_div(N, 2 * BM), k_chunks = ceil_div(M, BK);
+  const int64_t n_tiles = ceil_div(N, (nmma_for(r) > 256 ? 1 : 2) * BM), k_chunks = ceil_div(M, BK);
   int64_t S = num_sms / gcd64(n_tiles, num_sms);
   while (n_tiles * S < 2 * num_sms) S *= 2;
   int64_t cap = k_chunks / 8;
@@ -842,31 +943,39 @@ int tc_passA_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
     }
     if (n == 3) rotate = rt != 0;
   }
-  const int MT = 2;
+  // two 128-sample accumulators per CTA up to r = 256; one (of r columns, two MMAs) above
+  const int MT = nmma > 256 ? 1 : 2;
+  const int nb_rows = nmma > 256 ? 2 * 256 : nmma;  // operand rows loaded per 64-parameter block
   const int n_tiles2 = (int)ceil_div(N, (int64_t)BM * MT);
   if (group > n_tiles2) group = n_tiles2;
   size_t stages = 0;
   for (;; --KB) {
-    const size_t stage = (size_t)KB * (A_BYTES * MT + (size_t)nmma * BK * 2);
+    const size_t stage = (size_t)KB * (A_BYTES * MT + (size_t)nb_rows * BK * 2);
     stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
     if (stages >= 2 || KB == 1) break;
   }
   if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmX;
   if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, BK, (uint32_t)(BM * MT), true)) return -1;
-  if (!encode_blocked(&tmX, XhatT, M, r, (uint32_t)nmma)) return -1;
+  if (!encode_blocked(&tmX, XhatT, M, r, (uint32_t)(nmma > 256 ? 256 : nmma))) return -1;
   const int k_chunks = (int)ceil_div(M, (int64_t)BK * KB);
   const int kc_per_split = (int)ceil_div(k_chunks, splits);
   const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
-  const size_t smem = 1024 + stages * (size_t)KB * (A_BYTES * MT + (size_t)nmma * BK * 2) + sizeof(Ctl);
+  const size_t smem = 1024 + stages * (size_t)KB * (A_BYTES * MT + (size_t)nb_rows * BK * 2) + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tc_passA<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passA<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  k_tc_passA<2><<<(unsigned)(n_tiles2 * s_eff), THREADS, smem, st>>>(
-      tmO, tmX, N, r, nmma, 512, (int)stages, KB, n_tiles2, s_eff, group, k_chunks,
-      kc_per_split, rotate, Yp, (uint64_t)wait_us * 1000ull, status);
+  if (MT == 2)
+    k_tc_passA<2><<<(unsigned)(n_tiles2 * s_eff), THREADS, smem, st>>>(
+        tmO, tmX, N, r, nmma, 512, (int)stages, KB, n_tiles2, s_eff, group, k_chunks,
+        kc_per_split, rotate, Yp, (uint64_t)wait_us * 1000ull, status);
+  else
+    k_tc_passA<1><<<(unsigned)(n_tiles2 * s_eff), THREADS, smem, st>>>(
+        tmO, tmX, N, r, nmma, 512, (int)stages, KB, n_tiles2, s_eff, group, k_chunks,
+        kc_per_split, rotate, Yp, (uint64_t)wait_us * 1000ull, status);
   *splits_used = s_eff;
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
@@ -876,33 +985,46 @@ int tc_passB_launch(const void* O, int64_t ldo, int64_t N, int64_t M, const void
                     int compute_mu, int64_t wait_us, int* status, cudaStream_t st, const float* Zadd,
                     const float* wgt, float* g_out, const double* wsum) {
   if (!compute_mu) wgt = nullptr, g_out = nullptr;  // the weighted sums ride on the column-mean pass
-  constexpr int MT = 2;
   const int nmma = nmma_for(r);
-  const size_t stage = (size_t)A_BYTES * MT + (size_t)nmma * BK * 2;
+  // two 128-parameter accumulators per CTA up to r = 256; one (of r columns, two MMAs) above
+  const int MT = nmma > 256 ? 1 : 2;
+  const int nb_rows = nmma > 256 ? 2 * 256 : nmma;
+  const size_t stage = (size_t)A_BYTES * MT + (size_t)nb_rows * BK * 2;
   size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
   if (stages > MAX_STAGES) stages = MAX_STAGES;
   CUtensorMap tmO, tmY;
   if (!encode_2d(&tmO, O, (uint64_t)M, (uint64_t)N, (uint64_t)ldo * 2, 64, BK, true)) return -1;
-  if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)nmma, true)) return -1;
+  if (!encode_2d(&tmY, YhatT, (uint64_t)N, (uint64_t)r, (uint64_t)ldy * 2, BK, (uint32_t)(nmma > 256 ? 256 : nmma),
+                 true))
+    return -1;
   const size_t smem = 1024 + stages * stage + sizeof(Ctl);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_passB<2, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_tc_passB<1, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_tc_passB<0, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_passB<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
   dim3 grid((unsigned)ceil_div(M, (int64_t)BM * MT));
   const uint64_t lim = (uint64_t)wait_us * 1000ull;
-  if (compute_mu && wgt && g_out && wsum)
-    k_tc_passB<2, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
-                                                   ldz, mu_io, Zadd, wgt, g_out, wsum, lim, status);
-  else if (compute_mu)
-    k_tc_passB<1, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
-                                                   ldz, mu_io, Zadd, nullptr, nullptr, nullptr, lim, status);
-  else
-    k_tc_passB<0, MT><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z, (bf16*)ZT,
-                                                   ldz, mu_io, Zadd, nullptr, nullptr, nullptr, lim, status);
+  const int mode = (compute_mu && wgt && g_out && wsum) ? 2 : (compute_mu ? 1 : 0);
+  if (mode != 2) wgt = nullptr, g_out = nullptr, wsum = nullptr;
+#define WSSR_PASSB(MU_, MT_)                                                                                   \
+  k_tc_passB<MU_, MT_><<<grid, THREADS, smem, st>>>(tmO, tmY, N, M, r, nmma, 512, (int)stages, ysum, Z,          \
+                                                    (bf16*)ZT, ldz, mu_io, Zadd, wgt, g_out, wsum, lim, status)
+  if (MT == 2) {
+    if (mode == 2) WSSR_PASSB(2, 2);
+    else if (mode == 1) WSSR_PASSB(1, 2);
+    else WSSR_PASSB(0, 2);
+  } else {
+    if (mode == 2) WSSR_PASSB(2, 1);
+    else if (mode == 1) WSSR_PASSB(1, 1);
+    else WSSR_PASSB(0, 1);
+  }
+#undef WSSR_PASSB
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -922,6 +1044,34 @@ int gram_launch_impl(const void* XA, const void* XB, int64_t L, int r, int split
                      int* status, cudaStream_t st, int* splits_used) {
   const bool cross = XB != nullptr;
   const int nmma = nmma_for(r);
+  if (nmma > 256) {
+    // rows in blocks of 128 over a second grid dimension, two 256-row boxes of XB per stage
+    const size_t stage = (cross ? (size_t)A_BYTES : 0) + (size_t)2 * 256 * BK * 2;
+    size_t stages = (227 * 1024 - 1024 - sizeof(Ctl)) / stage;
+    if (stages > MAX_STAGES) stages = MAX_STAGES;
+    CUtensorMap tma, tmb;
+    if (!encode_blocked(&tma, XA, L, r, 128u)) return -1;
+    if (!encode_blocked(&tmb, cross ? XB : XA, L, r, 256u)) return -1;
+    const int k_chunks = (int)ceil_div(L, BK);
+    const int kc_per_split = (int)ceil_div(k_chunks, splits);
+    const int s_eff = (int)ceil_div(k_chunks, kc_per_split);
+    const size_t smem = 1024 + stages * stage + sizeof(Ctl);
+    static bool attr_big = false;
+    if (!attr_big) {
+      cudaFuncSetAttribute(k_tc_gram_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_tc_gram_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr_big = true;
+    }
+    dim3 grid((unsigned)s_eff, (unsigned)ceil_div(r, 128));
+    if (cross)
+      k_tc_gram_big<true><<<grid, THREADS, smem, st>>>(tma, tmb, r, nmma, (int)stages, k_chunks, kc_per_split, Gp,
+                                                       (uint64_t)wait_us * 1000ull, status);
+    else
+      k_tc_gram_big<false><<<grid, THREADS, smem, st>>>(tma, tmb, r, nmma, (int)stages, k_chunks, kc_per_split, Gp,
+                                                        (uint64_t)wait_us * 1000ull, status);
+    *splits_used = s_eff;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
+  }
   const int rows = r <= 128 ? 128 : 256;
   const int tmem_cols = rows == 256 ? 512 : tmem_cols_for(nmma);
   const size_t stage = (size_t)rows * BK * 2 + (cross ? (size_t)nmma * BK * 2 : 0);

@@ -580,7 +580,7 @@ wssr_status check_op(const wssr_ctx* h, const wssr_operator* op) {
   if (op->kind == WSSR_OP_MLP) {
     if (!op->mlp || !op->theta || !op->x) return WSSR_ERR_INVALID_ARG;
     if (mlp_Mp(op->mlp) != h->M || h->N > mlp_Nmax(op->mlp)) return WSSR_ERR_INVALID_ARG;
-    if (!h->use_tc) return WSSR_ERR_UNSUPPORTED;
+    if (!h->use_tc || h->r > WSSR_MF_RANK_MAX) return WSSR_ERR_UNSUPPORTED;
     return WSSR_OK;
   }
   if (op->kind != WSSR_OP_DENSE || !op->O || op->ld < h->M) return WSSR_ERR_INVALID_ARG;
@@ -608,7 +608,9 @@ void configure_rank(wssr_ctx* h, int r) {
   h->r = r;
   h->splits_simt = passA_simt_splits(h->N, h->M, r, h->num_sms);
   h->splits_tc = h->use_tc ? tc_passA_splits(h->N, h->M, r, h->num_sms) : 1;
-  h->splits_mf = (h->use_tc && h->M % 64 == 0) ? tc_mf_jvp_splits(h->N, h->M / 64, r, h->num_sms) : 1;
+  h->splits_mf = (h->use_tc && h->M % 64 == 0 && r <= WSSR_MF_RANK_MAX)
+                    ? tc_mf_jvp_splits(h->N, h->M / 64, r, h->num_sms)
+                    : 1;
   h->ldy = (h->N + r + 7) / 8 * 8;  // the operand copy of Y also holds the history rows
   h->mu_valid = false;
   h->c_ready = false;

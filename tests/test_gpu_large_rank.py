@@ -1,8 +1,10 @@
 """GPU parity above rank 256 (the paper's adaptive runs reach r_max of
-200-1600, Section 4.3 and Tab. 2): the SIMT engine with the r x r Cholesky
-factor and the Rayleigh-Ritz eigensolve working from the device workspace,
-against the FP64 oracle; and an adaptive chain whose maximum rank grows
-across 256 (Eq. (ruler), Algorithm 2).
+200-1600, Section 4.3 and Tab. 2): the tensor-core engine up to r = 512 (one
+128 x r TMEM accumulator per CTA, two MMAs of N <= 256; the Gram in 128-row
+blocks), the SIMT engine above, with the r x r Cholesky factor and the
+Rayleigh-Ritz eigensolve working from the device workspace, against the FP64
+oracle; a history-averaged step at r = 320 on the tensor cores; and an
+adaptive chain whose maximum rank grows across 256 (Eq. (ruler), Algorithm 2).
 
 The start is ten subspace iterations from a Gaussian block, as converged as
 the start of the lower-rank tests (the oracle's cold start ends in a one-sided
@@ -47,15 +49,23 @@ def compare(out, ref, tol_d, tol_s, tol_p):
 @pytest.mark.parametrize("dtype,engine,N,M,r,tols", [
     ("f32", "simt", 700, 1500, 320, (1e-5, 1e-4, 1e-3)),
     ("bf16", "auto", 800, 1600, 384, (1e-3, 1e-2, 5e-2)),
+    # r = 264: the second MMA of each product has N = 16; M = 3000 leaves a ragged block
+    ("bf16", "tcgen05", 600, 3000, 264, (1e-3, 1e-2, 5e-2)),
+    # r = 512: both 256-column halves full; 2056 = 32 x 64 + 8
+    ("bf16", "tcgen05", 1100, 2056, 512, (1e-3, 1e-2, 5e-2)),
 ])
 def test_step_above_rank_256(dtype, engine, N, M, r, tols):
     from paper_2512_05749_gb300 import WSSR
+    if engine == "tcgen05":
+        tc_or_skip()
     w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.2, noise=1e-4, lam=1e-3, dtype=dtype)
     O = wl.planted_O_np(w).astype(np.float32)
     Oex = bf16_round(O) if dtype == "bf16" else O.astype(np.float64)
     V = orc.subspace_iteration(orc.centre(Oex), wl.start_subspace_np(M, r, "lrk"), 10).astype(np.float32)
     g = wl.gradient_np(M, 0, "lrk").astype(np.float32)
     s = WSSR(N, M, r, w.lam, m=2, dtype=dtype, engine=engine)
+    if dtype == "bf16":
+        assert s.engine == "tcgen05" or not tc_available()
     d, sg, Vo = s.step(t(O, torch.bfloat16 if dtype == "bf16" else torch.float32), t(g), t(V))
     s.check("step above rank 256")
     ref = orc.wssr_step(Oex, g.astype(np.float64), V.astype(np.float64), w.lam, 2)
@@ -63,18 +73,58 @@ def test_step_above_rank_256(dtype, engine, N, M, r, tols):
     s.close()
 
 
-def test_tcgen05_rejects_rank_above_256():
+def tc_available():
     from paper_2512_05749_gb300 import wssr as W
     try:
         W.WSSR(64, 64, 8, 1e-3, dtype="bf16", engine="tcgen05").close()
     except W.WSSRError as e:
         if e.code == W.WSSR_ERR_UNSUPPORTED:
-            pytest.skip("tcgen05 engine not available")
+            return False
         raise
+    return True
+
+
+def tc_or_skip():
+    if not tc_available():
+        pytest.skip("tcgen05 engine not available")
+
+
+def test_tcgen05_rejects_rank_above_512():
+    from paper_2512_05749_gb300 import wssr as W
+    tc_or_skip()
     with pytest.raises(W.WSSRError) as e:
-        W.WSSR(600, 600, 264, 1e-3, dtype="bf16", engine="tcgen05")
+        W.WSSR(600, 600, 520, 1e-3, dtype="bf16", engine="tcgen05")
     assert e.value.code == W.WSSR_ERR_UNSUPPORTED
-    s = W.WSSR(600, 600, 264, 1e-3, dtype="bf16", engine="auto")  # the SIMT engine takes it
+    s = W.WSSR(600, 600, 520, 1e-3, dtype="bf16", engine="auto")  # the SIMT engine takes it
+    assert s.engine == "simt"
+    s.close()
+    s = W.WSSR(600, 600, 512, 1e-3, dtype="bf16", engine="auto")
+    assert s.engine == "tcgen05"
+    s.close()
+
+
+def test_averaged_step_rank_320_tcgen05():
+    """History averaging (Section 4.1, Eq. (Ohat)-(barS)) at r = 320 on the
+    tensor cores: the cross Gram of the history rows in 128-row blocks and the
+    history term's rotation, against the oracle's averaged step."""
+    from paper_2512_05749_gb300 import WSSR
+    tc_or_skip()
+    N, M, r, lam, weight = 900, 2000, 320, 1e-3, 0.6
+    w = wl.small_planted(N, M, r, K=min(N, M), sigma_power=1.2, noise=1e-4, lam=lam, dtype="bf16")
+    O = wl.planted_O_np(w).astype(np.float32)
+    Oex = bf16_round(O)
+    V = orc.subspace_iteration(orc.centre(Oex), wl.start_subspace_np(M, r, "h320"), 10).astype(np.float32)
+    sp = np.linspace(0.5, 0.01, r)
+    Lp = wl.gaussian_np((r,), "h320L")
+    g = wl.gradient_np(M, 0, "h320").astype(np.float32)
+    s = WSSR(N, M, r, lam, m=2, dtype="bf16", engine="tcgen05", history=True)
+    d, sg, Vo, Lb, gb = s.step_averaged(t(O, torch.bfloat16), t(g), t(V), t(sp, torch.float64),
+                                        t(Lp, torch.float64), weight)
+    s.check("averaged step at r = 320")
+    dr, sr, Vr, Lr, gr = orc.wssr_step_averaged(Oex, g.astype(np.float64), V.astype(np.float64), sp, Lp, lam, 2,
+                                                weight)
+    compare((d.double().cpu().numpy(), sg.cpu().numpy(), Vo.double().cpu().numpy()), (dr, sr, Vr), 1e-3, 1e-2,
+            5e-2)
     s.close()
 
 
