@@ -123,7 +123,10 @@ def test_averaged_step_rank_320_tcgen05():
     s.check("averaged step at r = 320")
     dr, sr, Vr, Lr, gr = orc.wssr_step_averaged(Oex, g.astype(np.float64), V.astype(np.float64), sp, Lp, lam, 2,
                                                 weight)
-    compare((d.double().cpu().numpy(), sg.cpu().numpy(), Vo.double().cpu().numpy()), (dr, sr, Vr), 1e-3, 1e-2,
+    # delta's low-rank part is about sqrt(r / M) = 0.4 of its norm here (against 0.12 in the
+    # rank-32 tests) and moves by about 2 u / sqrt(3) = 2.3e-3 per bf16 rounding of the basis:
+    # delta bound 5e-3 (measured 1.2e-3)
+    compare((d.double().cpu().numpy(), sg.cpu().numpy(), Vo.double().cpu().numpy()), (dr, sr, Vr), 5e-3, 1e-2,
             5e-2)
     s.close()
 
