@@ -1,6 +1,6 @@
 // Rayleigh-Ritz eigensolve of the r x r matrix H = (Y T)^T (Y T) / N on a
 // thread-block cluster (Section 4.2: the SVD of the small projected block
-// that replaces Algorithm 1's |diag R| step; r <= 256).
+// that replaces Algorithm 1's |diag R| step; r <= 512).
 //
 // Method: one-sided (Hestenes) cyclic Jacobi on a square root B of H
 // (B = R from the Cholesky factorisation H = R^T R). Rotating column pairs of
@@ -16,15 +16,16 @@
 // sums the partials in rank order, so all CTAs take bit-identical rotation
 // decisions without further communication.
 //
-// Layout: CTA c of the cluster holds rows [c RL, c RL + RL) of B and W, with
-// RL = ceil(r / EC_CLUSTER), column-major in shared memory (column pitch
-// EC_LD = 33 floats, so a warp's eight pairs x four row segments hit 32
-// distinct banks). Round k pairs index 0 with ring position n1 - 1 + k and
-// ring positions (i - 1 + k, n1 - 1 - i + k) mod n1 (n1 = r - 1), the
-// round-robin ordering of the one-CTA Jacobi. Four threads share a pair, each
-// with eight consecutive rows.
+// Layout: CTA c of the cluster holds rows [c RL, c RL + RL) of B (and of W),
+// with RL = ceil(r / 8), column-major in shared memory (see EcCfg for the
+// column pitch). Round k pairs index 0 with ring position n1 - 1 + k and ring
+// positions (i - 1 + k, n1 - 1 - i + k) mod n1 (n1 = r - 1), the round-robin
+// ordering of the one-CTA Jacobi. Four threads share a pair, each with a
+// segment of consecutive rows. Above r = 256, W does not fit beside B: rank 0
+// logs every round's rotations in the one-CTA Jacobi's log format and the
+// replay kernel builds W from them.
 //
-// After the sweeps: W is written unsorted; the FP64 Rayleigh quotients
+// After the sweeps: W is written (or replayed) unsorted; the FP64 Rayleigh quotients
 // w_j^T H w_j (second-order accurate in the eigenvector error) give the Ritz
 // values, which rank the columns in descending order.
 #include <cooperative_groups.h>
@@ -39,19 +40,39 @@ namespace wssr {
 namespace {
 
 constexpr int EC_CLUSTER = 8;
-constexpr int EC_THREADS = 512;
-constexpr int EC_MAXR = 256;
-constexpr int EC_RL = EC_MAXR / EC_CLUSTER;  // 32 rows per CTA at most
-constexpr int EC_SEG = EC_RL / 4;            // rows per thread (four threads per pair)
-constexpr int EC_LD = EC_RL + 1;
 
+// Two shapes: up to r = 256, 512 threads (four per pair, eight rows each) and
+// W in shared memory next to B; up to r = 512, 1024 threads (four per pair,
+// sixteen rows each), B alone in shared memory and the rotations logged for
+// the replay kernel (B and W would not fit). Column pitch LD: 33 words for 32
+// rows; 73 for 64 rows, with rows 32..63 shifted by 8 words, so that the four
+// row segments of a pair start in four different bank groups.
+template <int RMAX>
+struct EcCfg;
+template <>
+struct EcCfg<256> {
+  static constexpr int THREADS = 512, RL = 32, SEG = 8, LD = 33;
+  static constexpr bool W_SMEM = true;
+};
+template <>
+struct EcCfg<512> {
+  static constexpr int THREADS = 1024, RL = 64, SEG = 16, LD = 73;
+  static constexpr bool W_SMEM = false;
+};
+
+template <int RMAX>
+__device__ __forceinline__ int ec_pos(int l) {
+  return RMAX == 512 ? l + (l >= 32 ? 8 : 0) : l;
+}
+
+template <int RMAX>
 struct EcSmem {
-  float B[EC_MAXR * EC_LD];
-  float W[EC_MAXR * EC_LD];
-  float4 recv[2][EC_CLUSTER][EC_MAXR / 2];  // per buffer, source rank and pair: {app, aqq, apq, 0}
-  int rotated;                              // rank 0: rotations of the last sweep (read by every CTA)
-  int go;                                   // this CTA's copy of rank 0's decision
-  unsigned tmax;                            // largest |tan| of the sweep's rotations (float bits)
+  float B[RMAX * EcCfg<RMAX>::LD];
+  float W[EcCfg<RMAX>::W_SMEM ? RMAX * EcCfg<RMAX>::LD : 1];
+  float4 recv[2][EC_CLUSTER][RMAX / 2];  // per buffer, source rank and pair: {app, aqq, apq, 0}
+  int rotated;                           // rank 0: continue after the last sweep (read by every CTA)
+  int go;                                // this CTA's copy of rank 0's decision
+  unsigned tmax;                         // largest |tan| of the sweep's rotations (float bits)
 };
 
 __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
@@ -61,8 +82,8 @@ __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
 
 // Rotation zeroing b_p . b_q: the Jacobi rotation of the 2 x 2 Gram
 // [[app, apq], [apq, aqq]]; applied when the pair is not yet orthogonal to
-// `tol` relative to its norms and apq is above the rounding of the FP32 dot
-// products (about u sqrt(rows) of |b_p| |b_q|).
+// `tol` relative to its norms (tol above the rounding of the FP32 dot
+// products, about u sqrt(rows) of |b_p| |b_q|). c = 1, s = 0 otherwise.
 __device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, float tol, float& c, float& s,
                                             float& t) {
   c = 1.f, s = 0.f, t = 0.f;
@@ -75,11 +96,14 @@ __device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, flo
   return true;
 }
 
-__global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS, 1)
+template <int RMAX>
+__global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>::THREADS, 1)
     k_eig_cluster(const float* __restrict__ R, int r, int max_sweeps, float tol, float* __restrict__ W_out,
-                  int* __restrict__ nsweeps_out, int* __restrict__ round_cnt) {
+                  int* __restrict__ nsweeps_out, int* __restrict__ round_cnt, float2* __restrict__ rot_log,
+                  int* __restrict__ rank_out) {
+  using C = EcCfg<RMAX>;
   extern __shared__ __align__(16) unsigned char ec_raw[];
-  EcSmem& S = *reinterpret_cast<EcSmem*>(ec_raw);
+  EcSmem<RMAX>& S = *reinterpret_cast<EcSmem<RMAX>*>(ec_raw);
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
@@ -87,20 +111,20 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
   const int row0 = crank * RL;
   const int h = r / 2, n1 = r - 1;
 
-  // this CTA's rows of B = R and of W = I, column-major
-  for (int e = tid; e < r * EC_RL; e += EC_THREADS) {
-    const int j = e / EC_RL, l = e % EC_RL;
+  // this CTA's rows of B = R (and of W = I), column-major
+  for (int e = tid; e < r * C::RL; e += C::THREADS) {
+    const int j = e / C::RL, l = e % C::RL;
     const int row = row0 + l;
     const bool in = l < RL && row < r;
-    S.B[j * EC_LD + l] = in ? R[(int64_t)row * r + j] : 0.f;
-    S.W[j * EC_LD + l] = (in && row == j) ? 1.f : 0.f;
+    S.B[j * C::LD + ec_pos<RMAX>(l)] = in ? R[(int64_t)row * r + j] : 0.f;
+    if (C::W_SMEM) S.W[j * C::LD + ec_pos<RMAX>(l)] = (in && row == j) ? 1.f : 0.f;
   }
   // every CTA of the cluster has started (its shared memory may be written) and loaded its rows
   cluster.sync();
 
   const int i = tid >> 2, sub = tid & 3;
   const bool owner = i < h;
-  const int l0 = sub * EC_SEG;
+  const int l0 = ec_pos<RMAX>(sub * C::SEG);
   // A sweep whose largest rotation has |tan| below t_stop leaves off-diagonal
   // products of order t_stop^2 = tol relative: the next sweep would rotate at
   // most pairs at the threshold, so it is not run
@@ -116,8 +140,8 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
         p = i == 0 ? 0 : 1 + ec_ring_add(i - 1, k, n1);
         q = 1 + ec_ring_add(n1 - 1 - i, k, n1);
 #pragma unroll
-        for (int jj = 0; jj < EC_SEG; ++jj) {
-          const float bp = S.B[p * EC_LD + l0 + jj], bq = S.B[q * EC_LD + l0 + jj];
+        for (int jj = 0; jj < C::SEG; ++jj) {
+          const float bp = S.B[p * C::LD + l0 + jj], bq = S.B[q * C::LD + l0 + jj];
           app = fmaf(bp, bp, app);
           aqq = fmaf(bq, bq, aqq);
           apq = fmaf(bp, bq, apq);
@@ -150,19 +174,22 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
         float c, s, t;
         act = ec_rotation(tpp, tqq, tpq, tol, c, s, t);
         if (act && sub == 0) atomicMax(&S.tmax, __float_as_uint(fabsf(t)));
+        if (!C::W_SMEM && crank == 0 && sub == 0) rot_log[((int64_t)sweep * n1 + k) * h + i] = make_float2(c, s);
         if (act) {
 #pragma unroll
-          for (int jj = 0; jj < EC_SEG; ++jj) {
-            float* bp = &S.B[p * EC_LD + l0 + jj];
-            float* bq = &S.B[q * EC_LD + l0 + jj];
+          for (int jj = 0; jj < C::SEG; ++jj) {
+            float* bp = &S.B[p * C::LD + l0 + jj];
+            float* bq = &S.B[q * C::LD + l0 + jj];
             const float xp = *bp, xq = *bq;
             *bp = c * xp - s * xq;
             *bq = s * xp + c * xq;
-            float* wp = &S.W[p * EC_LD + l0 + jj];
-            float* wq = &S.W[q * EC_LD + l0 + jj];
-            const float yp = *wp, yq = *wq;
-            *wp = c * yp - s * yq;
-            *wq = s * yp + c * yq;
+            if (C::W_SMEM) {
+              float* wp = &S.W[p * C::LD + l0 + jj];
+              float* wq = &S.W[q * C::LD + l0 + jj];
+              const float yp = *wp, yq = *wq;
+              *wp = c * yp - s * yq;
+              *wq = s * yp + c * yq;
+            }
           }
         }
       }
@@ -173,7 +200,7 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
       buf ^= 1;
     }
     // Every CTA counted the same rotations (identical inputs, identical arithmetic), but the
-    // loop exit is taken from rank 0's count so that all CTAs meet the same cluster barriers
+    // loop exit is taken from rank 0's decision so that all CTAs meet the same cluster barriers
     if (crank == 0 && tid == 0) S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop) ? 1 : 0;
     cluster.sync();
     if (tid == 0) S.go = *cluster.map_shared_rank(&S.rotated, 0);
@@ -184,11 +211,16 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EC_THREADS,
     }
   }
   if (crank == 0 && tid == 0) *nsweeps_out = sweep;
-  // unsorted W, this CTA's rows
-  for (int e = tid; e < RL * r; e += EC_THREADS) {
-    const int l = e / r, j = e % r;
-    const int row = row0 + l;
-    if (row < r) W_out[(int64_t)row * r + j] = S.W[j * EC_LD + l];
+  if (C::W_SMEM) {
+    // unsorted W, this CTA's rows
+    for (int e = tid; e < RL * r; e += C::THREADS) {
+      const int l = e / r, j = e % r;
+      const int row = row0 + l;
+      if (row < r) W_out[(int64_t)row * r + j] = S.W[j * C::LD + ec_pos<RMAX>(l)];
+    }
+  } else if (crank == 0) {
+    // the replay of the log writes W in index order
+    for (int j = tid; j < r; j += C::THREADS) rank_out[j] = j;
   }
   // no CTA leaves while a peer could still address its shared memory
   cluster.sync();
@@ -245,21 +277,29 @@ __global__ void __launch_bounds__(1024) k_rr_sort(const double* __restrict__ q, 
 
 }  // namespace
 
-size_t eig_cluster_smem() { return sizeof(EcSmem); }
+size_t eig_cluster_smem(int r) { return r <= 256 ? sizeof(EcSmem<256>) : sizeof(EcSmem<512>); }
 
-bool eig_cluster_supported(int r) { return r >= 8 && r <= EC_MAXR && r % 2 == 0; }
+bool eig_cluster_supported(int r) { return r >= 8 && r <= 512 && r % 2 == 0; }
+
+bool eig_cluster_logs(int r) { return r > 256; }
 
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, cudaStream_t st) {
+                       int* round_cnt, float* rot_log, int* rank_out, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EcSmem)) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_eig_cluster<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(EcSmem<256>)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_eig_cluster<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(EcSmem<512>)) != cudaSuccess)
       return -1;
     attr_set = true;
   }
-  k_eig_cluster<<<EC_CLUSTER, EC_THREADS, sizeof(EcSmem), st>>>(R, r, max_sweeps, tol, W_unsorted, nsweeps,
-                                                                  round_cnt);
+  if (r <= 256)
+    k_eig_cluster<256><<<EC_CLUSTER, EcCfg<256>::THREADS, sizeof(EcSmem<256>), st>>>(
+        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out);
+  else
+    k_eig_cluster<512><<<EC_CLUSTER, EcCfg<512>::THREADS, sizeof(EcSmem<512>), st>>>(
+        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -116,8 +116,10 @@ void launch_gram(const float* X, int64_t L, int r, double* part, double* G, doub
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
                      cudaStream_t st, float* ws = nullptr);
 size_t chol_inv_smem(int r);
-// The factor itself: R (FP32 r x r, upper, zeros below) with G = R^T R (r <= WSSR_SMEM_RANK_MAX).
-void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st);
+// The factor itself: R (FP32 r x r, upper, zeros below) with G = R^T R (workspace ws above
+// WSSR_SMEM_RANK_MAX, as launch_chol_inv).
+void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st,
+                   float* ws = nullptr);
 int64_t chol_ws_floats(int r);
 // Xo = X T (L x r times r x r), optional bf16 copies (row-major L x r, transposed r x ldT)
 // and FP64 column-sum partials of the bf16/f32 operand values written.
@@ -154,10 +156,13 @@ void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int 
 // Rayleigh-Ritz eigensolve on an 8-CTA thread-block cluster (eig_cluster.cu):
 // one-sided Jacobi on R (H = R^T R), W (r x r, row-major, unsorted columns);
 // then q_j = w_j^T H w_j (FP64), sigma (descending) = sqrt(q) and W_sorted.
+// Above r = 256 (eig_cluster_logs) W is not written: the rotations go to rot_log
+// (the one-CTA Jacobi's log format, identity ranks in rank_out) for launch_jacobi_vectors.
 bool eig_cluster_supported(int r);
-size_t eig_cluster_smem();
+bool eig_cluster_logs(int r);
+size_t eig_cluster_smem(int r);
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, cudaStream_t st);
+                       int* round_cnt, float* rot_log, int* rank_out, cudaStream_t st);
 void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
                               float* W_sorted, cudaStream_t st);
 // FP64 refinements (r64.cu). Factor: T_out = T (I - E / 2), E = T^T G T - I (P, E:

@@ -577,15 +577,20 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
     k_chol_inv<true><<<1, 1024, sm, st>>>(G, r, T, status, shift_count, ws);
 }
 
-void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st) {
+void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st, float* ws) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_chol_inv<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess)
+                             (int)chol_inv_smem(WSSR_SMEM_RANK_MAX)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_chol_inv<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_inv_smem(WSSR_RANK_MAX)) != cudaSuccess)
       return;
     attr_set = true;
   }
-  k_chol_inv<false, true><<<1, 1024, chol_inv_smem(r), st>>>(G, r, R, status, shift_count, nullptr);
+  if (r <= WSSR_SMEM_RANK_MAX)
+    k_chol_inv<false, true><<<1, 1024, chol_inv_smem(r), st>>>(G, r, R, status, shift_count, nullptr);
+  else
+    k_chol_inv<true, true><<<1, 1024, chol_inv_smem(r), st>>>(G, r, R, status, shift_count, ws);
 }
 
 // ---------------------------------------------------------------------------

@@ -492,11 +492,18 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     // Ritz values from FP64 Rayleigh quotients of H, columns sorted by them
     const int ms = h->opt.jacobi_sweeps;
     int* cnt = reinterpret_cast<int*>(h->rot_log + (size_t)ms * (r - 1) * (r / 2) * 2);
-    launch_chol_R(h->G, r, h->T, h->status, h->status + 1, st);
+    launch_chol_R(h->G, r, h->T, h->status, h->status + 1, st, h->chol_ws);
     // rotation threshold: above the rounding of the FP32 dot products (about u sqrt(r) relative)
     const float tol = 4.f * 5.96e-8f * sqrtf((float)r);
-    if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, st) != 0) return WSSR_ERR_CUDA;
+    if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, h->rot_log, cnt + (size_t)ms * (r - 1), st) !=
+        0)
+      return WSSR_ERR_CUDA;
     h->launches += 2;
+    if (eig_cluster_logs(r)) {
+      // above r = 256 the cluster logs its rotations: W replayed from the log
+      launch_jacobi_vectors(h->rot_log, h->nsweeps, r, ms, h->Wu, st);
+      h->launches++;
+    }
     if (!refine) {
       launch_rr_quotients_sort(h->G, h->Wu, r, h->rq, sig, h->W, st);
       h->launches += 2;
