@@ -736,9 +736,40 @@ def run_mlp(args, w):
                        "lambda": w.lam, "m": w.m, "o_bytes": w.N * ld * (2 if args.dtype == "bf16" else 4)},
             "jacobian_ms_per_step": jac,
             "jacobian_write_GBps": w.N * w.M * (2 if args.dtype == "bf16" else 4) / jac / 1e6}
+    if args.accuracy_cols > 0:
+        line["accuracy"] = mlp_accuracy(w, args, s, ans, theta, xs[0], V, g, O, ld)
     print(json.dumps(line), flush=True)
     s.close()
     ans.close()
+
+
+def mlp_accuracy(w, args, s, ans, theta, x, V_prev, g, O, ld):
+    """One more GPU step (Jacobian kernel + step, the timed configuration) on the
+    samples x from the chain's last basis, against the FP64 oracle step on the
+    oracle's own per-sample Jacobian of the same network at the same samples
+    (the difference includes the FP32 rounding of the Jacobian, about 2e-5)."""
+    import numpy as np
+    import torch
+
+    from oracle import mlp_oracle as mo
+    from oracle import wssr_oracle as orc
+    ans.per_sample_jacobian(theta, x, out=O, dtype=args.dtype, ld=ld)
+    d, sg, V = s.step(O, g, V_prev)
+    s.check("accuracy step")
+    J = mo.per_sample_jacobian(theta.double().cpu().numpy(), w.widths, x.double().cpu().numpy())
+    g64, Vp64 = g.double().cpu().numpy(), V_prev.double().cpu().numpy()
+    t0 = time.perf_counter()
+    dr, sr, Vr = orc.wssr_step(J, g64, Vp64, w.lam, w.m)
+    t_or = time.perf_counter() - t0
+    d, sg, V = d.double().cpu().numpy(), sg.cpu().numpy(), V.double().cpu().numpy()
+    lr, lrr = d - g64 / w.lam, dr - g64 / w.lam
+    return {"delta_rel": float(np.linalg.norm(d - dr) / np.linalg.norm(dr)),
+            "delta_lr_rel": float(np.linalg.norm(lr - lrr) / np.linalg.norm(lrr)),
+            "sigma_max_rel": float(np.max(np.abs(sg - sr) / sr)),
+            "projector": float(orc.projector_distance(V, Vr)),
+            "oracle_step_s_measured": t_or,
+            "sample": f"full size (N={w.N}, M={w.M}, r={w.r}); oracle on its FP64 per-sample Jacobian of the same "
+                      f"network and samples; the GPU's basis fed to both sides"}
 
 
 def mlp_cpu_sample(w, cols: int):
