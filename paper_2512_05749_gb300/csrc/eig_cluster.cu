@@ -12,9 +12,12 @@
 // of B (and of W) split over the CTAs every update is local to its CTA. The
 // only exchange is, per round, the three partial dot products of every pair
 // (||b_p||^2, ||b_q||^2, b_p . b_q over the CTA's rows), which each CTA
-// stores into every peer's shared memory; after one cluster barrier every CTA
-// sums the partials in rank order, so all CTAs take bit-identical rotation
-// decisions without further communication.
+// stores into every peer's shared memory with st.async, completing bytes on
+// the receiver's mbarrier of that round's buffer (two buffers alternate). A
+// CTA waits for its own barrier only (bounded), then sums the partials in
+// rank order, so all CTAs take bit-identical rotation decisions without a
+// cluster-wide barrier per round; cluster barriers remain at the start, at
+// the end of every sweep (the loop exit is rank 0's decision) and at exit.
 //
 // Layout: CTA c of the cluster holds rows [c RL, c RL + RL) of B (and of W),
 // with RL = ceil(r / 8), column-major in shared memory (see EcCfg for the
@@ -68,12 +71,61 @@ __device__ __forceinline__ int ec_pos(int l) {
 template <int RMAX>
 struct EcSmem {
   float B[RMAX * EcCfg<RMAX>::LD];
-  float W[EcCfg<RMAX>::W_SMEM ? RMAX * EcCfg<RMAX>::LD : 1];
+  float W[EcCfg<RMAX>::W_SMEM ? RMAX * EcCfg<RMAX>::LD : 4];
   float4 recv[2][EC_CLUSTER][RMAX / 2];  // per buffer, source rank and pair: {app, aqq, apq, 0}
+  uint64_t bar[2];                       // per buffer: completes when all ranks' partials have landed
   int rotated;                           // rank 0: continue after the last sweep (read by every CTA)
   int go;                                // this CTA's copy of rank 0's decision
   unsigned tmax;                         // largest |tan| of the sweep's rotations (float bits)
+  int abort;                             // a bounded wait ran out in this CTA
 };
+
+// Distributed shared memory: the partials of a round go to every rank with
+// st.async, each store completing its bytes on the receiver's mbarrier of
+// that buffer, so a round needs no cluster-wide barrier.
+__device__ __forceinline__ uint32_t ec_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t ec_mapa(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void ec_st_async(uint32_t raddr, float4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   raddr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void ec_bar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ec_saddr(b)) : "memory");
+}
+__device__ __forceinline__ void ec_bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ec_saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool ec_bar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(ec_saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t ec_gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false when the deadline passes or the CTA already aborted.
+__device__ __noinline__ bool ec_bar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns, volatile int* abort) {
+  if (ec_bar_test(b, parity)) return true;
+  const uint64_t t0 = ec_gtimer();
+  for (;;) {
+    if (ec_bar_test(b, parity)) return true;
+    if (*abort) return false;
+    if (ec_gtimer() - t0 > limit_ns) return false;
+  }
+}
 
 __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
   const int s = a + b;
@@ -100,7 +152,7 @@ template <int RMAX>
 __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>::THREADS, 1)
     k_eig_cluster(const float* __restrict__ R, int r, int max_sweeps, float tol, float* __restrict__ W_out,
                   int* __restrict__ nsweeps_out, int* __restrict__ round_cnt, float2* __restrict__ rot_log,
-                  int* __restrict__ rank_out) {
+                  int* __restrict__ rank_out, uint64_t limit_ns, int* status) {
   using C = EcCfg<RMAX>;
   extern __shared__ __align__(16) unsigned char ec_raw[];
   EcSmem<RMAX>& S = *reinterpret_cast<EcSmem<RMAX>*>(ec_raw);
@@ -119,7 +171,14 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
     S.B[j * C::LD + ec_pos<RMAX>(l)] = in ? R[(int64_t)row * r + j] : 0.f;
     if (C::W_SMEM) S.W[j * C::LD + ec_pos<RMAX>(l)] = (in && row == j) ? 1.f : 0.f;
   }
-  // every CTA of the cluster has started (its shared memory may be written) and loaded its rows
+  if (tid == 0) {
+    ec_bar_init(&S.bar[0]);
+    ec_bar_init(&S.bar[1]);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // every CTA of the cluster has started (its shared memory and barriers may be addressed) and
+  // loaded its rows
   cluster.sync();
 
   const int i = tid >> 2, sub = tid & 3;
@@ -129,11 +188,17 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
   // products of order t_stop^2 = tol relative: the next sweep would rotate at
   // most pairs at the threshold, so it is not run
   const float t_stop = sqrtf(tol);
-  int buf = 0, sweep = 0;
+  const uint32_t round_bytes = (uint32_t)EC_CLUSTER * (uint32_t)h * 16u;
+  int sweep = 0;
+  uint32_t gr = 0;  // rounds so far: buffer gr & 1, its barrier's phase (gr >> 1) & 1
   for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
     if (tid == 0) S.tmax = 0u;
-    for (int k = 0; k < n1; ++k) {
+    for (int k = 0; k < n1; ++k, ++gr) {
+      const int buf = (int)(gr & 1u);
+      // this round's partials from all ranks land on bar[buf] (the arrival may follow them)
+      // (after an abort nothing is sent or expected any more)
+      if (tid == 0 && !S.abort) ec_bar_expect(&S.bar[buf], round_bytes);
       int p = 0, q = 0;
       float app = 0.f, aqq = 0.f, apq = 0.f;
       if (owner) {
@@ -154,17 +219,21 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
         aqq += __shfl_xor_sync(0xffffffffu, aqq, o);
         apq += __shfl_xor_sync(0xffffffffu, apq, o);
       }
-      if (owner) {
+      if (owner && !S.abort) {
         const float4 v = make_float4(app, aqq, apq, 0.f);
+        const uint32_t la = ec_saddr(&S.recv[buf][crank][i]), lb = ec_saddr(&S.bar[buf]);
 #pragma unroll
         for (int d = 0; d < EC_CLUSTER / 4; ++d) {
-          float4* dst = cluster.map_shared_rank(&S.recv[buf][crank][i], sub * (EC_CLUSTER / 4) + d);
-          *dst = v;
+          const int dst = sub * (EC_CLUSTER / 4) + d;
+          ec_st_async(ec_mapa(la, dst), v, ec_mapa(lb, dst));
         }
       }
-      cluster.sync();
+      if (!ec_bar_wait(&S.bar[buf], (gr >> 1) & 1u, limit_ns, &S.abort)) {
+        if (!S.abort) set_status(status, WSSR_ERR_DEVICE_TIMEOUT);
+        S.abort = 1;  // rotations stop; the rounds still run, so every CTA meets the same barriers
+      }
       bool act = false;
-      if (owner) {
+      if (owner && !S.abort) {
         float tpp = 0.f, tqq = 0.f, tpq = 0.f;
 #pragma unroll
         for (int d = 0; d < EC_CLUSTER; ++d) {
@@ -197,11 +266,10 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
       const int cnt = __syncthreads_count(act && sub == 0);
       if (crank == 0 && tid == 0 && round_cnt) round_cnt[sweep * n1 + k] = cnt;
       rotated += cnt;
-      buf ^= 1;
     }
     // Every CTA counted the same rotations (identical inputs, identical arithmetic), but the
     // loop exit is taken from rank 0's decision so that all CTAs meet the same cluster barriers
-    if (crank == 0 && tid == 0) S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop) ? 1 : 0;
+    if (crank == 0 && tid == 0) S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop && !S.abort) ? 1 : 0;
     cluster.sync();
     if (tid == 0) S.go = *cluster.map_shared_rank(&S.rotated, 0);
     __syncthreads();
@@ -284,7 +352,7 @@ bool eig_cluster_supported(int r) { return r >= 8 && r <= 512 && r % 2 == 0; }
 bool eig_cluster_logs(int r) { return r > 256; }
 
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, float* rot_log, int* rank_out, cudaStream_t st) {
+                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_eig_cluster<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -294,12 +362,15 @@ int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* 
       return -1;
     attr_set = true;
   }
+  const uint64_t lim = (uint64_t)wait_us * 1000ull;
   if (r <= 256)
     k_eig_cluster<256><<<EC_CLUSTER, EcCfg<256>::THREADS, sizeof(EcSmem<256>), st>>>(
-        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out);
+        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out, lim,
+        status);
   else
     k_eig_cluster<512><<<EC_CLUSTER, EcCfg<512>::THREADS, sizeof(EcSmem<512>), st>>>(
-        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out);
+        R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out, lim,
+        status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -162,7 +162,7 @@ bool eig_cluster_supported(int r);
 bool eig_cluster_logs(int r);
 size_t eig_cluster_smem(int r);
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, float* rot_log, int* rank_out, cudaStream_t st);
+                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st);
 void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
                               float* W_sorted, cudaStream_t st);
 // FP64 refinements (r64.cu). Factor: T_out = T (I - E / 2), E = T^T G T - I (P, E:

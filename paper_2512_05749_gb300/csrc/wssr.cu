@@ -495,8 +495,8 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     launch_chol_R(h->G, r, h->T, h->status, h->status + 1, st, h->chol_ws);
     // rotation threshold: above the rounding of the FP32 dot products (about u sqrt(r) relative)
     const float tol = 4.f * 5.96e-8f * sqrtf((float)r);
-    if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, h->rot_log, cnt + (size_t)ms * (r - 1), st) !=
-        0)
+    if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, h->rot_log, cnt + (size_t)ms * (r - 1),
+                           h->opt.wait_cap, h->status, st) != 0)
       return WSSR_ERR_CUDA;
     h->launches += 2;
     if (eig_cluster_logs(r)) {
