@@ -76,7 +76,7 @@ struct EcSmem {
   uint64_t bar[2];                       // per buffer: completes when all ranks' partials have landed
   int rotated;                           // rank 0: continue after the last sweep (read by every CTA)
   int go;                                // this CTA's copy of rank 0's decision
-  unsigned offmax;                       // largest |b_p . b_q| / (|b_p| |b_q|) of the sweep (float bits)
+  unsigned tmax;                         // largest |tan| of the sweep's rotations (float bits)
   int abort;                             // a bounded wait ran out in this CTA
 };
 
@@ -137,12 +137,10 @@ __device__ __forceinline__ int ec_ring_add(int a, int b, int n1) {
 // `tol` relative to its norms (tol above the rounding of the FP32 dot
 // products, about u sqrt(rows) of |b_p| |b_q|). c = 1, s = 0 otherwise.
 __device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, float tol, float& c, float& s,
-                                            float& rel) {
-  c = 1.f, s = 0.f, rel = 0.f;
+                                            float& t) {
+  c = 1.f, s = 0.f, t = 0.f;
   const float nrm = sqrtf(app * aqq);
-  if (nrm > 0.f) rel = fabsf(apq) / nrm;
   if (!(fabsf(apq) > tol * nrm)) return false;
-  float t;
   const float tau = (aqq - app) / (2.f * apq);
   t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
   c = __frsqrt_rn(1.f + t * t);
@@ -186,17 +184,19 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
   const int i = tid >> 2, sub = tid & 3;
   const bool owner = i < h;
   const int l0 = ec_pos<RMAX>(sub * C::SEG);
-  // Quadratic convergence: a sweep in which every pair's relative off-diagonal
-  // b_p . b_q / (|b_p| |b_q|) was below off_stop leaves off-diagonals of order
-  // off_stop^2 = tol / 4 after its rotations, below the threshold: the next
-  // sweep would rotate nothing, so it is not run
-  const float off_stop = 0.5f * sqrtf(tol);
+  // A sweep whose rotations all had |tan| below t_stop (small angles: the
+  // pairs are resolved, not near-degenerate) leaves off-diagonals of order
+  // t_stop^2 = tol relative: the next sweep would rotate at most pairs at the
+  // threshold, so it is not run. (A small relative off-diagonal alone is not
+  // enough: a near-degenerate pair takes a large rotation however small its
+  // coupling, and mixes its neighbours' couplings at that size.)
+  const float t_stop = sqrtf(tol);
   const uint32_t round_bytes = (uint32_t)EC_CLUSTER * (uint32_t)h * 16u;
   int sweep = 0;
   uint32_t gr = 0;  // rounds so far: buffer gr & 1, its barrier's phase (gr >> 1) & 1
   for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
-    if (tid == 0) S.offmax = 0u;
+    if (tid == 0) S.tmax = 0u;
     for (int k = 0; k < n1; ++k, ++gr) {
       const int buf = (int)(gr & 1u);
       // this round's partials from all ranks land on bar[buf] (the arrival may follow them)
@@ -243,9 +243,9 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
           const float4 v = S.recv[buf][d][i];
           tpp += v.x, tqq += v.y, tpq += v.z;
         }
-        float c, s, rel;
-        act = ec_rotation(tpp, tqq, tpq, tol, c, s, rel);
-        if (act && sub == 0) atomicMax(&S.offmax, __float_as_uint(rel));
+        float c, s, t;
+        act = ec_rotation(tpp, tqq, tpq, tol, c, s, t);
+        if (act && sub == 0) atomicMax(&S.tmax, __float_as_uint(fabsf(t)));
         if (!C::W_SMEM && crank == 0 && sub == 0) rot_log[((int64_t)sweep * n1 + k) * h + i] = make_float2(c, s);
         if (act) {
 #pragma unroll
@@ -273,12 +273,12 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
     // Every CTA counted the same rotations (identical inputs, identical arithmetic), but the
     // loop exit is taken from rank 0's decision so that all CTAs meet the same cluster barriers
     if (crank == 0 && tid == 0)
-      S.rotated = (rotated > 0 && __uint_as_float(S.offmax) >= off_stop && !S.abort) ? 1 : 0;
+      S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop && !S.abort) ? 1 : 0;
     cluster.sync();
     if (tid == 0) S.go = *cluster.map_shared_rank(&S.rotated, 0);
     __syncthreads();
     if (!S.go) {
-      ++sweep;  // the last sweep: no rotation, or every pair below off_stop
+      ++sweep;  // the last sweep: no rotation, or none above t_stop
       break;
     }
   }
