@@ -325,26 +325,29 @@ __global__ void __launch_bounds__(256) k_rr_quotients(const double* __restrict__
 }
 
 // Descending order of the quotients (ties by index): sigma[rank] = sqrt(q),
-// column j of W moves to column rank(j) of Ws.
-__global__ void __launch_bounds__(1024) k_rr_sort(const double* __restrict__ q, const float* __restrict__ W, int r,
-                                                  double* __restrict__ sigma, float* __restrict__ Ws) {
+// column j of W moves to column rank(j) of Ws. Every CTA ranks all r values
+// (in shared memory) and moves rows [16 blockIdx.x, 16 blockIdx.x + 16).
+__global__ void __launch_bounds__(256) k_rr_sort(const double* __restrict__ q, const float* __restrict__ W, int r,
+                                                 double* __restrict__ sigma, float* __restrict__ Ws) {
+  __shared__ double q_s[1024];
   __shared__ int rank_of[1024];
   const int tid = threadIdx.x;
-  for (int j = tid; j < r; j += 1024) {
-    const double qj = q[j];
+  for (int j = tid; j < r; j += 256) q_s[j] = q[j];
+  __syncthreads();
+  for (int j = tid; j < r; j += 256) {
+    const double qj = q_s[j];
     int rk = 0;
     for (int b = 0; b < r; ++b) {
-      const double qb = q[b];
+      const double qb = q_s[b];
       rk += (qb > qj) || (qb == qj && b < j);
     }
     rank_of[j] = rk;
-    sigma[rk] = qj > 0.0 ? sqrt(qj) : 0.0;
+    if (blockIdx.x == 0) sigma[rk] = qj > 0.0 ? sqrt(qj) : 0.0;
   }
   __syncthreads();
-  for (int e = tid; e < r * r; e += 1024) {
-    const int a = e / r, j = e % r;
-    Ws[(int64_t)a * r + rank_of[j]] = W[e];
-  }
+  const int a1 = min(r, 16 * (int)blockIdx.x + 16);
+  for (int a = 16 * blockIdx.x; a < a1; ++a)
+    for (int j = tid; j < r; j += 256) Ws[(int64_t)a * r + rank_of[j]] = W[(int64_t)a * r + j];
 }
 
 }  // namespace
@@ -381,7 +384,7 @@ int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* 
 void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
                               float* W_sorted, cudaStream_t st) {
   k_rr_quotients<<<r, 256, 0, st>>>(H, W_unsorted, r, q);
-  k_rr_sort<<<1, 1024, 0, st>>>(q, W_unsorted, r, sigma, W_sorted);
+  k_rr_sort<<<(unsigned)ceil_div(r, 16), 256, 0, st>>>(q, W_unsorted, r, sigma, W_sorted);
 }
 
 }  // namespace wssr

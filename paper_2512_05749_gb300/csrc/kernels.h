@@ -175,6 +175,14 @@ void launch_refine_factor(const double* G, const float* T, int r, double* P, dou
 void launch_dgemm_rr(const double* A, const float* B, int r, float* C, cudaStream_t st);
 void launch_refine_eigenvectors(const double* H, const float* X, int r, double* P, double* S, double* G, double* E,
                                 double* Xn, double* lam, double* sigma, float* W_sorted, cudaStream_t st);
+// The apply from the K-blocked bf16 basis Xh and the r x r TW with V = Xh TW:
+// cX = Xh^T g (FP64, partials as launch_dot, dot_blk_part_elems of them),
+// y = A^T x / A x for an r x r FP32 A, delta = g / lam_eff + Xh f.
+int64_t dot_blk_part_elems(int64_t M, int r);
+void launch_dot_blk(const void* Xblk, const float* g, int64_t M, int r, double* part, double* cX, cudaStream_t st);
+void launch_matvec_r(const float* A, const double* x, int r, int trans, double* y, cudaStream_t st);
+void launch_woodbury_blk(const void* Xblk, const float* g, const double* f, int64_t M, int r, double lam_eff,
+                         float* delta, cudaStream_t st);
 // c = V^T g (FP64), M x r V. The partial sums use at most DOT_MAX_BLOCKS row
 // blocks (8 CTAs per SM on 152 SMs), so dot_part_elems(M, r) <= DOT_MAX_BLOCKS * r.
 constexpr int DOT_MAX_BLOCKS = 1216;

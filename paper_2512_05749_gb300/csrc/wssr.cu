@@ -565,11 +565,21 @@ wssr_status ssi_rr(wssr_ctx* h, const wssr_operator* op, const float* V_start, i
   return rr_finish(h, op, Xop, V_out, sigma, hist, st);
 }
 
+// Eq. (updated_sr_1) apply. With Xblk (the tensor-core engine after its Rayleigh-Ritz
+// step, V = Xblk TW with TW in h->TW) it reads the bf16 K-blocked basis instead of
+// V (half the bytes): c = TW^T (Xblk^T g), delta = g / lam_eff + Xblk (TW e).
 wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const float* g, float* delta,
-                     cudaStream_t st) {
+                     cudaStream_t st, const void* Xblk = nullptr) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_APPLY, st);
-  if (!h->c_ready) launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
+  if (Xblk) {
+    launch_dot_blk(Xblk, g, h->M, r, h->dot_part, h->rq, st);
+    launch_matvec_r(h->TW, h->rq, r, 1, h->c, st);
+    h->launches += 3;
+  } else {
+    if (!h->c_ready) launch_dot(V, g, h->M, r, h->dot_part, h->c, st);
+    h->launches += 2;
+  }
   h->c_ready = false;
   // complement weight 1/lam_eff: 1/lambda (damped), 1/sigma_floor (cutoff), none (pseudo-inverse)
   const double lam_eff = h->opt.apply_mode == WSSR_APPLY_CUTOFF ? h->opt.sigma_floor
@@ -577,8 +587,14 @@ wssr_status woodbury(wssr_ctx* h, const float* V, const double* sigma, const flo
                                                                 : h->lam;
   launch_woodbury_coeffs(sigma, h->c, r, h->lam, h->opt.apply_mode, h->opt.sigma_floor, h->e,
                          h->status, st, h->opt.r_reg);
-  launch_woodbury(V, g, h->e, h->M, r, lam_eff, delta, st);
-  h->launches += 4;
+  if (Xblk) {
+    launch_matvec_r(h->TW, h->e, r, 0, h->rq, st);  // f = TW e
+    launch_woodbury_blk(Xblk, g, h->rq, h->M, r, lam_eff, delta, st);
+    h->launches += 3;
+  } else {
+    launch_woodbury(V, g, h->e, h->M, r, lam_eff, delta, st);
+    h->launches += 2;
+  }
   return check_launch(h);
 }
 
@@ -792,7 +808,7 @@ wssr_status wssr_step(wssr_handle h, const wssr_operator* op, const float* g, co
   h->mu_valid = false;
   if ((s = prepare_op(h, op, st)) != WSSR_OK) return s;
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g, st)) != WSSR_OK) return s;
-  return woodbury(h, V_out, sigma, g, delta, st);
+  return woodbury(h, V_out, sigma, g, delta, st, h->use_tc ? h->Xhat : nullptr);
 }
 
 wssr_status wssr_step_host(wssr_handle h, const void* O_host, int64_t ld, const float* g_host,
@@ -890,7 +906,7 @@ wssr_status wssr_step_averaged(wssr_handle h, const wssr_operator* op, const flo
   }
   Hist hist{weight, sqrt(weight * (double)h->N / (1.0 - weight)), (1.0 - weight) / (double)h->N, sigma_prev};
   if ((s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, h->gbar, st, &hist)) != WSSR_OK) return s;
-  if ((s = woodbury(h, V_out, sigma, h->gbar, delta, st)) != WSSR_OK) return s;
+  if ((s = woodbury(h, V_out, sigma, h->gbar, delta, st, h->Xhat)) != WSSR_OK) return s;
   // Lbar = diag(1/sigma) V_out^T gbar (Eq. (Lbar)); h->c holds V_out^T gbar
   launch_lbar(h->c, sigma, r, Lbar_out, st);
   h->launches++;
@@ -932,7 +948,7 @@ wssr_status wssr_step_local_energy(wssr_handle h, const wssr_operator* op, const
   s = ssi_rr(h, op, V_prev, h->opt.m, V_out, sigma, g_out, st);
   h->fuse_w = nullptr, h->fuse_g = nullptr;
   if (s != WSSR_OK) return s;
-  return woodbury(h, V_out, sigma, g_out, delta, st);
+  return woodbury(h, V_out, sigma, g_out, delta, st, h->use_tc ? h->Xhat : nullptr);
 }
 
 wssr_status wssr_init_subspace(wssr_handle h, const wssr_operator* op, const float* V_rand,
