@@ -1413,39 +1413,43 @@ __global__ void __launch_bounds__(256) k_woodbury(const float* __restrict__ V, c
 
 // The apply from the bf16 K-blocked basis Xh instead of V = Xh TW (half the
 // bytes): part[b][j] = sum over the CTA's 64-parameter blocks of Xh[:, j] . g
-// (FP64 per CTA); thread j reads row j of each block (64 contiguous bf16).
+// (FP64 per CTA); thread j reads row j of each block (64 contiguous bf16). The
+// CTA's slice of g (at most DOT_BLK_MAX_BLOCKS blocks) is staged once.
+constexpr int DOT_BLK_MAX_BLOCKS = 32;
 __global__ void __launch_bounds__(256) k_dot_blk(const bf16* __restrict__ Xb, const float* __restrict__ g, int64_t M,
                                                  int r, int64_t blk_per_cta, double* __restrict__ part) {
-  __shared__ float gs[64];
+  __shared__ __align__(16) float gs[DOT_BLK_MAX_BLOCKS * 64];
   const int64_t nblk = ceil_div(M, 64);
   const int64_t b0 = (int64_t)blockIdx.x * blk_per_cta;
   const int64_t b1 = b0 + blk_per_cta < nblk ? b0 + blk_per_cta : nblk;
+  const int nb = (int)(b1 - b0);
+  for (int e = threadIdx.x; e < nb * 64; e += 256) {
+    const int64_t m = b0 * 64 + e;
+    gs[e] = m < M ? g[m] : 0.f;
+  }
+  __syncthreads();
   double acc[2] = {0.0, 0.0};
-  for (int64_t b = b0; b < b1; ++b) {
-    __syncthreads();
-    if (threadIdx.x < 64) {
-      const int64_t m = b * 64 + threadIdx.x;
-      gs[threadIdx.x] = m < M ? g[m] : 0.f;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = threadIdx.x + 256 * h;
-      if (j >= r) break;
-      const uint4* row = reinterpret_cast<const uint4*>(Xb + (b * r + j) * 64);
-      float a = 0.f;
+  for (int h = 0; h < 2; ++h) {
+    const int j = threadIdx.x + 256 * h;
+    if (j >= r) break;
+    float a = 0.f, a2 = 0.f;
+    for (int bi = 0; bi < nb; ++bi) {
+      const uint4* row = reinterpret_cast<const uint4*>(Xb + ((b0 + bi) * r + j) * 64);
+      const float* gb = gs + bi * 64;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint4 v = __ldcs(row + q);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          a = fmaf(__uint_as_float(w[e] << 16), gs[q * 8 + 2 * e], a);
-          a = fmaf(__uint_as_float(w[e] & 0xFFFF0000u), gs[q * 8 + 2 * e + 1], a);
+          a = fmaf(__uint_as_float(w[e] << 16), gb[q * 8 + 2 * e], a);
+          a2 = fmaf(__uint_as_float(w[e] & 0xFFFF0000u), gb[q * 8 + 2 * e + 1], a2);
         }
       }
-      acc[h] += (double)a;
+      if ((bi & 7) == 7) acc[h] += (double)(a + a2), a = 0.f, a2 = 0.f;
     }
+    acc[h] += (double)(a + a2);
   }
   for (int h = 0; h < 2; ++h) {
     const int j = threadIdx.x + 256 * h;
@@ -1453,35 +1457,48 @@ __global__ void __launch_bounds__(256) k_dot_blk(const bf16* __restrict__ Xb, co
   }
 }
 
-// y = A^T x (trans) or A x, A r x r FP32 row-major, x and y FP64 (one thread per output).
-__global__ void k_matvec_r(const float* __restrict__ A, const double* __restrict__ x, int r, int trans,
-                           double* __restrict__ y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// y = A^T x (trans) or A x, A r x r FP32 row-major, x and y FP64: one warp per
+// output, lanes over k, FP64 products and a warp reduction.
+__global__ void __launch_bounds__(256) k_matvec_r(const float* __restrict__ A, const double* __restrict__ x, int r,
+                                                  int trans, double* __restrict__ y) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= r) return;
   double s = 0.0;
-  for (int k = 0; k < r; ++k) s = fma((double)(trans ? A[(int64_t)k * r + i] : A[(int64_t)i * r + k]), x[k], s);
-  y[i] = s;
+  for (int k = lane; k < r; k += 32)
+    s = fma((double)(trans ? A[(int64_t)k * r + i] : A[(int64_t)i * r + k]), x[k], s);
+  s = warp_sum(s);
+  if (lane == 0) y[i] = s;
 }
 
-// delta[m] = g[m] inv_lam + sum_j Xh[m, j] f[j] (Xh bf16 K-blocked); a warp covers 32
-// consecutive parameters of one 64-parameter block (64 contiguous bytes per column j).
+// delta[m] = g[m] inv_lam + sum_j Xh[m, j] f[j] (Xh bf16 K-blocked); a thread
+// covers two consecutive parameters (one bf16x2 load per column j), a warp 64
+// = one block (128 contiguous bytes per column).
 __global__ void __launch_bounds__(256) k_woodbury_blk(const bf16* __restrict__ Xb, const float* __restrict__ g,
                                                       const double* __restrict__ f, int64_t M, int r, float inv_lam,
                                                       float* __restrict__ delta) {
   __shared__ float fs[512];
   for (int i = threadIdx.x; i < r; i += blockDim.x) fs[i] = (float)f[i];
   __syncthreads();
-  const int64_t m = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t m = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 2;
   if (m >= M) return;
-  const bf16* col = Xb + (m >> 6) * (int64_t)r * 64 + (m & 63);
-  float s0 = 0.f, s1 = 0.f;
+  const __nv_bfloat162* col = reinterpret_cast<const __nv_bfloat162*>(Xb + (m >> 6) * (int64_t)r * 64 + (m & 63));
+  float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
   int j = 0;
   for (; j + 1 < r; j += 2) {
-    s0 = fmaf(__bfloat162float(col[(int64_t)j * 64]), fs[j], s0);
-    s1 = fmaf(__bfloat162float(col[(int64_t)(j + 1) * 64]), fs[j + 1], s1);
+    const float2 v0 = __bfloat1622float2(col[(int64_t)j * 32]);
+    const float2 v1 = __bfloat1622float2(col[(int64_t)(j + 1) * 32]);
+    s0 = fmaf(v0.x, fs[j], s0);
+    s1 = fmaf(v0.y, fs[j], s1);
+    t0 = fmaf(v1.x, fs[j + 1], t0);
+    t1 = fmaf(v1.y, fs[j + 1], t1);
   }
-  if (j < r) s0 = fmaf(__bfloat162float(col[(int64_t)j * 64]), fs[j], s0);
-  delta[m] = fmaf(g[m], inv_lam, s0 + s1);
+  if (j < r) {
+    const float2 v0 = __bfloat1622float2(col[(int64_t)j * 32]);
+    s0 = fmaf(v0.x, fs[j], s0);
+    s1 = fmaf(v0.y, fs[j], s1);
+  }
+  delta[m] = fmaf(g[m], inv_lam, s0 + t0);
+  if (m + 1 < M) delta[m + 1] = fmaf(g[m + 1], inv_lam, s1 + t1);
 }
 
 __global__ void k_check_finite(const float* __restrict__ x, int64_t n, int* status) {
@@ -1504,24 +1521,30 @@ void launch_dot(const float* V, const float* g, int64_t M, int r, double* part, 
   k_colsum_finalize<<<(unsigned)ceil_div(r, 32), 1024, 0, st>>>(part, nbe, r, 1.0, c);
 }
 
-int64_t dot_blk_part_elems(int64_t M, int r) { return (int64_t)dot_nb(M) * r; }
+int64_t dot_blk_part_elems(int64_t M, int r) {
+  const int64_t nblk = ceil_div(M, 64);
+  int64_t per = ceil_div(nblk, dot_nb(M));
+  if (per > DOT_BLK_MAX_BLOCKS) per = DOT_BLK_MAX_BLOCKS;
+  return ceil_div(nblk, per) * r;
+}
 
 void launch_dot_blk(const void* Xblk, const float* g, int64_t M, int r, double* part, double* cX, cudaStream_t st) {
   const int64_t nblk = ceil_div(M, 64);
   const int nb = dot_nb(M);
-  const int64_t per = ceil_div(nblk, nb);
+  int64_t per = ceil_div(nblk, nb);
+  if (per > DOT_BLK_MAX_BLOCKS) per = DOT_BLK_MAX_BLOCKS;  // (then more CTAs than dot_nb: see dot_blk_part_elems)
   const int nbe = (int)ceil_div(nblk, per);
   k_dot_blk<<<nbe, 256, 0, st>>>((const bf16*)Xblk, g, M, r, per, part);
   k_colsum_finalize<<<(unsigned)ceil_div(r, 32), 1024, 0, st>>>(part, nbe, r, 1.0, cX);
 }
 
 void launch_matvec_r(const float* A, const double* x, int r, int trans, double* y, cudaStream_t st) {
-  k_matvec_r<<<(unsigned)ceil_div(r, 128), 128, 0, st>>>(A, x, r, trans, y);
+  k_matvec_r<<<(unsigned)ceil_div(r, 8), 256, 0, st>>>(A, x, r, trans, y);
 }
 
 void launch_woodbury_blk(const void* Xblk, const float* g, const double* f, int64_t M, int r, double lam_eff,
                          float* delta, cudaStream_t st) {
-  k_woodbury_blk<<<(unsigned)ceil_div(M, 256), 256, 0, st>>>((const bf16*)Xblk, g, f, M, r,
+  k_woodbury_blk<<<(unsigned)ceil_div(M, 512), 256, 0, st>>>((const bf16*)Xblk, g, f, M, r,
                                                                (float)(1.0 / lam_eff), delta);
 }
 

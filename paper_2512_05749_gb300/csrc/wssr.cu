@@ -764,7 +764,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(Hp, (size_t)r * r * d);
   ALLOC(c, (size_t)r * d);
   ALLOC(e, (size_t)r * d);
-  ALLOC(dot_part, (size_t)dot_part_elems(M, r) * d);
+  ALLOC(dot_part, (size_t)std::max(dot_part_elems(M, r), dot_blk_part_elems(M, r)) * d);
   if (chol_ws_floats(r) > 0) ALLOC(chol_ws, (size_t)chol_ws_floats(r) * f);
   if (jacobi_ws_floats(r) > 0) ALLOC(jac_ws, (size_t)jacobi_ws_floats(r) * f);
   ALLOC(TX, (size_t)r * r * f);
