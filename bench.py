@@ -669,6 +669,7 @@ def run_ours(args, w):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
         "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
+        "jacobi_patch": {"steps": stats["patch_steps"], "rotations": stats["patch_rotations"]},
         "bf16_vs_fp32": compare,
         "accuracy": accuracy,
         "cpu_baseline": cpu,
@@ -990,6 +991,7 @@ def run_mlp_mf(args, w):
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "jacobi_sweeps_last_step": stats["jacobi_sweeps"],
             "jacobi_rotations_per_sweep": stats["rotations_per_sweep"],
+            "jacobi_patch": {"steps": stats["patch_steps"], "rotations": stats["patch_rotations"]},
             "vs_materialised_fp32": compare, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 

@@ -423,7 +423,11 @@ wssr_status wssr_extend_basis(const float* V_prev, int64_t M, int32_t r_prev, co
  * handle's last stream). out[0] = Jacobi sweeps of its Rayleigh-Ritz
  * eigensolve, out[1] = shifted Cholesky retries since wssr_create,
  * out[2] = kernel launches it enqueued, out[3 + s] = plane rotations applied
- * in sweep s (0 past the last sweep). Writes n values (n >= 0). */
+ * in sweep s (0 past the last sweep), for s < jacobi_sweeps; then
+ * out[3 + jacobi_sweeps] = steps of the eigensolve's patch phase (rotations of
+ * the pairs left above the threshold, found from the whole Gram, in place of
+ * the closing sweeps; r <= 256 on the cluster eigensolve, else 0) and
+ * out[4 + jacobi_sweeps] = the rotations it applied. Writes n values (n >= 0). */
 wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n);
 
 /* Free the workspace (synchronises the device first). NULL is ignored. */

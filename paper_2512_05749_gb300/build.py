@@ -50,6 +50,8 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     extra = ["-DWSSR_CHECK_BOUNDS"] if checked else []
+    # extra compile flags for tuning builds (e.g. -DWSSR_EIG_TRACE); a change needs force=True
+    extra += os.environ.get("WSSR_NVCC_FLAGS", "").split()
 
     def one(src):
         obj = os.path.join(bdir, src.replace(".cu", ".o"))

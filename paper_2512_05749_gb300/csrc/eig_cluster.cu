@@ -68,10 +68,23 @@ __device__ __forceinline__ int ec_pos(int l) {
   return RMAX == 512 ? l + (l >= 32 ? 8 : 0) : l;
 }
 
+// Shared memory of the patch phase (up to r = 256, where W is in shared memory).
+template <int RMAX>
+struct EcPatchSmem {
+  static constexpr int N = EcCfg<RMAX>::W_SMEM ? RMAX : 1;
+  float gd[N];        // diagonal of B^T B
+  int4 vl[2 * N];     // the violators of all ranks: {p, q, (b_p . b_q) bits, 0}
+  int2 spq[N / 2 + 1];  // the pairs rotated in this step
+  float2 scs[N / 2 + 1];
+  int wsum[32];       // warp totals of the list scan
+  int nsel;
+};
+
 template <int RMAX>
 struct EcSmem {
   float B[RMAX * EcCfg<RMAX>::LD];
   float W[EcCfg<RMAX>::W_SMEM ? RMAX * EcCfg<RMAX>::LD : 4];
+  EcPatchSmem<RMAX> pt;
   float4 recv[2][EC_CLUSTER][RMAX / 2];  // per buffer, source rank and pair: {app, aqq, apq, 0}
   uint64_t bar[2];                       // per buffer: completes when all ranks' partials have landed
   int rotated;                           // rank 0: continue after the last sweep (read by every CTA)
@@ -148,11 +161,240 @@ __device__ __forceinline__ bool ec_rotation(float app, float aqq, float apq, flo
   return true;
 }
 
+// Patch phase (r <= 256). The closing sweeps of cyclic Jacobi visit all
+// r (r - 1) / 2 pairs to rotate a handful (a warm step's last two sweeps
+// rotate tens of pairs, then one). After a sweep with few rotations the pairs
+// still coupled above tol are found from the whole Gram B^T B instead: each
+// rank forms B_c^T B_c over its rows into the global workspace, each rank sums
+// the eight partials of its slice of pairs (rows p = c mod 8) and lists the
+// violators, and every rank then takes the same greedy set of disjoint
+// violators in list order and rotates them with the Jacobi rotations of their
+// summed 2 x 2 Grams. This repeats until no pair is above tol (convergence:
+// every pair at once, a stricter test than a sweep without rotations), with a
+// return to full sweeps when the violators outnumber the list (2 r) or the
+// steps run out. Control flow depends only on integers every rank reads from
+// the same workspace words after a cluster barrier.
+constexpr int EC_PATCH_STEPS = 16;
+constexpr int EC_PATCH_CLS = 32;  // column classes j mod 32 of the Gram tiles
+
+// Workspace: the partial Grams (EC_CLUSTER x r x r floats, upper triangle
+// written), then 16 ints (list counts per rank, then the patch steps (Gram
+// checks) and patch rotations of the last launch), then the lists
+// (EC_CLUSTER x 2 r int4).
+__host__ __device__ __forceinline__ size_t ec_patch_counts_off(int r) {
+  return (size_t)EC_CLUSTER * r * r * sizeof(float);
+}
+__host__ __device__ __forceinline__ size_t ec_patch_lists_off(int r) { return ec_patch_counts_off(r) + 64; }
+__host__ __device__ __forceinline__ int ec_patch_cap(int r) { return 2 * r; }
+
+// WSSR_EIG_TRACE (a build flag for tuning): rank 0 prints the clock cycles of
+// each patch step's parts (Gram, reduction and list, gather, selection, rotation).
+#ifdef WSSR_EIG_TRACE
+#define EC_TRACE_MARK(k) \
+  if (crank == 0 && tid == 0) tr[k] = clock64()
+#else
+#define EC_TRACE_MARK(k)
+#endif
+
+// Returns true when no pair is left above tol, false to go back to full sweeps.
+template <int RMAX>
+__device__ __forceinline__ bool ec_patch(EcSmem<RMAX>& S, unsigned char* __restrict__ ws, int r, float tol,
+                                      int crank) {
+  using C = EcCfg<RMAX>;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = C::THREADS / 32;
+  constexpr int PER = RMAX / EC_PATCH_CLS;  // columns of one class
+  constexpr int PQ = PER / 2;               // of which one thread takes half on the q side
+  constexpr int NPAIR = EC_PATCH_CLS * (EC_PATCH_CLS + 1) / 2;  // class pairs tp <= tq
+  constexpr int NBLK = (NPAIR + 31) / 32 * 64;                    // 32 pairs x 2 halves a group
+  constexpr int SLOTS = C::THREADS / RMAX;  // rows of a slice handled at once
+  constexpr int NJ = RMAX / (EC_CLUSTER * SLOTS);
+  static_assert(NJ <= 32, "slice rows per thread exceed the mask");
+  float* part = reinterpret_cast<float*>(ws);
+  int* counts = reinterpret_cast<int*>(ws + ec_patch_counts_off(r));
+  int* stats = counts + EC_CLUSTER;
+  int4* lists = reinterpret_cast<int4*>(ws + ec_patch_lists_off(r));
+  const int cap = ec_patch_cap(r);
+  const size_t rr = (size_t)r * r;
+  float* mine = part + (size_t)crank * rr;
+#ifdef WSSR_EIG_TRACE
+  long long tr[6];
+#endif
+  for (int step = 0; step < EC_PATCH_STEPS; ++step) {
+    __syncthreads();
+    EC_TRACE_MARK(0);
+    // B_c^T B_c: thread = block of columns (tp + 32 a, tq + 32 (PQ hb + b)), tp <= tq,
+    // hb = 0, 1 (one per warp); lanes take consecutive (tp, tq), i.e. consecutive tq
+    // (distinct banks: column j of row l sits in bank (j + l) mod 32)
+    for (int blk = tid; blk < NBLK; blk += C::THREADS) {
+      const int hb = (blk >> 5) & 1;
+      int rem = ((blk >> 6) << 5) | (blk & 31);
+      if (rem >= NPAIR) continue;
+      int tp = 0;
+      while (rem >= EC_PATCH_CLS - tp) rem -= EC_PATCH_CLS - tp, ++tp;
+      const int tq = tp + rem;
+      float acc[PER][PQ];
+#pragma unroll
+      for (int a = 0; a < PER; ++a)
+#pragma unroll
+        for (int b = 0; b < PQ; ++b) acc[a][b] = 0.f;
+      for (int l = 0; l < C::RL; ++l) {
+        const int lp = ec_pos<RMAX>(l);
+        float bp[PER], bq[PQ];
+#pragma unroll
+        for (int a = 0; a < PER; ++a) bp[a] = S.B[min(tp + EC_PATCH_CLS * a, r - 1) * C::LD + lp];
+#pragma unroll
+        for (int b = 0; b < PQ; ++b) bq[b] = S.B[min(tq + EC_PATCH_CLS * (PQ * hb + b), r - 1) * C::LD + lp];
+#pragma unroll
+        for (int a = 0; a < PER; ++a)
+#pragma unroll
+          for (int b = 0; b < PQ; ++b) acc[a][b] = fmaf(bp[a], bq[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < PER; ++a)
+#pragma unroll
+        for (int b = 0; b < PQ; ++b) {
+          const int p = tp + EC_PATCH_CLS * a, q = tq + EC_PATCH_CLS * (PQ * hb + b);
+          if (p < r && q < r && (tp < tq || p <= q)) mine[(size_t)min(p, q) * r + max(p, q)] = acc[a][b];
+        }
+    }
+    cluster.sync();  // every rank's partial Gram is in the workspace (read past L1 below)
+    EC_TRACE_MARK(1);
+    for (int t = tid; t < r; t += C::THREADS) {
+      float g = 0.f;
+      for (int k = 0; k < EC_CLUSTER; ++k) g += __ldcg(part + (size_t)k * rr + (size_t)t * r + t);
+      S.pt.gd[t] = g;
+    }
+    __syncthreads();
+    // this rank's slice: rows p = crank + 8 (SLOTS j + slot), columns q > p
+    const int slot = tid / RMAX, q = tid % RMAX;
+    float sv[NJ];
+    unsigned mask = 0u;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int p = crank + EC_CLUSTER * (SLOTS * j + slot);
+      sv[j] = 0.f;
+      if (p < r && q > p && q < r) {
+        float g = 0.f;
+#pragma unroll
+        for (int k = 0; k < EC_CLUSTER; ++k) g += __ldcg(part + (size_t)k * rr + (size_t)p * r + q);
+        sv[j] = g;
+        // the test of ec_rotation, on the same values
+        const float nrm = sqrtf(S.pt.gd[p] * S.pt.gd[q]);
+        if (fabsf(g) > tol * nrm) mask |= 1u << j;
+      }
+    }
+    // block exclusive scan of the violator counts: fixed list positions
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) S.pt.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < NW ? S.pt.wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < NW) S.pt.wsum[lane] = v;
+    }
+    __syncthreads();
+    int off = (warp ? S.pt.wsum[warp - 1] : 0) + incl - cnt;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (!((mask >> j) & 1u)) continue;
+      const int p = crank + EC_CLUSTER * (SLOTS * j + slot);
+      if (off < cap) lists[(size_t)crank * cap + off] = make_int4(p, q, __float_as_int(sv[j]), 0);
+      ++off;
+    }
+    if (tid == 0) counts[crank] = S.pt.wsum[NW - 1];
+    cluster.sync();  // every rank's violators are listed
+    EC_TRACE_MARK(2);
+    int total = 0;
+    bool over = false;
+#pragma unroll
+    for (int k = 0; k < EC_CLUSTER; ++k) {
+      const int c = __ldcg(counts + k);
+      total += c;
+      over |= c > cap;
+    }
+    if (crank == 0 && tid == 0) stats[0] += 1;
+    if (total == 0) return true;
+    if (over || total > cap) return false;
+    {
+      int base = 0;
+      for (int k = 0; k < EC_CLUSTER; ++k) {
+        const int c = __ldcg(counts + k);
+        for (int e = tid; e < c; e += C::THREADS) S.pt.vl[base + e] = __ldcg(lists + (size_t)k * cap + e);
+        base += c;
+      }
+    }
+    __syncthreads();
+    EC_TRACE_MARK(3);
+    if (tid == 0) {
+      // greedy disjoint pairs in list order (the first violator is always taken)
+      unsigned taken[RMAX / 32];
+#pragma unroll
+      for (int w = 0; w < RMAX / 32; ++w) taken[w] = 0u;
+      int ns = 0;
+      for (int e = 0; e < total; ++e) {
+        const int4 v = S.pt.vl[e];
+        const int p = v.x, qq = v.y;
+        if (((taken[p >> 5] >> (p & 31)) | (taken[qq >> 5] >> (qq & 31))) & 1u) continue;
+        float c, s, t;
+        if (!ec_rotation(S.pt.gd[p], S.pt.gd[qq], __int_as_float(v.z), tol, c, s, t)) continue;
+        taken[p >> 5] |= 1u << (p & 31);
+        taken[qq >> 5] |= 1u << (qq & 31);
+        S.pt.spq[ns] = make_int2(p, qq);
+        S.pt.scs[ns] = make_float2(c, s);
+        ++ns;
+      }
+      S.pt.nsel = ns;
+      if (crank == 0) stats[1] += ns;
+    }
+    __syncthreads();
+    EC_TRACE_MARK(4);
+    const int ns = S.pt.nsel;
+    for (int e = tid; e < ns * C::RL; e += C::THREADS) {
+      const int k = e / C::RL, l = ec_pos<RMAX>(e % C::RL);
+      const int2 pq = S.pt.spq[k];
+      const float2 cs = S.pt.scs[k];
+      float* bp = &S.B[pq.x * C::LD + l];
+      float* bq = &S.B[pq.y * C::LD + l];
+      const float xp = *bp, xq = *bq;
+      *bp = cs.x * xp - cs.y * xq;
+      *bq = cs.y * xp + cs.x * xq;
+      if (C::W_SMEM) {
+        float* wp = &S.W[pq.x * C::LD + l];
+        float* wq = &S.W[pq.y * C::LD + l];
+        const float yp = *wp, yq = *wq;
+        *wp = cs.x * yp - cs.y * yq;
+        *wq = cs.y * yp + cs.x * yq;
+      }
+    }
+#ifdef WSSR_EIG_TRACE
+    __syncthreads();
+    EC_TRACE_MARK(5);
+    if (crank == 0 && tid == 0)
+      printf("eig patch step %d: violators %d selected %d cycles gram %lld reduce %lld gather %lld select %lld "
+             "rotate %lld\n",
+             step, total, ns, tr[1] - tr[0], tr[2] - tr[1], tr[3] - tr[2], tr[4] - tr[3], tr[5] - tr[4]);
+#endif
+  }
+  return false;
+}
+
 template <int RMAX>
 __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>::THREADS, 1)
     k_eig_cluster(const float* __restrict__ R, int r, int max_sweeps, float tol, float* __restrict__ W_out,
                   int* __restrict__ nsweeps_out, int* __restrict__ round_cnt, float2* __restrict__ rot_log,
-                  int* __restrict__ rank_out, uint64_t limit_ns, int* status) {
+                  int* __restrict__ rank_out, uint64_t limit_ns, int* status, unsigned char* __restrict__ patch_ws) {
   using C = EcCfg<RMAX>;
   extern __shared__ __align__(16) unsigned char ec_raw[];
   EcSmem<RMAX>& S = *reinterpret_cast<EcSmem<RMAX>*>(ec_raw);
@@ -170,6 +412,11 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
     const bool in = l < RL && row < r;
     S.B[j * C::LD + ec_pos<RMAX>(l)] = in ? R[(int64_t)row * r + j] : 0.f;
     if (C::W_SMEM) S.W[j * C::LD + ec_pos<RMAX>(l)] = (in && row == j) ? 1.f : 0.f;
+  }
+  const bool patch_ok = C::W_SMEM && patch_ws != nullptr;
+  if (patch_ok && crank == 0 && tid == 0) {
+    int* pstats = reinterpret_cast<int*>(patch_ws + ec_patch_counts_off(r)) + EC_CLUSTER;
+    pstats[0] = 0, pstats[1] = 0;
   }
   if (tid == 0) {
     ec_bar_init(&S.bar[0]);
@@ -194,7 +441,7 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
   const uint32_t round_bytes = (uint32_t)EC_CLUSTER * (uint32_t)h * 16u;
   int sweep = 0;
   uint32_t gr = 0;  // rounds so far: buffer gr & 1, its barrier's phase (gr >> 1) & 1
-  for (; sweep < max_sweeps; ++sweep) {
+  while (sweep < max_sweeps) {
     int rotated = 0;
     if (tid == 0) S.tmax = 0u;
     for (int k = 0; k < n1; ++k, ++gr) {
@@ -271,15 +518,21 @@ __global__ void __cluster_dims__(EC_CLUSTER, 1, 1) __launch_bounds__(EcCfg<RMAX>
       rotated += cnt;
     }
     // Every CTA counted the same rotations (identical inputs, identical arithmetic), but the
-    // loop exit is taken from rank 0's decision so that all CTAs meet the same cluster barriers
-    if (crank == 0 && tid == 0)
-      S.rotated = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop && !S.abort) ? 1 : 0;
+    // loop exit is taken from rank 0's decision so that all CTAs meet the same cluster barriers:
+    // 0 = done (no rotation, or none above t_stop), 1 = another sweep, 2 = the patch phase
+    if (crank == 0 && tid == 0) {
+      int next = (rotated > 0 && __uint_as_float(S.tmax) >= t_stop && !S.abort) ? 1 : 0;
+      if (next && patch_ok && rotated <= r * r / 4) next = 2;
+      S.rotated = next;
+    }
     cluster.sync();
     if (tid == 0) S.go = *cluster.map_shared_rank(&S.rotated, 0);
     __syncthreads();
-    if (!S.go) {
-      ++sweep;  // the last sweep: no rotation, or none above t_stop
-      break;
+    const int go = S.go;
+    ++sweep;
+    if (!go) break;
+    if constexpr (C::W_SMEM) {
+      if (go == 2 && ec_patch<RMAX>(S, patch_ws, r, tol, crank)) break;
     }
   }
   if (crank == 0 && tid == 0) *nsweeps_out = sweep;
@@ -368,8 +621,18 @@ bool eig_cluster_supported(int r) { return r >= 8 && r <= 512 && r % 2 == 0; }
 
 bool eig_cluster_logs(int r) { return r > 256; }
 
+size_t eig_patch_ws_bytes(int r) {
+  return r > 256 ? 0 : ec_patch_lists_off(r) + (size_t)EC_CLUSTER * ec_patch_cap(r) * sizeof(int4);
+}
+
+const int* eig_patch_stats(const void* patch_ws, int r) {
+  return reinterpret_cast<const int*>(static_cast<const unsigned char*>(patch_ws) + ec_patch_counts_off(r)) +
+         EC_CLUSTER;
+}
+
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st) {
+                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st,
+                       void* patch_ws) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_eig_cluster<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -383,11 +646,11 @@ int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* 
   if (r <= 256)
     k_eig_cluster<256><<<EC_CLUSTER, EcCfg<256>::THREADS, sizeof(EcSmem<256>), st>>>(
         R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out, lim,
-        status);
+        status, static_cast<unsigned char*>(patch_ws));
   else
     k_eig_cluster<512><<<EC_CLUSTER, EcCfg<512>::THREADS, sizeof(EcSmem<512>), st>>>(
         R, r, max_sweeps, tol, W_unsorted, nsweeps, round_cnt, reinterpret_cast<float2*>(rot_log), rank_out, lim,
-        status);
+        status, nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -161,8 +161,14 @@ void launch_jacobi_vectors(const float* rot_log, const int* nsweeps, int r, int 
 bool eig_cluster_supported(int r);
 bool eig_cluster_logs(int r);
 size_t eig_cluster_smem(int r);
+// patch_ws (eig_patch_ws_bytes(r), r <= 256; NULL: full sweeps only): the closing
+// sweeps are replaced by rotations of the pairs still above tol, found from the
+// whole Gram; eig_patch_stats(ws, r) -> {patch steps, patch rotations} (device ints).
 int launch_eig_cluster(const float* R, int r, int max_sweeps, float tol, float* W_unsorted, int* nsweeps,
-                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st);
+                       int* round_cnt, float* rot_log, int* rank_out, int64_t wait_us, int* status, cudaStream_t st,
+                       void* patch_ws);
+size_t eig_patch_ws_bytes(int r);
+const int* eig_patch_stats(const void* patch_ws, int r);
 void launch_rr_quotients_sort(const double* H, const float* W_unsorted, int r, double* q, double* sigma,
                               float* W_sorted, cudaStream_t st);
 // FP64 refinements (r64.cu). Factor: T_out = T (I - E / 2), E = T^T G T - I (P, E:

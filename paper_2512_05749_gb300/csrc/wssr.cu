@@ -117,6 +117,8 @@ struct wssr_ctx {
   float* TW = nullptr;         // r x r: TX W
   float* tc_gram_part = nullptr;  // tcgen05 Gram partials (splits x r x r)
   float* chol_ws = nullptr;       // r x r factor blocks above the shared-memory rank
+  void* eig_ws = nullptr;         // patch phase of the cluster eigensolve (r <= 256)
+  bool eig_patched = false;       // the last eigensolve ran with the patch phase
   float* jac_ws = nullptr;        // Jacobi matrix (ring coordinates) above the shared-memory rank
   void* TWT3 = nullptr;           // three bf16 terms of (T_X W)^T
   bool c_ready = false;           // h->c already holds V_out^T g
@@ -367,16 +369,22 @@ struct Hist {
 
 int64_t rows_of(const wssr_ctx* h, const Hist* hist) { return h->N + (hist ? h->r : 0); }
 
+// G = scale X^T X for a float block of L rows (FP32 products, FP64 partial sums).
+void gram_rows(wssr_ctx* h, const float* X, int64_t L, double* G, double scale, cudaStream_t st) {
+  launch_gram(X, L, h->r, h->gram_part, G, scale, st);
+  h->launches += 2;
+}
+
 // One Cholesky QR pass on a float block: Xo = X R^-1 (optional operand copies /
 // column sums over the first csum_rows rows).
 void cholqr_pass(wssr_ctx* h, const float* X, int64_t L, float* Xo, void* lp_row, void* lpT,
                  int64_t ldT, double* colsum_part, int64_t* nb_out, cudaStream_t st, int64_t csum_rows = -1) {
   const int r = h->r;
   Timed tm(h, WSSR_KCAT_ORTH, st);
-  launch_gram(X, L, r, h->gram_part, h->G, 1.0, st);
+  gram_rows(h, X, L, h->G, 1.0, st);
   launch_chol_inv(h->G, r, h->TY, h->status, h->status + 1, st, h->chol_ws);
   launch_apply(X, L, r, h->TY, Xo, lp_row, is_bf16(h) ? 1 : 0, lpT, ldT, colsum_part, nb_out, st, csum_rows);
-  h->launches += 4;
+  h->launches += 2;
 }
 
 // The r history rows of Y: Y[N + j, :] = gamma sigma_prev[j] (V_prev^T Xop)[j, :].
@@ -455,6 +463,15 @@ bool use_cluster_eig(int r) {
   return !onecta && eig_cluster_supported(r);
 }
 
+// WSSR_TUNE_EIG=nopatch runs the cluster eigensolve's closing sweeps in full (for comparisons).
+bool use_eig_patch() {
+  static const bool off = [] {
+    const char* e = getenv("WSSR_TUNE_EIG");
+    return e && strcmp(e, "nopatch") == 0;
+  }();
+  return !off;
+}
+
 // Rayleigh-Ritz on span(Xh) = span(Xh TX): Y = (O_c Xh) TX, H = Y^T Y scaled,
 // H = W L W^T (Jacobi), V_out = Xh (TX W), sigma from FP64 Rayleigh quotients.
 wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, float* V_out, double* sigma,
@@ -484,7 +501,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
   }
   right_multiply_Y(h, h->Y, TXu, L, st);
   Timed tm(h, WSSR_KCAT_RR, st);
-  launch_gram(h->Y, L, r, h->gram_part, h->G, gscale, st);
+  gram_rows(h, h->Y, L, h->G, gscale, st);
   double* sig = sigma ? sigma : h->c;  // h->c is r doubles of scratch when sigma is not wanted
   const bool on_cluster = use_cluster_eig(r);
   if (on_cluster) {
@@ -495,8 +512,9 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
     launch_chol_R(h->G, r, h->T, h->status, h->status + 1, st, h->chol_ws);
     // rotation threshold: above the rounding of the FP32 dot products (about u sqrt(r) relative)
     const float tol = 4.f * 5.96e-8f * sqrtf((float)r);
+    h->eig_patched = h->eig_ws && r <= 256 && use_eig_patch();
     if (launch_eig_cluster(h->T, r, ms, tol, h->Wu, h->nsweeps, cnt, h->rot_log, cnt + (size_t)ms * (r - 1),
-                           h->opt.wait_cap, h->status, st) != 0)
+                           h->opt.wait_cap, h->status, st, h->eig_patched ? h->eig_ws : nullptr) != 0)
       return WSSR_ERR_CUDA;
     h->launches += 2;
     if (eig_cluster_logs(r)) {
@@ -509,6 +527,7 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
       h->launches += 2;
     }
   } else {
+    h->eig_patched = false;
     launch_jacobi(h->G, r, h->opt.jacobi_sweeps, h->rot_log, h->nsweeps, h->status, st, h->jac_ws);
     launch_jacobi_vectors(h->rot_log, h->nsweeps, r, h->opt.jacobi_sweeps, h->W, st);
     h->launches += 2;
@@ -534,8 +553,8 @@ wssr_status rr_finish(wssr_ctx* h, const wssr_operator* op, const void* Xop, flo
                      nullptr, st);
     h->launches += 1;
   }
-  // Gram (2), T W (1)
-  h->launches += 2 + 1;
+  // T W (1)
+  h->launches += 1;
   if (!on_cluster && !refine) {
     // Ritz values: FP64 Rayleigh quotients of the rotated block Y W
     launch_apply(h->Y, L, r, h->W, h->Y2, nullptr, 0, nullptr, 0, nullptr, nullptr, st);
@@ -767,6 +786,7 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   ALLOC(dot_part, (size_t)std::max(dot_part_elems(M, r), dot_blk_part_elems(M, r)) * d);
   if (chol_ws_floats(r) > 0) ALLOC(chol_ws, (size_t)chol_ws_floats(r) * f);
   if (jacobi_ws_floats(r) > 0) ALLOC(jac_ws, (size_t)jacobi_ws_floats(r) * f);
+  if (eig_cluster_supported(std::min(r, 256))) ALLOC(eig_ws, eig_patch_ws_bytes(std::min(r, 256)));
   ALLOC(TX, (size_t)r * r * f);
   ALLOC(TY, (size_t)r * r * f);
   ALLOC(TW, (size_t)r * r * f);
@@ -1107,13 +1127,21 @@ wssr_status wssr_get_stats(wssr_handle h, int64_t* out, int32_t n) {
     if (cudaMemcpy(rounds.data(), cnt, rounds.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       return WSSR_ERR_CUDA;
   }
+  int patch[2] = {0, 0};
+  if (n > 3 + ms && h->eig_patched &&
+      cudaMemcpy(patch, eig_patch_stats(h->eig_ws, r), sizeof(patch), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return WSSR_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     int64_t v = 0;
     if (i == 0) v = dev_vals[0];
     else if (i == 1) v = dev_vals[1];
     else if (i == 2) v = h->launches;
-    else if (i - 3 < ms && i - 3 < dev_vals[0])
-      for (int k = 0; k < r - 1; ++k) v += rounds[(size_t)(i - 3) * (r - 1) + k];
+    else if (i - 3 < ms) {
+      if (i - 3 < dev_vals[0])
+        for (int k = 0; k < r - 1; ++k) v += rounds[(size_t)(i - 3) * (r - 1) + k];
+    } else if (i - 3 - ms < 2) {
+      v = patch[i - 3 - ms];
+    }
     out[i] = v;
   }
   return WSSR_OK;

@@ -375,14 +375,16 @@ def wssr_profile_end(h: int):
 
 
 def wssr_get_stats(h: int, max_sweeps: int = 12) -> dict:
-    """{'jacobi_sweeps', 'cholesky_shifts', 'launches', 'rotations_per_sweep'} of the
-    last step (synchronises)."""
-    n = 3 + max_sweeps
+    """{'jacobi_sweeps', 'cholesky_shifts', 'launches', 'rotations_per_sweep',
+    'patch_steps', 'patch_rotations'} of the last step (synchronises);
+    max_sweeps must be the handle's jacobi_sweeps option."""
+    n = 5 + max_sweeps
     out = (ctypes.c_int64 * n)()
     _check(load().wssr_get_stats(h, out, n), "wssr_get_stats")
     sweeps = int(out[0])
     return {"jacobi_sweeps": sweeps, "cholesky_shifts": out[1], "launches": out[2],
-            "rotations_per_sweep": [int(out[3 + i]) for i in range(min(sweeps, max_sweeps))]}
+            "rotations_per_sweep": [int(out[3 + i]) for i in range(min(sweeps, max_sweeps))],
+            "patch_steps": int(out[3 + max_sweeps]), "patch_rotations": int(out[4 + max_sweeps])}
 
 
 def wssr_mlp_param_count(desc: wssr_mlp_desc) -> int:
