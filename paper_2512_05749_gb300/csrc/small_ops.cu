@@ -8,6 +8,10 @@
 //   - the Woodbury apply of Eq. (updated_sr_1).
 #include <math.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -543,6 +547,427 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Cholesky factor up to r = WSSR_SMEM_RANK_MAX, all 32 x 32 blocks in shared
+// memory, one CTA of 16 warps. Same factor as k_chol_inv (FP64 equilibration,
+// FP32 blocked Cholesky of D G D, T = D R'^-1 or R = R' D^-1), organised for
+// latency:
+//   * a 32 x 32 block product is one warp's task, each lane an 8 x 4 tile of
+//     the output: three 16-byte shared loads per 32 FMAs. Blocks store the
+//     16-byte chunk j / 4 of row i at chunk (j / 4) xor (i / 8), so both the
+//     row-oriented and the column-oriented operand reads of a warp hit 32
+//     distinct banks;
+//   * the diagonal block is factored by one warp in registers (reciprocal
+//     square roots, no divisions), and the next diagonal block is updated and
+//     factored by warp 0 while the other warps run the rest of the trailing
+//     update (one step of lookahead; the warps that share warp 0's scheduler
+//     sit that phase out): two CTA barriers per block column;
+//   * the panel R_KJ = R_KK^-T A_KJ by forward substitution, one warp per
+//     block, in place;
+//   * the Gram is read as doubles and rounded to float in integer operations
+//     (the FP64 pipe of this part is narrow);
+//   * T = R'^-1: the diagonal blocks inverted by back substitution (one warp
+//     each, all at once), then recursive doubling over the diagonal: for the pair of
+//     diagonal regions [T11 X; 0 T22] of the level, X = -T11 (R12 T22), with
+//     the products of a level spread over warps (R12 T22 into a temporary of
+//     8 blocks, taken in column chunks from the last column, so that the
+//     columns of R12 still needed are never overwritten).
+namespace {
+
+constexpr int C2_TMP = 8;  // temporary blocks of the inverse
+
+// double -> float, round to nearest even, in integer operations (IEEE 754
+// binary64 -> binary32; results below the normal float range flush to a signed
+// zero): FP64 conversions and classifications run on the few FP64 units of
+// this part. *nonfinite set for an infinite or NaN input.
+__device__ __forceinline__ float c2_d2f(double x, bool& nonfinite) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ex == 0x7FF) {
+    nonfinite = true;
+    return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  }
+  int e = ex - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  unsigned mr = (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull), half = 0x10000000u;
+  if (rem > half || (rem == half && (mr & 1u))) {
+    if (++mr == 0x800000u) mr = 0u, ++e;
+  }
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mr);
+}
+constexpr int C2_WARPS = 16, C2_THREADS = 32 * C2_WARPS;
+
+__device__ __forceinline__ int c2_sw(int i, int j) { return (i << 5) + ((((j >> 2) ^ (i >> 3))) << 2) + (j & 3); }
+__device__ __forceinline__ const float4* c2_chunk(const float* b, int i, int c) {
+  return reinterpret_cast<const float4*>(b + (i << 5) + ((c ^ (i >> 3)) << 2));
+}
+
+// acc[t][u] += sum_k L(k, 8 rg + t) Rm(k, 4 cg + u)   (L^T Rm)
+__device__ __forceinline__ void c2_tn(float (&acc)[8][4], const float* L, const float* Rm, int rg, int cg) {
+#pragma unroll 4
+  for (int k = 0; k < 32; ++k) {
+    const float4 l0 = *c2_chunk(L, k, 2 * rg), l1 = *c2_chunk(L, k, 2 * rg + 1);
+    const float4 x = *c2_chunk(Rm, k, cg);
+    const float l[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+    const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[t][u] = fmaf(l[t], xv[u], acc[t][u]);
+  }
+}
+
+// acc[t][u] += sum_k L(8 rg + t, k) Rm(k, 4 cg + u)   (L Rm); each k step
+// issues 32 independent FMAs
+__device__ __forceinline__ void c2_nn(float (&acc)[8][4], const float* L, const float* Rm, int rg, int cg) {
+  const float* Lr = L + ((8 * rg) << 5);
+#pragma unroll 1
+  for (int kc = 0; kc < 8; ++kc) {
+    float lv[8][4], xv[4][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const float4 l = *reinterpret_cast<const float4*>(Lr + (t << 5) + ((kc ^ rg) << 2));
+      lv[t][0] = l.x, lv[t][1] = l.y, lv[t][2] = l.z, lv[t][3] = l.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 x = *c2_chunk(Rm, 4 * kc + q, cg);
+      xv[q][0] = x.x, xv[q][1] = x.y, xv[q][2] = x.z, xv[q][3] = x.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[t][u] = fmaf(lv[t][q], xv[q][u], acc[t][u]);
+  }
+}
+
+__device__ __forceinline__ void c2_zero(float (&acc)[8][4]) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
+}
+
+// C = sign acc (mode 0) or C -= acc (mode 1), this lane's 8 x 4 tile
+__device__ __forceinline__ void c2_put(float* C, const float (&acc)[8][4], int rg, int cg, int mode, float sign) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    float4* p = reinterpret_cast<float4*>(C + ((8 * rg + t) << 5) + ((cg ^ rg) << 2));
+    if (mode == 0) {
+      *p = make_float4(sign * acc[t][0], sign * acc[t][1], sign * acc[t][2], sign * acc[t][3]);
+    } else {
+      float4 v = *p;
+      v.x -= acc[t][0], v.y -= acc[t][1], v.z -= acc[t][2], v.w -= acc[t][3];
+      *p = v;
+    }
+  }
+}
+
+// One warp: A (32 x 32, upper part valid) = R^T R, R upper written over A,
+// rinv[k] = 1 / R_kk; lane j holds column j. Step k: pivot A_kk from lane k,
+// its reciprocal square root (hardware estimate and one Newton step,
+// y (3 - x y^2) / 2), row k of R = A_k. / sqrt(A_kk), and the rank-1 update of
+// the rows below with R_ki broadcast from lane i. Returns true on a pivot at or
+// below 1e-8 (the Gram is equilibrated to unit diagonal).
+__device__ __forceinline__ bool c2_factor(float* A, float* rinv, int lane) {
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = A[c2_sw(i, lane)];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float piv = __shfl_sync(0xffffffffu, a[k], k);
+    bad |= !(piv > 1e-8f);
+    const float x = fmaxf(piv, 1e-30f);
+    float rs = rsqrtf(x);
+    rs = rs * fmaf(-0.5f * x * rs, rs, 1.5f);
+    const float rk = lane > k ? a[k] * rs : (lane == k ? x * rs : 0.f);
+    A[c2_sw(k, lane)] = rk;
+    if (lane == k) rinv[k] = rs;
+#pragma unroll
+    for (int i = k + 1; i < 32; ++i) a[i] = fmaf(-__shfl_sync(0xffffffffu, rk, i), rk, a[i]);
+  }
+  return bad;
+}
+
+// One warp: Tb = R^-1 for the upper triangular R in A (rinv[i] = 1 / R_ii):
+// column `lane` by back substitution from the bottom, rows of R read as
+// broadcast 16-byte chunks.
+__device__ __forceinline__ void c2_tinv(const float* A, float* Tb, const float* rinv, int lane) {
+  float t[32];
+#pragma unroll
+  for (int i = 31; i >= 0; --i) {
+    float sq[4] = {(i == lane) ? 1.f : 0.f, 0.f, 0.f, 0.f};  // four independent partial sums
+#pragma unroll
+    for (int c = (i + 1) >> 2; c < 8; ++c) {
+      const float4 v = *c2_chunk(A, i, c);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * c + q;
+        if (k > i) sq[q] = fmaf(-vv[q], t[k], sq[q]);
+      }
+    }
+    t[i] = ((sq[0] + sq[1]) + (sq[2] + sq[3])) * rinv[i];
+  }
+  __syncwarp();  // Tb may be A itself
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Tb[c2_sw(i, lane)] = t[i];
+}
+
+// One warp: the panel block in place, X = R^-T A (R^T X = A, R upper in Rkk,
+// rinv[i] = 1 / R_ii): column `lane` by forward substitution, each solved row
+// removed from the rows below with row i of R (broadcast chunks).
+__device__ __forceinline__ void c2_panel(const float* Rkk, const float* rinv, float* A, int lane) {
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = A[c2_sw(i, lane)];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    a[i] *= rinv[i];
+#pragma unroll
+    for (int c = (i + 1) >> 2; c < 8; ++c) {
+      const float4 v = *c2_chunk(Rkk, i, c);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * c + q > i) a[4 * c + q] = fmaf(-vv[q], a[i], a[4 * c + q]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) A[c2_sw(i, lane)] = a[i];
+}
+
+template <bool OUT_R>
+__global__ void __launch_bounds__(C2_THREADS) k_chol2(const double* __restrict__ G, int r, float* __restrict__ T,
+                                                int* status, int* shift_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = (r + CB - 1) / CB;
+  const int nblk = nb * (nb + 1) / 2;
+  double* d = reinterpret_cast<double*>(smem_raw);                                        // r doubles
+  float* B = reinterpret_cast<float*>(smem_raw + (size_t)WSSR_SMEM_RANK_MAX * sizeof(double));  // nblk blocks
+  float* TMP = B + (size_t)nblk * CBE;                                   // C2_TMP blocks (the inverse)
+  float* rinv = TMP + (OUT_R ? 0 : (size_t)C2_TMP * CBE);                // 1 / R_ii, nb x 32
+  __shared__ float df[WSSR_SMEM_RANK_MAX];  // d (FP32), or 1 / d for the R output
+  __shared__ int flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rg = lane >> 3, cg = lane & 7;
+#ifdef WSSR_CHOL_TRACE
+  long long tc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  tc[0] = clock64();
+#endif
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  if (tid < r) {
+    const double gii = G[(int64_t)tid * r + tid];
+    if (!isfinite(gii)) flag = 2;
+    else if (!(gii > 0.0)) flag = 1;
+    d[tid] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
+    df[tid] = (float)d[tid];
+  }
+  __syncthreads();
+  if (flag) {
+    if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
+    return;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const float shift = attempt ? 1e-5f : 0.f;
+    for (int e0 = tid; e0 < CBE; e0 += C2_THREADS) {
+      // equilibrated upper blocks, identity padding beyond r; thread = element (i, c) of every block
+      const int i = e0 / CB, c = e0 % CB;
+      int I = 0, J = 0;
+      for (int b0 = 0; b0 < nblk; b0 += 12) {
+        // twelve loads in flight per thread (the Gram is read once, latency-bound)
+        double gv[12];
+        int gi[12], gj[12];
+#pragma unroll
+        for (int u = 0; u < 12; ++u) {
+          gi[u] = I * CB + i, gj[u] = J * CB + c;
+          gv[u] = (b0 + u < nblk && gi[u] < r && gj[u] < r) ? G[(int64_t)gi[u] * r + gj[u]] : 0.0;
+          if (++J == nb) J = ++I;
+        }
+#pragma unroll
+        for (int u = 0; u < 12; ++u) {
+          if (b0 + u >= nblk) break;
+          float v;
+          if (gi[u] < r && gj[u] < r) {
+            bool nonfinite = false;
+            const float g = c2_d2f(gv[u], nonfinite);
+            if (nonfinite) flag = 2;
+            v = g * df[gi[u]] * df[gj[u]] + (gi[u] == gj[u] ? shift : 0.f);
+          } else {
+            v = (gi[u] == gj[u]) ? 1.f : 0.f;
+          }
+          B[(b0 + u) * CBE + c2_sw(i, c)] = v;
+        }
+      }
+    }
+    __syncthreads();
+#ifdef WSSR_CHOL_TRACE
+    tc[1] = clock64();
+#endif
+    if (flag == 2) break;
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    if (warp == 0) {
+      const bool bad = c2_factor(B, rinv, lane);
+      if (lane == 0 && bad) flag = 1;
+    }
+    __syncthreads();
+    for (int K = 0; K < nb && !flag; ++K) {
+      const int np = nb - 1 - K;
+      // panel, in place: R_KJ = R_KK^-T A_KJ
+      if (warp < np) c2_panel(B + blk_id(K, K, nb) * CBE, rinv + K * CB, B + blk_id(K, K + 1 + warp, nb) * CBE, lane);
+      __syncthreads();
+      if (np > 0) {
+        // trailing A_IJ -= R_KI^T R_KJ, K < I <= J; warp 0 takes (K+1, K+1) and factors it,
+        // alone on its scheduler (warps 4, 8, 12 share it and sit this phase out)
+        if (warp == 0) {
+          float* A = B + blk_id(K + 1, K + 1, nb) * CBE;
+          const float* R1 = B + blk_id(K, K + 1, nb) * CBE;
+          float acc[8][4];
+          c2_zero(acc);
+          c2_tn(acc, R1, R1, rg, cg);
+          c2_put(A, acc, rg, cg, 1, 1.f);
+          __syncwarp();
+#ifdef WSSR_CHOL_TRACE
+          const long long cd = clock64();
+#endif
+          const bool bad = c2_factor(A, rinv + (K + 1) * CB, lane);
+          if (lane == 0 && bad) flag = 1;
+#ifdef WSSR_CHOL_TRACE
+          tc[6] += clock64() - cd;
+#endif
+        } else if (warp & 3) {
+          const int ntr = np * (np + 1) / 2;
+          constexpr int NWK = C2_WARPS - C2_WARPS / 4;  // worker warps
+          const int widx = warp - warp / 4 - 1;
+          for (int m = 1 + widx; m < ntr; m += NWK) {
+            int ii = 0, rem = m;
+            while (rem >= np - ii) rem -= np - ii, ++ii;
+            const int jj = ii + rem;
+            float acc[8][4];
+            c2_zero(acc);
+            c2_tn(acc, B + blk_id(K, K + 1 + ii, nb) * CBE, B + blk_id(K, K + 1 + jj, nb) * CBE, rg, cg);
+            c2_put(B + blk_id(K + 1 + ii, K + 1 + jj, nb) * CBE, acc, rg, cg, 1, 1.f);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#ifdef WSSR_CHOL_TRACE
+    tc[2] = clock64();
+#endif
+    if (flag == 0) break;
+    if (flag == 1 && attempt == 0) {
+      if (tid == 0 && shift_count) atomicAdd(shift_count, 1);
+      __syncthreads();
+    }
+  }
+  if (flag) {
+    if (tid == 0) set_status(status, flag == 2 ? WSSR_ERR_NONFINITE : WSSR_ERR_BREAKDOWN);
+    return;
+  }
+  if (OUT_R) {
+    // R = R' D^-1: column j scaled by 1 / d_j; zeros below the diagonal
+    __syncthreads();
+    if (tid < r) df[tid] = (float)(1.0 / d[tid]);
+    __syncthreads();
+    for (int i = warp; i < r; i += C2_WARPS) {
+      const int I = i / CB, ii = i % CB;
+      float* Rrow = T + (int64_t)i * r;
+      for (int j = lane; j < r; j += 32) {
+        const int J = j / CB;
+        Rrow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + c2_sw(ii, lane)] * df[j] : 0.f;
+      }
+    }
+    return;
+  }
+  if constexpr (!OUT_R) {
+  // the diagonal blocks become T_KK = R_KK^-1
+  if (warp < nb) c2_tinv(B + blk_id(warp, warp, nb) * CBE, B + blk_id(warp, warp, nb) * CBE, rinv + warp * CB, lane);
+  __syncthreads();
+#ifdef WSSR_CHOL_TRACE
+  tc[3] = clock64();
+#endif
+  // recursive doubling: level s pairs the inverted regions [a, a + s) and [a + s, a + s + s2)
+  for (int s = 1; s < nb; s *= 2) {
+    const int npair = (nb + 2 * s - 1) / (2 * s);  // pairs with a + s < nb: all but maybe the last
+    int cw = C2_TMP / (s * npair);
+    if (cw < 1) cw = 1;
+    const int nchunk = (s + cw - 1) / cw;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      // phase 1: P_pc = sum_{k <= c} R12[p][k] T22[k][c] for this chunk's columns (from the last)
+      for (int task = warp; task < npair * s * cw; task += C2_WARPS) {
+        const int pr = task / (s * cw), w = task % (s * cw), p = w / cw, cl = w % cw;
+        const int a = pr * 2 * s, s2 = min(s, nb - a - s);
+        if (s2 <= 0) continue;
+        const int c = s2 - 1 - (ch * cw + cl);
+        if (c < 0) continue;
+        float acc[8][4];
+        c2_zero(acc);
+        for (int k = 0; k <= c; ++k)
+          c2_nn(acc, B + blk_id(a + p, a + s + k, nb) * CBE, B + blk_id(a + s + k, a + s + c, nb) * CBE, rg, cg);
+        c2_put(TMP + task * CBE, acc, rg, cg, 0, 1.f);
+      }
+      __syncthreads();
+      // phase 2: X_pc = -sum_{q >= p} T11[p][q] P_qc, over R12[p][c]
+      for (int task = warp; task < npair * s * cw; task += C2_WARPS) {
+        const int pr = task / (s * cw), w = task % (s * cw), p = w / cw, cl = w % cw;
+        const int a = pr * 2 * s, s2 = min(s, nb - a - s);
+        if (s2 <= 0) continue;
+        const int c = s2 - 1 - (ch * cw + cl);
+        if (c < 0) continue;
+        float acc[8][4];
+        c2_zero(acc);
+        for (int q = p; q < s; ++q)
+          c2_nn(acc, B + blk_id(a + p, a + q, nb) * CBE, TMP + (pr * s * cw + q * cw + cl) * CBE, rg, cg);
+        c2_put(B + blk_id(a + p, a + s + c, nb) * CBE, acc, rg, cg, 0, -1.f);
+      }
+      __syncthreads();
+    }
+#ifdef WSSR_CHOL_TRACE
+    if (s == 1) tc[4] = clock64();
+    if (s == 2) tc[5] = clock64();
+#endif
+  }
+#ifdef WSSR_CHOL_TRACE
+  tc[7] = clock64();
+#endif
+  // T = D T' (rows scaled by d_i), zeros below the diagonal
+  for (int i = warp; i < r; i += C2_WARPS) {
+    const float di = df[i];
+    const int I = i / CB, ii = i % CB;
+    float* Trow = T + (int64_t)i * r;
+    for (int j = lane; j < r; j += 32) {
+      const int J = j / CB;
+      Trow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + c2_sw(ii, lane)] * di : 0.f;
+    }
+  }
+#ifdef WSSR_CHOL_TRACE
+  if (tid == 0)
+    printf("chol2 r %d: cycles load %lld factor %lld (warp 0 diagonal %lld) diag-inverses %lld level1 %lld "
+           "level2 %lld rest %lld output %lld\n",
+           r, tc[1] - tc[0], tc[2] - tc[1], tc[6], tc[3] - tc[2], tc[4] - tc[3], tc[5] - tc[4], tc[7] - tc[5],
+           clock64() - tc[7]);
+#endif
+  }
+}
+}  // namespace
+
+size_t chol2_smem(int r, bool out_r) {
+  const int nb = (r + CB - 1) / CB;
+  const size_t blocks = (size_t)nb * (nb + 1) / 2 + (out_r ? 0 : C2_TMP);
+  return (size_t)WSSR_SMEM_RANK_MAX * sizeof(double) + blocks * CBE * sizeof(float) + (size_t)nb * CB * sizeof(float);
+}
+
 // floats of the r x r factor's blocks (packed upper blocks, panel, diagonal inverses)
 int64_t chol_blocks_floats(int r) {
   const int nb = (r + CB - 1) / CB;
@@ -558,8 +983,33 @@ size_t chol_inv_smem(int r) {
 
 int64_t chol_ws_floats(int r) { return r <= WSSR_SMEM_RANK_MAX ? 0 : chol_blocks_floats(r); }
 
+// WSSR_TUNE_CHOL=strip runs the strip-GEMM kernel at every rank (for comparisons).
+bool use_chol2(int r) {
+  static const bool strip = [] {
+    const char* e = getenv("WSSR_TUNE_CHOL");
+    return e && strcmp(e, "strip") == 0;
+  }();
+  return !strip && r <= WSSR_SMEM_RANK_MAX;
+}
+
+template <bool OUT_R>
+bool chol2_attr() {
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncSetAttribute(k_chol2<OUT_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol2_smem(WSSR_SMEM_RANK_MAX, OUT_R)) != cudaSuccess)
+      return false;  // the error stays pending and is reported by the caller's launch check
+    done = true;
+  }
+  return true;
+}
+
 void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_count,
                      cudaStream_t st, float* ws) {
+  if (use_chol2(r)) {
+    if (chol2_attr<false>()) k_chol2<false><<<1, C2_THREADS, chol2_smem(r, false), st>>>(G, r, T, status, shift_count);
+    return;
+  }
   const size_t sm = chol_inv_smem(r);
   static bool attr_set = false;
   if (!attr_set) {
@@ -578,6 +1028,10 @@ void launch_chol_inv(const double* G, int r, float* T, int* status, int* shift_c
 }
 
 void launch_chol_R(const double* G, int r, float* R, int* status, int* shift_count, cudaStream_t st, float* ws) {
+  if (use_chol2(r)) {
+    if (chol2_attr<true>()) k_chol2<true><<<1, C2_THREADS, chol2_smem(r, true), st>>>(G, r, R, status, shift_count);
+    return;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_chol_inv<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
