@@ -779,33 +779,39 @@ __global__ void __launch_bounds__(C2_THREADS) k_chol2(const double* __restrict__
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     const float shift = attempt ? 1e-5f : 0.f;
-    for (int e0 = tid; e0 < CBE; e0 += C2_THREADS) {
-      // equilibrated upper blocks, identity padding beyond r; thread = element (i, c) of every block
-      const int i = e0 / CB, c = e0 % CB;
+    {
+      // equilibrated upper blocks, identity padding beyond r; thread = elements (i, c), (i, c + 1)
+      // of every block (one 16-byte load of two doubles: r and c are even), eight loads in flight
+      const int i = tid >> 4, c = (tid & 15) * 2;
       int I = 0, J = 0;
-      for (int b0 = 0; b0 < nblk; b0 += 12) {
-        // twelve loads in flight per thread (the Gram is read once, latency-bound)
-        double gv[12];
-        int gi[12], gj[12];
+      for (int b0 = 0; b0 < nblk; b0 += 8) {
+        double2 gv[8];
+        int gi[8], gj[8];
 #pragma unroll
-        for (int u = 0; u < 12; ++u) {
+        for (int u = 0; u < 8; ++u) {
           gi[u] = I * CB + i, gj[u] = J * CB + c;
-          gv[u] = (b0 + u < nblk && gi[u] < r && gj[u] < r) ? G[(int64_t)gi[u] * r + gj[u]] : 0.0;
+          gv[u] = (b0 + u < nblk && gi[u] < r && gj[u] < r)
+                      ? *reinterpret_cast<const double2*>(G + (int64_t)gi[u] * r + gj[u])
+                      : make_double2(0.0, 0.0);
           if (++J == nb) J = ++I;
         }
 #pragma unroll
-        for (int u = 0; u < 12; ++u) {
+        for (int u = 0; u < 8; ++u) {
           if (b0 + u >= nblk) break;
-          float v;
-          if (gi[u] < r && gj[u] < r) {
-            bool nonfinite = false;
-            const float g = c2_d2f(gv[u], nonfinite);
-            if (nonfinite) flag = 2;
-            v = g * df[gi[u]] * df[gj[u]] + (gi[u] == gj[u] ? shift : 0.f);
-          } else {
-            v = (gi[u] == gj[u]) ? 1.f : 0.f;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int gjh = gj[u] + h;
+            float v;
+            if (gi[u] < r && gjh < r) {
+              bool nonfinite = false;
+              const float g = c2_d2f(h ? gv[u].y : gv[u].x, nonfinite);
+              if (nonfinite) flag = 2;
+              v = g * df[gi[u]] * df[gjh] + (gi[u] == gjh ? shift : 0.f);
+            } else {
+              v = (gi[u] == gjh) ? 1.f : 0.f;
+            }
+            B[(b0 + u) * CBE + c2_sw(i, c + h)] = v;
           }
-          B[(b0 + u) * CBE + c2_sw(i, c)] = v;
         }
       }
     }
@@ -880,12 +886,21 @@ __global__ void __launch_bounds__(C2_THREADS) k_chol2(const double* __restrict__
     __syncthreads();
     if (tid < r) df[tid] = (float)(1.0 / d[tid]);
     __syncthreads();
+    // rows over warps, 16-byte column chunks over lanes (r is a multiple of 8)
     for (int i = warp; i < r; i += C2_WARPS) {
       const int I = i / CB, ii = i % CB;
       float* Rrow = T + (int64_t)i * r;
-      for (int j = lane; j < r; j += 32) {
+      for (int j = 4 * lane; j < r; j += 128) {
         const int J = j / CB;
-        Rrow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + c2_sw(ii, lane)] * df[j] : 0.f;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (I <= J) {
+          v = *c2_chunk(B + blk_id(I, J, nb) * CBE, ii, (j % CB) >> 2);
+          v.x = i <= j ? v.x * df[j] : 0.f;
+          v.y = i <= j + 1 ? v.y * df[j + 1] : 0.f;
+          v.z = i <= j + 2 ? v.z * df[j + 2] : 0.f;
+          v.w = i <= j + 3 ? v.w * df[j + 3] : 0.f;
+        }
+        *reinterpret_cast<float4*>(Rrow + j) = v;
       }
     }
     return;
@@ -946,9 +961,17 @@ __global__ void __launch_bounds__(C2_THREADS) k_chol2(const double* __restrict__
     const float di = df[i];
     const int I = i / CB, ii = i % CB;
     float* Trow = T + (int64_t)i * r;
-    for (int j = lane; j < r; j += 32) {
+    for (int j = 4 * lane; j < r; j += 128) {
       const int J = j / CB;
-      Trow[j] = (I <= J && i <= j) ? B[blk_id(I, J, nb) * CBE + c2_sw(ii, lane)] * di : 0.f;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (I <= J) {
+        v = *c2_chunk(B + blk_id(I, J, nb) * CBE, ii, (j % CB) >> 2);
+        v.x = i <= j ? v.x * di : 0.f;
+        v.y = i <= j + 1 ? v.y * di : 0.f;
+        v.z = i <= j + 2 ? v.z * di : 0.f;
+        v.w = i <= j + 3 ? v.w * di : 0.f;
+      }
+      *reinterpret_cast<float4*>(Trow + j) = v;
     }
   }
 #ifdef WSSR_CHOL_TRACE
