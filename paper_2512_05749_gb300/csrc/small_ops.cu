@@ -134,8 +134,16 @@ constexpr int GT = 64;          // output tile
 constexpr int GK = 32;          // rows per smem stage
 constexpr int GFLUSH = 256;     // rows per FP32 partial
 
-int gram_nb(int64_t L) {
+// Row chunks of the Gram: about 608 CTAs (four per SM of the 152) over the
+// tile pairs, at least 128 rows a chunk. Each chunk writes an r x r FP64
+// partial that the reduction reads back, so chunks much shorter than that
+// cost more in partials than they gain in parallelism.
+int gram_nb(int64_t L, int r) {
+  const int T = (r + GT - 1) / GT;
+  const int pairs = T * (T + 1) / 2;
   int64_t nb = ceil_div(L, 128);
+  const int64_t cap = 608 / pairs;
+  if (nb > cap) nb = cap;
   if (nb > 256) nb = 256;
   if (nb < 1) nb = 1;
   return (int)nb;
@@ -232,11 +240,11 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int r, do
 }
 }  // namespace
 
-int64_t gram_part_elems(int64_t L, int r) { return (int64_t)gram_nb(L) * r * r; }
+int64_t gram_part_elems(int64_t L, int r) { return (int64_t)gram_nb(L, r) * r * r; }
 
 void launch_gram_any(const void* X, int x_bf16, int64_t L, int r, double* part, double* G,
                      double scale, cudaStream_t st) {
-  const int nb = gram_nb(L);
+  const int nb = gram_nb(L, r);
   const int64_t chunk = ceil_div(ceil_div(L, nb), GK) * GK;
   const int nbe = (int)ceil_div(L, chunk);
   const int T = (r + GT - 1) / GT;

@@ -747,7 +747,10 @@ wssr_status wssr_create(int64_t N, int64_t M, int32_t r, double lambda, const ws
   h->yp_elems = yp_capacity(h);
   // column-sum partials: split reduction (16-row blocks of Y), casts and applies (64-row blocks)
   const int64_t blocks64 = std::max(ceil_div(N, 16), ceil_div(std::max(N + r, M), 64));
-  const int64_t gpart = std::max(gram_part_elems(N + r, r), gram_part_elems(M, r));
+  // the Gram partials at every working rank up to r_cap (their count depends on the rank)
+  int64_t gpart = 0;
+  for (int rr = 8; rr <= r; rr += 8)
+    gpart = std::max(gpart, std::max(gram_part_elems(N + rr, rr), gram_part_elems(M, rr)));
   cudaError_t e = cudaSuccess;
 #define ALLOC(p, bytes) \
   if (e == cudaSuccess) e = dalloc(h->regions, &h->p, (bytes))
