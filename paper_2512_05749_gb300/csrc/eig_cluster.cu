@@ -74,11 +74,43 @@ struct EcPatchSmem {
   static constexpr int N = EcCfg<RMAX>::W_SMEM ? RMAX : 1;
   float gd[N];        // diagonal of B^T B
   int4 vl[2 * N];     // the violators of all ranks: {p, q, (b_p . b_q) bits, 0}
+  int4 vl2[2 * N];    // the next list while it is assembled
   int2 spq[N / 2 + 1];  // the pairs rotated in this step
   float2 scs[N / 2 + 1];
+  int colidx[N / 4 + 2];  // the columns those pairs rotated (incremental check)
+  unsigned rmask[N / 32 + 1];
   int wsum[32];       // warp totals of the list scan
   int nsel;
 };
+
+// Block-wide exclusive scan of one count per thread (all threads call it):
+// returns this thread's offset, *total the sum. Deterministic positions.
+template <int THREADS>
+__device__ __forceinline__ int ec_block_scan(int cnt, int* wsum, int* total) {
+  constexpr int NW = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  __syncthreads();  // wsum may still be read from a previous scan
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int v = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < NW) wsum[lane] = v;
+  }
+  __syncthreads();
+  *total = wsum[NW - 1];
+  return (warp ? wsum[warp - 1] : 0) + incl - cnt;
+}
 
 template <int RMAX>
 struct EcSmem {
@@ -202,12 +234,11 @@ __device__ __forceinline__ bool ec_patch(EcSmem<RMAX>& S, unsigned char* __restr
                                       int crank) {
   using C = EcCfg<RMAX>;
   cg::cluster_group cluster = cg::this_cluster();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = C::THREADS / 32;
+  const int tid = threadIdx.x;
   constexpr int PER = RMAX / EC_PATCH_CLS;  // columns of one class
-  constexpr int PQ = PER / 2;               // of which one thread takes half on the q side
+  constexpr int PQ = PER;                   // q-side columns of one thread's block
   constexpr int NPAIR = EC_PATCH_CLS * (EC_PATCH_CLS + 1) / 2;  // class pairs tp <= tq
-  constexpr int NBLK = (NPAIR + 31) / 32 * 64;                    // 32 pairs x 2 halves a group
+  constexpr int NBLK = NPAIR;
   constexpr int SLOTS = C::THREADS / RMAX;  // rows of a slice handled at once
   constexpr int NJ = RMAX / (EC_CLUSTER * SLOTS);
   static_assert(NJ <= 32, "slice rows per thread exceed the mask");
@@ -221,16 +252,25 @@ __device__ __forceinline__ bool ec_patch(EcSmem<RMAX>& S, unsigned char* __restr
 #ifdef WSSR_EIG_TRACE
   long long tr[6];
 #endif
+  constexpr int NJI = (RMAX / 4 * RMAX / EC_CLUSTER + C::THREADS - 1) / C::THREADS;  // incremental entries
+  static_assert(NJI <= 32, "incremental entries per thread exceed the mask");
+  static_assert(2 * RMAX <= C::THREADS, "one list entry per thread in the filter");
+  int nv = 0;         // entries of S.pt.vl: the violators found by the last check
+  bool have = false;  // a previous step left its list, diagonal and rotated pairs
   for (int step = 0; step < EC_PATCH_STEPS; ++step) {
     __syncthreads();
     EC_TRACE_MARK(0);
-    // B_c^T B_c: thread = block of columns (tp + 32 a, tq + 32 (PQ hb + b)), tp <= tq,
-    // hb = 0, 1 (one per warp); lanes take consecutive (tp, tq), i.e. consecutive tq
-    // (distinct banks: column j of row l sits in bank (j + l) mod 32)
+    const int ns_prev = have ? S.pt.nsel : 0;
+    // after a step that rotated few columns, only their Gram rows are formed again
+    const bool incr = have && 2 * ns_prev <= r / 4;
+    int total = 0;
+    if (!incr) {
+    // B_c^T B_c: thread = block of columns (tp + 32 a, tq + 32 b), tp <= tq; lanes take
+    // consecutive (tp, tq), i.e. consecutive tq (distinct banks: column j of row l sits
+    // in bank (j + l) mod 32)
     for (int blk = tid; blk < NBLK; blk += C::THREADS) {
-      const int hb = (blk >> 5) & 1;
-      int rem = ((blk >> 6) << 5) | (blk & 31);
-      if (rem >= NPAIR) continue;
+      constexpr int hb = 0;
+      int rem = blk;
       int tp = 0;
       while (rem >= EC_PATCH_CLS - tp) rem -= EC_PATCH_CLS - tp, ++tp;
       const int tq = tp + rem;
@@ -286,26 +326,8 @@ __device__ __forceinline__ bool ec_patch(EcSmem<RMAX>& S, unsigned char* __restr
       }
     }
     // block exclusive scan of the violator counts: fixed list positions
-    const int cnt = __popc(mask);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) S.pt.wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      int v = lane < NW ? S.pt.wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-      }
-      if (lane < NW) S.pt.wsum[lane] = v;
-    }
-    __syncthreads();
-    int off = (warp ? S.pt.wsum[warp - 1] : 0) + incl - cnt;
+    int mine_total = 0;
+    int off = ec_block_scan<C::THREADS>(__popc(mask), S.pt.wsum, &mine_total);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       if (!((mask >> j) & 1u)) continue;
@@ -313,50 +335,184 @@ __device__ __forceinline__ bool ec_patch(EcSmem<RMAX>& S, unsigned char* __restr
       if (off < cap) lists[(size_t)crank * cap + off] = make_int4(p, q, __float_as_int(sv[j]), 0);
       ++off;
     }
-    if (tid == 0) counts[crank] = S.pt.wsum[NW - 1];
+    if (tid == 0) counts[crank] = mine_total;
     cluster.sync();  // every rank's violators are listed
     EC_TRACE_MARK(2);
-    int total = 0;
     bool over = false;
+    int cnt8[EC_CLUSTER];
+#pragma unroll
+    for (int k = 0; k < EC_CLUSTER; ++k) cnt8[k] = __ldcg(counts + k);
 #pragma unroll
     for (int k = 0; k < EC_CLUSTER; ++k) {
-      const int c = __ldcg(counts + k);
-      total += c;
-      over |= c > cap;
+      total += cnt8[k];
+      over |= cnt8[k] > cap;
     }
     if (crank == 0 && tid == 0) stats[0] += 1;
     if (total == 0) return true;
     if (over || total > cap) return false;
     {
       int base = 0;
+#pragma unroll
       for (int k = 0; k < EC_CLUSTER; ++k) {
-        const int c = __ldcg(counts + k);
-        for (int e = tid; e < c; e += C::THREADS) S.pt.vl[base + e] = __ldcg(lists + (size_t)k * cap + e);
-        base += c;
+        for (int e = tid; e < cnt8[k]; e += C::THREADS) S.pt.vl[base + e] = __ldcg(lists + (size_t)k * cap + e);
+        base += cnt8[k];
       }
     }
+    } else {
+      // the columns the last step rotated, in pair order, and their mask
+      const int nc = 2 * ns_prev;
+      for (int w = tid; w <= RMAX / 32; w += C::THREADS) S.pt.rmask[w] = 0u;
+      __syncthreads();
+      if (tid < ns_prev) {
+        const int2 pq = S.pt.spq[tid];
+        S.pt.colidx[2 * tid] = pq.x, S.pt.colidx[2 * tid + 1] = pq.y;
+        atomicOr(&S.pt.rmask[pq.x >> 5], 1u << (pq.x & 31));
+        atomicOr(&S.pt.rmask[pq.y >> 5], 1u << (pq.y & 31));
+      }
+      __syncthreads();
+      // this rank's rows of those columns' Gram rows: P[ix][k] = sum_l B[l][x] B[l][k]
+      for (int e = tid; e < nc * r; e += C::THREADS) {
+        const int ix = e / r, k = e % r, x = S.pt.colidx[ix];
+        float acc = 0.f;
+        for (int l = 0; l < C::RL; ++l) {
+          const int lp = ec_pos<RMAX>(l);
+          acc = fmaf(S.B[x * C::LD + lp], S.B[k * C::LD + lp], acc);
+        }
+        mine[(size_t)ix * r + k] = acc;
+      }
+      cluster.sync();  // every rank's partial rows are in the workspace
+      EC_TRACE_MARK(1);
+      // the new diagonal of the rotated columns (every CTA, rank order)
+      for (int t = tid; t < nc; t += C::THREADS) {
+        const int x = S.pt.colidx[t];
+        float g = 0.f;
+        for (int k = 0; k < EC_CLUSTER; ++k) g += __ldcg(part + (size_t)k * rr + (size_t)t * r + x);
+        S.pt.gd[x] = g;
+      }
+      __syncthreads();
+      // this rank's contiguous range of the entries (ix, k); a pair of two rotated
+      // columns is taken once, from the row of its smaller column
+      const int E = nc * r;
+      const int e0 = (int)((int64_t)E * crank / EC_CLUSTER), e1 = (int)((int64_t)E * (crank + 1) / EC_CLUSTER);
+      float sv[NJI];
+      int pv[NJI], qv[NJI];
+      unsigned mask = 0u;
+#pragma unroll
+      for (int j = 0; j < NJI; ++j) {
+        const int e = e0 + tid + C::THREADS * j;
+        sv[j] = 0.f, pv[j] = 0, qv[j] = 0;
+        if (e < e1) {
+          const int ix = e / r, k = e % r, x = S.pt.colidx[ix];
+          const bool krot = (S.pt.rmask[k >> 5] >> (k & 31)) & 1u;
+          if (k != x && !(krot && k < x)) {
+            float g = 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < EC_CLUSTER; ++c8) g += __ldcg(part + (size_t)c8 * rr + (size_t)ix * r + k);
+            const float nrm = sqrtf(S.pt.gd[min(x, k)] * S.pt.gd[max(x, k)]);
+            if (fabsf(g) > tol * nrm) {
+              mask |= 1u << j;
+              sv[j] = g, pv[j] = min(x, k), qv[j] = max(x, k);
+            }
+          }
+        }
+      }
+      int mine_total = 0;
+      int off = ec_block_scan<C::THREADS>(__popc(mask), S.pt.wsum, &mine_total);
+#pragma unroll
+      for (int j = 0; j < NJI; ++j) {
+        if (!((mask >> j) & 1u)) continue;
+        if (off < cap) lists[(size_t)crank * cap + off] = make_int4(pv[j], qv[j], __float_as_int(sv[j]), 0);
+        ++off;
+      }
+      if (tid == 0) counts[crank] = mine_total;
+      cluster.sync();  // every rank's new violators are listed
+      EC_TRACE_MARK(2);
+      // the list: the last check's violators away from the rotated columns (in
+      // their order), then the new ones in rank order
+      bool keep = false;
+      int4 old = make_int4(0, 0, 0, 0);
+      if (tid < nv) {
+        old = S.pt.vl[tid];
+        keep = !(((S.pt.rmask[old.x >> 5] >> (old.x & 31)) | (S.pt.rmask[old.y >> 5] >> (old.y & 31))) & 1u);
+      }
+      int nkeep = 0;
+      const int pos = ec_block_scan<C::THREADS>(keep ? 1 : 0, S.pt.wsum, &nkeep);
+      if (keep) S.pt.vl2[pos] = old;
+      int nnew = 0;
+      bool over = false;
+      int cnt8[EC_CLUSTER];
+#pragma unroll
+      for (int k = 0; k < EC_CLUSTER; ++k) cnt8[k] = __ldcg(counts + k);
+#pragma unroll
+      for (int k = 0; k < EC_CLUSTER; ++k) {
+        nnew += cnt8[k];
+        over |= cnt8[k] > cap;
+      }
+      total = nkeep + nnew;
+      if (crank == 0 && tid == 0) stats[0] += 1;
+      if (total == 0) return true;
+      if (over || total > cap) return false;
+      int base = nkeep;
+#pragma unroll
+      for (int k = 0; k < EC_CLUSTER; ++k) {
+        for (int e = tid; e < cnt8[k]; e += C::THREADS) S.pt.vl2[base + e] = __ldcg(lists + (size_t)k * cap + e);
+        base += cnt8[k];
+      }
+      __syncthreads();
+      for (int e = tid; e < total; e += C::THREADS) S.pt.vl[e] = S.pt.vl2[e];
+    }
+    nv = total;
+    have = true;
     __syncthreads();
     EC_TRACE_MARK(3);
-    if (tid == 0) {
-      // greedy disjoint pairs in list order (the first violator is always taken)
-      unsigned taken[RMAX / 32];
-#pragma unroll
-      for (int w = 0; w < RMAX / 32; ++w) taken[w] = 0u;
+    if (tid < 32) {
+      // greedy disjoint pairs in list order (the first violator is always taken), one warp:
+      // each chunk of 32 entries is tested against the taken columns (lane w < 8 holds
+      // word w of the mask), then its candidates are accepted in list order unless an
+      // accepted earlier entry of the chunk shares a column (the same choice as a serial
+      // walk of the list)
+      const int lane = tid;
+      unsigned takenw = 0u;
       int ns = 0;
-      for (int e = 0; e < total; ++e) {
-        const int4 v = S.pt.vl[e];
-        const int p = v.x, qq = v.y;
-        if (((taken[p >> 5] >> (p & 31)) | (taken[qq >> 5] >> (qq & 31))) & 1u) continue;
-        float c, s, t;
-        if (!ec_rotation(S.pt.gd[p], S.pt.gd[qq], __int_as_float(v.z), tol, c, s, t)) continue;
-        taken[p >> 5] |= 1u << (p & 31);
-        taken[qq >> 5] |= 1u << (qq & 31);
-        S.pt.spq[ns] = make_int2(p, qq);
-        S.pt.scs[ns] = make_float2(c, s);
-        ++ns;
+      for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        int p = -1, qq = -1;
+        float c = 1.f, sn = 0.f;
+        bool cand = false;
+        if (e < total) {
+          const int4 v = S.pt.vl[e];
+          p = v.x, qq = v.y;
+          float t;
+          cand = ec_rotation(S.pt.gd[p], S.pt.gd[qq], __int_as_float(v.z), tol, c, sn, t);
+        }
+        const unsigned wp = __shfl_sync(0xffffffffu, takenw, p >= 0 ? p >> 5 : 0);
+        const unsigned wq = __shfl_sync(0xffffffffu, takenw, qq >= 0 ? qq >> 5 : 0);
+        if (cand && (((wp >> (p & 31)) | (wq >> (qq & 31))) & 1u)) cand = false;
+        const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+        unsigned acc = 0u;
+        for (unsigned m = cmask; m; m &= m - 1u) {  // the candidates, in list order
+          const int j = __ffs(m) - 1;
+          const int pj = __shfl_sync(0xffffffffu, p, j), qj = __shfl_sync(0xffffffffu, qq, j);
+          const bool shares = ((acc >> lane) & 1u) && (p == pj || p == qj || qq == pj || qq == qj);
+          if (!__any_sync(0xffffffffu, shares)) acc |= 1u << j;
+        }
+        if ((acc >> lane) & 1u) {
+          const int pos = ns + __popc(acc & ((1u << lane) - 1u));
+          S.pt.spq[pos] = make_int2(p, qq);
+          S.pt.scs[pos] = make_float2(c, sn);
+        }
+        for (unsigned m = acc; m; m &= m - 1u) {
+          const int j = __ffs(m) - 1;
+          const int pj = __shfl_sync(0xffffffffu, p, j), qj = __shfl_sync(0xffffffffu, qq, j);
+          if ((pj >> 5) == lane) takenw |= 1u << (pj & 31);
+          if ((qj >> 5) == lane) takenw |= 1u << (qj & 31);
+        }
+        ns += __popc(acc);
       }
-      S.pt.nsel = ns;
-      if (crank == 0) stats[1] += ns;
+      if (lane == 0) {
+        S.pt.nsel = ns;
+        if (crank == 0) stats[1] += ns;
+      }
     }
     __syncthreads();
     EC_TRACE_MARK(4);
