@@ -578,11 +578,12 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ G,
 //     each, all at once), then recursive doubling over the diagonal: for the pair of
 //     diagonal regions [T11 X; 0 T22] of the level, X = -T11 (R12 T22), with
 //     the products of a level spread over warps (R12 T22 into a temporary of
-//     8 blocks, taken in column chunks from the last column, so that the
-//     columns of R12 still needed are never overwritten).
+//     16 blocks, taken in column chunks from the last column when a level's
+//     products need more, so that the columns of R12 still needed are never
+//     overwritten).
 namespace {
 
-constexpr int C2_TMP = 8;  // temporary blocks of the inverse
+constexpr int C2_TMP = 16;  // temporary blocks of the inverse (a level's products in one chunk)
 
 // double -> float, round to nearest even, in integer operations (IEEE 754
 // binary64 -> binary32; results below the normal float range flush to a signed
@@ -923,7 +924,10 @@ __global__ void __launch_bounds__(C2_THREADS) k_chol2(const double* __restrict__
   // recursive doubling: level s pairs the inverted regions [a, a + s) and [a + s, a + s + s2)
   for (int s = 1; s < nb; s *= 2) {
     const int npair = (nb + 2 * s - 1) / (2 * s);  // pairs with a + s < nb: all but maybe the last
+    // column chunk: as wide as the temporary allows, but no wider than the level
+    // (every task real, on consecutive warps spread over the four schedulers)
     int cw = C2_TMP / (s * npair);
+    if (cw > s) cw = s;
     if (cw < 1) cw = 1;
     const int nchunk = (s + cw - 1) / cw;
     for (int ch = 0; ch < nchunk; ++ch) {
