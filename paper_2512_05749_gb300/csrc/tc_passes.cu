@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&ctl->full[s], 1);
-      mbar_init(&ctl->empty[s], MU ? 2 : 1);
+      mbar_init(&ctl->empty[s], MU ? 5 : 1);  // the MMA commit (+ each of the 4 epilogue warps)
     }
     mbar_init(&ctl->accum, 1);
     ctl->abort = 0;
@@ -337,12 +337,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
         }
-        // all 128 threads decide together, so the named barrier never misses arrivals
-        if (!epi_bar_and(got)) {
-          if (et == 0) timeout(ctl, status);
+        // each warp releases the stage on its own (no epilogue-wide barrier on the
+        // ring's critical path); a warp whose wait ran out marks the abort, which
+        // ends the other warps' waits, and leaves without arriving
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) timeout(ctl, status);
           break;
         }
-        if (et == 0) mbar_arrive(&ctl->empty[s]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->empty[s]);
         if ((i & 15) == 15) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
