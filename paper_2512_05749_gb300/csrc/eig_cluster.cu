@@ -28,6 +28,12 @@
 // logs every round's rotations in the one-CTA Jacobi's log format and the
 // replay kernel builds W from them.
 //
+// Up to r = 256 the closing sweeps give way to a patch phase once a sweep
+// rotates few pairs (ec_patch below): the pairs still coupled above the
+// threshold are found from the Gram B^T B (whole, then only the rows of the
+// columns rotated since) and rotated as greedy sets of disjoint pairs, with
+// two cluster barriers per check.
+//
 // After the sweeps: W is written (or replayed) unsorted; the FP64 Rayleigh quotients
 // w_j^T H w_j (second-order accurate in the eigenvector error) give the Ritz
 // values, which rank the columns in descending order.
